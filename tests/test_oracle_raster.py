@@ -1,0 +1,195 @@
+"""Pins of the oracle's binning, blending and gradient -- CPU only."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import raster as R
+from paper_2408_12894_gb300 import synth
+
+
+def _scene(seed, n, W=64, H=64, s_mean=-3.0, deg=0, radius=1.0):
+    g = synth.gaussian_set(seed, n, k=4, radius=radius, sh_degree=deg, s_mean=s_mean)
+    cam = synth.camera((0.3, -0.2, -3.0), W, H)
+    return g, cam
+
+
+@pytest.mark.parametrize("seed,n,W,H,tile", [(0, 200, 64, 64, 16), (1, 150, 70, 45, 16),
+                                             (2, 200, 64, 64, 8), (3, 120, 40, 40, 32)])
+def test_tiled_equals_per_pixel_brute_force(seed, n, W, H, tile):
+    g, cam = _scene(seed, n, W, H)
+    cfg = R.Config(tile_w=tile, tile_h=tile if tile != 32 else 8)
+    img_t, tf_t, _ = R.render(g, 0, 0.0, cam, cfg, tiled=True)
+    img_b, tf_b, _ = R.render(g, 0, 0.0, cam, cfg, tiled=False)
+    np.testing.assert_allclose(img_t, img_b, atol=1e-12)
+    np.testing.assert_allclose(tf_t, tf_b, atol=1e-12)
+
+
+def test_binning_invariants_and_per_tile_brute_force():
+    g, cam = _scene(4, 300, 80, 48, s_mean=-2.5)
+    cfg = R.Config()
+    pre = R.preprocess(R.params(g), 0, 0.0, cam, cfg)
+    keys, vals, ranges, tx, ty = R.tile_lists(pre, cam, cfg)
+    assert keys.size == int(pre["tiles_touched"].sum())
+    assert np.all(np.diff(keys.astype(np.float64)) >= 0) and np.all(keys[1:] >= keys[:-1])
+    # ranges partition [0, P)
+    nz = ranges[ranges[:, 1] > ranges[:, 0]]
+    assert nz[0, 0] == 0 and nz[-1, 1] == keys.size
+    assert np.all(nz[1:, 0] == nz[:-1, 1])
+    # brute force per tile: Gaussians whose rectangle covers the tile, by (depth, index)
+    t0, t1, u0, u1 = pre["tile_rect"]
+    depth = pre["depth"].detach().numpy().astype(np.float32)
+    for tile in range(tx * ty):
+        x, y = tile % tx, tile // tx
+        cover = np.nonzero((t0 <= x) & (x <= t1) & (u0 <= y) & (y <= u1)
+                           & (pre["tiles_touched"] > 0))[0]
+        want = cover[np.lexsort((cover, depth[cover]))]
+        s, e = ranges[tile]
+        assert np.array_equal(vals[s:e], want)
+
+
+def test_single_gaussian_renders_its_analytic_falloff():
+    W = H = 48
+    z0, sx, sy, o = 3.0, 0.05, 0.09, 0.8
+    cam = synth.camera((0.0, 0.0, -z0), W, H)
+    u_col = np.array([0.2, 0.7, 0.4])
+    g = {"means": np.zeros((1, 3)), "quats": np.array([[1.0, 0, 0, 0]]),
+         "s_opt": np.log([[sx, sy, 0.07]]), "opacity_logit": np.array([math.log(o / (1 - o))]),
+         "sh": ((u_col - 0.5) / synth.Y00)[None, None, :]}
+    for dil in (0.3, 0.0):
+        cfg = R.Config(dilation=dil)
+        img, tf, last = R.render(g, 0, 0.0, cam, cfg)
+        f = cam["fx"]
+        vx, vy = (f * sx / z0) ** 2 + dil, (f * sy / z0) ** 2 + dil
+        xs = np.arange(W) + 0.5 - W / 2
+        ys = np.arange(H) + 0.5 - H / 2
+        q = xs[None, :] ** 2 / vx + ys[:, None] ** 2 / vy
+        a = np.minimum(0.99, o * np.exp(-0.5 * q))
+        a = np.where(a >= 1 / 255, a, 0.0)
+        np.testing.assert_allclose(img, u_col[:, None, None] * a[None], atol=1e-12)
+        np.testing.assert_allclose(tf, 1 - a, atol=1e-12)
+        assert np.array_equal(last, (a > 0).astype(int))
+
+
+def _stack(n, opac, W=16, H=16, same_depth=False, colours=None):
+    cam = synth.camera((0.0, 0.0, -3.0), W, H)
+    z = np.zeros(n) if same_depth else np.linspace(0, 0.5, n)
+    cols = np.full((n, 3), 1.0) if colours is None else colours
+    return {"means": np.stack([np.zeros(n), np.zeros(n), z], 1),
+            "quats": np.tile([1.0, 0, 0, 0], (n, 1)), "s_opt": np.full((n, 3), math.log(2.0)),
+            "opacity_logit": np.full(n, math.log(opac / (1 - opac))),
+            "sh": ((cols - 0.5) / synth.Y00)[:, None, :]}, cam
+
+
+def test_early_stop_closed_form():
+    # six broad Gaussians on the optical axis with opacity 0.95: alpha ~ 0.947 at the pixel
+    # next to the axis; after three T ~ 1.5e-4 and the fourth would take T below 1e-4, so
+    # three are blended and T_final is the closed-form product of the first three
+    g, cam = _stack(6, 0.95)
+    img, tf, last = R.render(g, 0, 0.0, cam, R.Config())
+    f = cam["fx"]
+    z = 3.0 + np.linspace(0, 0.5, 6)
+    var = (f * 2.0 / z) ** 2 + 0.3
+    a = 0.95 * np.exp(-0.5 * (0.5 ** 2 + 0.5 ** 2) / var)
+    assert np.prod(1 - a[:4]) < 1e-4 <= np.prod(1 - a[:3])
+    assert last[8, 8] == 3
+    assert tf[8, 8] == pytest.approx(np.prod(1 - a[:3]), rel=1e-12)
+    assert img[0, 8, 8] == pytest.approx(1 - np.prod(1 - a[:3]), rel=1e-12)
+    assert tf.min() >= 1e-4
+
+
+def test_alpha_clamp_and_coverage_identity():
+    # all colours 1 and black background: C = sum_i alpha_i T_i = 1 - T_final exactly
+    g, cam = _scene(5, 300, 48, 48, s_mean=-2.0)
+    g["sh"][:, 0, :] = 0.5 / synth.Y00
+    img, tf, _ = R.render(g, 0, 0.0, cam, R.Config())
+    np.testing.assert_allclose(img, np.broadcast_to(1 - tf, img.shape), atol=1e-12)
+    assert np.all(tf >= 1e-4) and np.all(tf <= 1)
+    # a single fully opaque Gaussian: alpha clamps at 0.99
+    g1, cam1 = _stack(1, 0.999999)
+    img1, tf1, _ = R.render(g1, 0, 0.0, cam1, R.Config())
+    assert tf1[8, 8] == pytest.approx(0.01, rel=1e-12)
+    assert img1[0, 8, 8] == pytest.approx(0.99, rel=1e-12)
+
+
+def test_equal_depth_ties_break_by_index():
+    cols = np.array([[1.0, 0, 0], [0, 0, 1.0]])
+    g, cam = _stack(2, 0.6, same_depth=True, colours=cols)
+    img, _, _ = R.render(g, 0, 0.0, cam, R.Config())
+    g2 = {k: v[::-1].copy() for k, v in g.items()}
+    img2, _, _ = R.render(g2, 0, 0.0, cam, R.Config())
+    # the lower index is in front: red in front for g, blue in front for g2
+    assert img[0, 8, 8] > img[2, 8, 8]
+    assert img2[2, 8, 8] > img2[0, 8, 8]
+
+
+def test_background():
+    g, cam = _scene(6, 50, 32, 32)
+    cfg = R.Config(bg=(0.25, 0.5, 1.0))
+    img, tf, _ = R.render(g, 0, 0.0, cam, cfg)
+    img0, tf0, _ = R.render(g, 0, 0.0, cam, R.Config())
+    np.testing.assert_allclose(img, img0 + np.array(cfg.bg)[:, None, None] * tf0[None], atol=1e-12)
+
+
+def test_empty_scene():
+    g, cam = _scene(7, 5, 32, 32)
+    g["means"][:, 2] = -10.0           # behind the camera
+    img, tf, last = R.render(g, 0, 0.0, cam, R.Config(bg=(0.1, 0.2, 0.3)))
+    assert np.all(tf == 1) and np.all(last == 0)
+    np.testing.assert_allclose(img[:, 3, 3], [0.1, 0.2, 0.3])
+
+
+def _fd_scene(seed):
+    rng = np.random.default_rng(seed)
+    g = synth.gaussian_set(seed, 12, k=3, radius=0.6, sh_degree=3, s_mean=-2.3, s_std=0.3)
+    o = rng.uniform(0.05, 0.6, 12)
+    g["opacity_logit"] = np.log(o / (1 - o)).astype(np.float32)
+    cam = synth.camera((0.2, 0.1, -2.5), 32, 32)
+    return g, cam
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gradient_matches_central_finite_differences(seed):
+    g, cam = _fd_scene(seed)
+    cfg = R.Config(tile_w=8, tile_h=8)
+    s_min = 0.02
+    rng = np.random.default_rng(100 + seed)
+    w = rng.normal(size=(3, 32, 32))
+    _, _, _, grads = R.forward_backward(g, 3, s_min, cam, cfg, w)
+
+    def loss_and_state(gg):
+        p = R.params(gg)
+        with torch.no_grad():
+            pre = R.preprocess(p, 3, s_min, cam, cfg)
+            img, _, _ = R.render_tiled(pre, cam, cfg)
+            return float((img * w).sum()), R.discrete_state(pre, cam, cfg)
+
+    f0, st0 = loss_and_state(g)
+    checked = skipped = 0
+    for name in ("means", "quats", "s_opt", "opacity_logit", "sh"):
+        base = np.asarray(g[name], dtype=np.float64)
+        flat = base.reshape(-1)
+        picks = rng.choice(flat.size, size=min(flat.size, 24), replace=False)
+        for j in picks:
+            h = 1e-5 * max(1.0, abs(flat[j]))
+            vals = []
+            same = True
+            for sgn in (1, -1):
+                pert = flat.copy()
+                pert[j] += sgn * h
+                gg = dict(g)
+                gg[name] = pert.reshape(base.shape)
+                f, st = loss_and_state(gg)
+                same &= st == st0
+                vals.append(f)
+            if not same:
+                skipped += 1
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = grads[name].reshape(-1)[j]
+            scale = np.abs(grads[name]).max() + 1e-30
+            assert abs(fd - an) <= 1e-6 * abs(an) + 1e-7 * scale, (name, j, fd, an)
+            checked += 1
+    print("fd checked", checked, "skipped", skipped)
+    assert checked >= 80 and skipped <= checked // 4, (checked, skipped)
