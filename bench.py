@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the FLoD splatting path on GB300.
+
+Workload (the headline configuration): the finest level of the 5-level scene -- 3,000,000
+Gaussians (64 clusters, radius 20, SH degree 3, level-by-level initialised with Eq. 5 from
+levels 1..4), one 1920x1080 pinhole camera at distance 40, upstream image gradient
+N(0, 1e-3). A step is one training iteration of that level: preprocess, binning + radix
+sort, forward blending, blending backward, preprocess backward (gradients to means, s_opt,
+quaternions, opacity logits and SH). The forward-only frame rate is reported beside it.
+
+``value`` = fwd+bwd iterations per second over all ranks (inputs resident in HBM; the 708 MB
+parameter set and the per-step buffers exceed the 129 MB L2, so no flush is needed).
+``e2e`` = the same through the Python API with the step's input (the upstream image
+gradient) copied from pinned host memory and the rendered image read back, every step.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same step.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under torchrun each rank
+runs an independent replica (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s fwd & fwd+bwd it/s (3M Gaussians), batched vs per-view"
+WORKLOAD = "FLoD 5-level scene, level 5 (3M Gaussians, SH3), 1920x1080, fwd+bwd per level"
+# peak of plain float32 ALU work: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz
+ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# algorithmic float32 work per (pixel, Gaussian) evaluation, FMA = 2 (derivation in the design doc)
+FLOP_FWD_EVAL = 25
+FLOP_BWD_EVAL = 80
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="flod", choices=["flod", "reference"])
+    ap.add_argument("--small", action="store_true", help="300k-Gaussian level (smoke runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------------------
+
+def level_counts(small: bool):
+    from paper_2408_12894_gb300 import synth
+    return (2_000, 8_000, 30_000, 100_000, 300_000) if small else synth.LEVEL_COUNTS
+
+
+def make_level(small: bool):
+    """Numpy arrays of the finest level (s_opt as drawn: Eq. 5 is applied on the device)."""
+    from paper_2408_12894_gb300 import synth
+    levels = synth.level_scene(counts=level_counts(small))
+    return levels[-1][0]
+
+
+def clock_sampler(dev_index: int):
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
+                              "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+    rows = []
+
+    def pump():
+        for line in p.stdout:
+            rows.append([x.strip() for x in line.split(",")])
+
+    th = threading.Thread(target=pump, daemon=True)
+    th.start()
+    return p, th, rows
+
+
+def clock_summary(s):
+    if s is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p, th, rows = s
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    th.join(timeout=2)
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        try:
+            sm.append(float(r[0]))
+            mx.append(float(r[1]))
+        except (ValueError, IndexError):
+            continue
+        for n, v in zip(names, r[3:7]):
+            if v.strip().lower() == "active":
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ---------------------------------------------------------------------------------------
+
+class OracleStep:
+    """Times the FP64 oracle on a bounded sample of one training step and scales it to the
+    full step: preprocess forward+backward and binning on a slice of the Gaussians (scaled by
+    N / slice) plus blending forward+backward on a sample of tiles (scaled by tiles / sample).
+    The tile lists come from an untimed FP64 preprocess of the whole level."""
+
+    def __init__(self, g, cam, s_min, slice_n=40_000, tiles=6, seed=0):
+        import numpy as np
+        import torch
+        from oracle import raster as R
+        self.R, self.np, self.torch = R, np, torch
+        self.g, self.cam, self.s_min = g, cam, s_min
+        self.cfg = R.Config()
+        self.n = g["means"].shape[0]
+        self.slice_n = min(slice_n, self.n)
+        with torch.no_grad():
+            pre = R.preprocess(R.params(g), 3, s_min, cam, self.cfg)
+        self.pre = {k: pre[k] for k in ("mean2d", "conic", "opacity", "rgb")}
+        self.lists = R.tile_lists(pre, cam, self.cfg)
+        ranges = self.lists[2]
+        counts = ranges[:, 1] - ranges[:, 0]
+        rng = np.random.default_rng(seed)
+        nz = np.nonzero(counts)[0]
+        self.sample = rng.choice(nz, size=min(tiles, nz.size), replace=False)
+        self.n_tiles = ranges.shape[0]
+        self.grad_out = rng.normal(0, 1e-3, (3, cam["height"], cam["width"]))
+
+    def step_seconds(self) -> float:
+        R, np, torch = self.R, self.np, self.torch
+        sub = {k: (v[:self.slice_n] if k != "sh_degree" else v) for k, v in self.g.items()}
+        t0 = time.perf_counter()
+        p = R.params(sub, requires_grad=True)
+        pre = R.preprocess(p, 3, self.s_min, self.cam, self.cfg)
+        k, v = R.bin_pairs(pre["tile_rect"], pre["tiles_touched"], pre["depth"].detach().numpy(),
+                           self.lists[3], self.n_tiles)
+        R.sort_pairs(k, v)
+        outs = [pre[n] for n in ("mean2d", "conic", "opacity", "rgb")]
+        torch.autograd.backward(outs, [torch.ones_like(o) for o in outs])
+        t_slice = time.perf_counter() - t0
+        keys, vals, ranges, tx, ty = self.lists
+        leaves = {n: self.pre[n].detach().clone().requires_grad_(True) for n in self.pre}
+        bg = torch.zeros(3, dtype=torch.float64)
+        t0 = time.perf_counter()
+        for tile in self.sample:
+            s, e = ranges[tile]
+            gi = torch.as_tensor(vals[s:e].astype(np.int64))
+            x0, y0 = (tile % tx) * 16, (tile // tx) * 16
+            xs = np.arange(x0, min(x0 + 16, self.cam["width"]))
+            ys = np.arange(y0, min(y0 + 16, self.cam["height"]))
+            gx, gy = np.meshgrid(xs, ys)
+            pix = torch.as_tensor(np.stack([gx.ravel() + 0.5, gy.ravel() + 0.5], 1))
+            a = R.alpha_raw(pix, leaves["mean2d"][gi], leaves["conic"][gi], leaves["opacity"][gi])
+            col, _, _ = R.blend(a, leaves["rgb"][gi], bg)
+            go = torch.as_tensor(self.grad_out[:, y0:y0 + len(ys), x0:x0 + len(xs)].reshape(3, -1).T)
+            (col * go).sum().backward()
+        t_tiles = time.perf_counter() - t0
+        return t_slice * self.n / self.slice_n + t_tiles * self.n_tiles / max(len(self.sample), 1)
+
+    def describe(self) -> str:
+        return (f"preprocess fwd+bwd and binning of {self.slice_n} of {self.n} Gaussians "
+                f"(x{self.n / self.slice_n:.0f}) + blend fwd+bwd of {len(self.sample)} of "
+                f"{self.n_tiles} 16x16 tiles (x{self.n_tiles / max(len(self.sample), 1):.0f})")
+
+
+def run_reference(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    from paper_2408_12894_gb300 import synth
+    g = make_level(a.small)
+    g["s_opt"] = adjust_chain_numpy(g["s_opt"], level_counts(a.small))
+    cam = synth.level_camera()
+    ost = OracleStep(g, cam, synth.LEVEL_SMIN[-1], slice_n=20_000, tiles=3)
+    for _ in range(a.warmup):
+        ost.step_seconds()
+    secs = [ost.step_seconds() for _ in range(a.steps)]
+    mean = sum(secs) / len(secs)
+    v = 1.0 / mean
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "it/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * mean,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "gaussians": g["means"].shape[0],
+                                            "resolution": "1920x1080", "sh_degree": 3},
+            "cpu_baseline": {"value": v, "unit": "it/s", "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": ost.describe()},
+            "e2e": {"value": v, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def adjust_chain_numpy(s_opt, counts):
+    """Eq. 5 chain for the oracle arm (FP64): Gaussians present at level l are moved from
+    level l's constraint to level l+1's, l = 1..4."""
+    import numpy as np
+    import torch
+    from oracle import gaussians as OG
+    from paper_2408_12894_gb300 import synth
+    s = torch.as_tensor(s_opt.astype(np.float64))
+    for l in range(4):
+        s[:counts[l]] = OG.adjust_scale(s[:counts[l]], synth.LEVEL_SMIN[l], synth.LEVEL_SMIN[l + 1])
+    return s.numpy().astype(np.float32)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+
+def run_flod(a):
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2408_12894_gb300 import _build, flod, synth
+    _build.build()
+    counts = level_counts(a.small)
+    g = make_level(a.small)
+    gs = flod.GaussianSet.from_numpy(g, synth.LEVEL_SMIN[-1])
+    for l in range(4):   # level-by-level initialisation (Eq. 5), on the device
+        flod.flod_adjust_scale(gs.s_opt[:counts[l]], synth.LEVEL_SMIN[l], synth.LEVEL_SMIN[l + 1])
+    cam = synth.level_camera()
+    view = flod.view_struct(cam)
+    rast = flod.Rasterizer([gs], [view])
+    rgb, T, nc = rast.forward()                    # sizes the pair capacity once
+    torch.cuda.synchronize()
+    pairs = int(rast.pair_count.item())
+    rast.pair_capacity = int(pairs * 1.2) + 4096
+    rast._alloc()
+    H, W = cam["height"], cam["width"]
+    dL_host = torch.as_tensor(synth.upstream_gradient(11, [cam])).pin_memory()
+    dL = dL_host.to("cuda")
+    grads = [[torch.zeros_like(getattr(gs, f)) for f in flod.GaussianSet.FIELDS]]
+    grads_c = flod.grads_struct(grads)
+    st = torch.cuda.current_stream()
+
+    def fwd():
+        rast.preprocess()
+        rast.bin_sort()
+        rast.render_fwd(rgb, T, nc)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(st)
+        rast.preprocess()
+        if ev:
+            ev[1].record(st)
+        rast.bin_sort()
+        if ev:
+            ev[2].record(st)
+        rast.render_fwd(rgb, T, nc)
+        if ev:
+            ev[3].record(st)
+        for t in grads[0]:
+            t.zero_()
+        if ev:
+            ev[4].record(st)
+        rast.blend_bwd(dL, T, nc)
+        if ev:
+            ev[5].record(st)
+        rast.preprocess_bwd(grads_c)
+        if ev:
+            ev[6].record(st)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert flod.flod_read_status(rast.ws) == 0, "device status error"
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- forward frames
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.steps):
+        fwd()
+    e1.record(st)
+    barrier()
+    fwd_ms = e0.elapsed_time(e1) / a.steps
+
+    # ---- fwd+bwd training steps (the headline), per-stage events
+    clk = clock_sampler(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(a.steps)]
+    ev_before = rast.eval_counts()
+    barrier()
+    t_wall = time.perf_counter()
+    for i in range(a.steps):
+        step(evs[i])
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = clock_summary(clk)
+    ev_after = rast.eval_counts()
+    step_ms = [evs[i][0].elapsed_time(evs[i][6]) for i in range(a.steps)]
+    total_ms = evs[0][0].elapsed_time(evs[-1][6])
+    names = ["preprocess", "bin_sort", "render_fwd", "zero_grads", "blend_bwd", "preprocess_bwd"]
+    stage_ms = {n: sum(evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(a.steps)) / a.steps
+                for j, n in enumerate(names)}
+    ms = total_ms / a.steps
+    if dist is not None:
+        t = torch.tensor([ms, fwd_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, fwd_ms = t.tolist()
+
+    # ---- end to end: upstream gradient in from pinned host memory, image back, every step
+    img_host = torch.empty(3 * H * W, dtype=torch.float32).pin_memory()
+    barrier()
+    e2e0, e2e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e0.record(st)
+    for _ in range(a.steps):
+        dL.copy_(dL_host, non_blocking=True)
+        step()
+        img_host.copy_(rgb, non_blocking=True)
+    e2e1.record(st)
+    barrier()
+    e2e_ms = e2e0.elapsed_time(e2e1) / a.steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+
+    fwd_evals = (ev_after[0] - ev_before[0]) / a.steps
+    bwd_evals = (ev_after[1] - ev_before[1]) / a.steps
+    kernels = {"render_fwd": (stage_ms["render_fwd"], fwd_evals * FLOP_FWD_EVAL),
+               "blend_bwd": (stage_ms["blend_bwd"], bwd_evals * FLOP_BWD_EVAL)}
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    d_ms, d_flop = kernels[dom]
+    achieved = d_flop / (d_ms * 1e-3) / 1e12
+    n_tiles = int(rast.layout.tiles)
+    n_passes = (32 + max(1, math.ceil(math.log2(max(n_tiles, 2)))) + 7) // 8
+    # preprocess 1; bin_sort: block sums, scan, emit, histogram, plan, n_passes, ranges;
+    # render_fwd 1; blend_bwd 1; preprocess_bwd 1 (memsets and torch's zero_ not counted)
+    launches_per_step = 1 + (5 + n_passes + 1) + 1 + 1 + 1
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * 1e3 / ms, "unit": "it/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": int(gs.n), "resolution": f"{W}x{H}",
+                       "sh_degree": 3, "tile": "16x16", "pairs_per_step": pairs,
+                       "l2": "inputs larger than L2 (708 MB parameters, no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "fwd_fps": world * 1e3 / fwd_ms, "fwd_ms": fwd_ms,
+            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "step_ms_median": statistics.median(step_ms),
+            "wall_ms_per_step": 1e3 * t_wall / a.steps,
+            "evals_per_step": {"fwd": fwd_evals, "bwd": bwd_evals},
+            "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved,
+                         "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / ALU_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+            "e2e": {"value": world * 1e3 / e2e_ms, "unit": "it/s",
+                    "h2d_bytes_per_step": int(dL.numel() * 4),
+                    "d2h_bytes_per_step": int(rgb.numel() * 4)},
+            "gpu_launches": launches_per_step * a.steps,
+            "clocks": clocks,
+        }
+        if not a.no_cpu_baseline and world == 1:
+            try:
+                g_np = dict(g)
+                g_np["s_opt"] = gs.s_opt.cpu().numpy()
+                ost = OracleStep(g_np, cam, synth.LEVEL_SMIN[-1])
+                sec = ost.step_seconds()
+                line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "it/s",
+                                        "cores": torch.get_num_threads(), "kind": "oracle",
+                                        "sample": ost.describe()}
+            except Exception as ex:   # report, never hide
+                line["cpu_baseline"] = {"value": None, "unit": "it/s", "kind": "oracle",
+                                        "error": repr(ex)}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_flod(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * flod.h -- C ABI of the GB300 (sm_103a) splatting path of FLoD
+ * ("FLoD: Integrating Flexible Level of Detail into 3D Gaussian Splatting for
+ * Customizable Rendering", arXiv 2408.12894).
+ *
+ * The path renders and differentiates one level of a multi-level 3D Gaussian set, or a
+ * distance-selected mix of levels, through a tile-based rasterizer:
+ *
+ *   flod_select_levels   Eq. 6 / Eq. 7 (Sec. 5.2): per-Gaussian level band by distance
+ *   flod_preprocess      Eq. 4 (Sec. 4.1) scale constraint, Eq. 1 (Sec. 3) covariance,
+ *                        projection to 2D (Eq. 2, Sec. 3), SH colour, extent, tile rect
+ *   flod_bin_sort        (tile, depth) keys and their stable radix sort; tile ranges
+ *   flod_render_fwd      depth-ordered alpha blending (Sec. 3, after Eq. 2)
+ *   flod_render_bwd      gradient of the above to means, s_opt, quaternions, opacity
+ *                        logits and SH (the Backpropagation step of Algorithm 1)
+ *   flod_adjust_scale    Eq. 5 (Sec. 4.2, AdjustScale of Algorithm 1)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All array pointers are DEVICE pointers of the current CUDA device, allocated by the
+ *   caller; the library never allocates device memory and keeps no state between calls
+ *   except a per-device cache of occupancy figures.
+ * - Calls enqueue work on `stream` and return without waiting. Argument checks are done on
+ *   the host before anything is enqueued; on a check failure nothing is enqueued and the
+ *   status says why. Errors found on the device (pair capacity exceeded, a bounded spin
+ *   that ran out) set bits of the workspace status word, read with flod_read_status().
+ *   No call aborts, traps or prints.
+ * - Cameras: world->camera [R|t] row-major 3x4 (OpenCV axes: x right, y down, z forward),
+ *   pinhole u = fx*x/z + cx, v = fy*y/z + cy; pixel (i, j) samples at (i+0.5, j+0.5).
+ * - Gaussians are structure-of-arrays float32: means [n,3], quats [n,4] (w,x,y,z, any
+ *   nonzero length), s_opt [n,3] (the learnable scale of Eq. 4), opacity_logit [n]
+ *   (opacity = sigmoid), sh [n,(deg+1)^2,3] (real SH, Condon-Shortley phase, index
+ *   l*l+l+m; colour = max(0, sum + 0.5)).
+ * - A "view" is one camera rendering one source of Gaussians: a whole set, or a selection
+ *   list from flod_select_levels. Several views in one call form a batch: every stage runs
+ *   once over all views (one launch per kernel) and the per-view outputs are concatenated.
+ */
+#ifndef FLOD_H
+#define FLOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *flod_stream; /* a cudaStream_t; NULL = the legacy stream */
+
+typedef enum {
+  FLOD_OK = 0,
+  FLOD_ERR_INVALID_ARG = 1, /* a pointer, size or enum out of range; nothing enqueued */
+  FLOD_ERR_CAPACITY = 2,    /* more (Gaussian, tile) pairs than pair_capacity */
+  FLOD_ERR_TIMEOUT = 3,     /* a bounded device-side wait ran out */
+  FLOD_ERR_CUDA = 4,        /* a CUDA runtime call failed (launch, memset) */
+  FLOD_ERR_UNSUPPORTED = 5, /* e.g. no sm_103a device */
+  FLOD_ERR_WORKSPACE = 6    /* workspace smaller than flod_workspace_size() */
+} flod_status;
+
+/* Device status bits (flod_read_status). */
+#define FLOD_DEV_CAPACITY 0x1u /* pairs exceeded pair_capacity: pairs beyond it dropped */
+#define FLOD_DEV_TIMEOUT 0x2u  /* radix-sort look-back wait gave up */
+
+#define FLOD_MAX_VIEWS 128
+#define FLOD_MAX_SETS 16
+#define FLOD_SEL_SHIFT 28 /* selection entry = (set << FLOD_SEL_SHIFT) | index */
+#define FLOD_MAX_PAIRS ((1ull << 30) - 1)
+
+typedef struct {
+  float viewmat[12]; /* world -> camera, row-major [R | t] */
+  float fx, fy, cx, cy;
+  int width, height;
+  float cam_pos[3]; /* camera centre in world space (SH view direction) */
+} flod_camera;
+
+typedef struct {
+  const float *means;
+  const float *quats;
+  const float *s_opt;
+  const float *opacity_logit;
+  const float *sh;
+  int n;         /* Gaussians in the set, < 2^28 */
+  int sh_degree; /* 0..3 */
+  float s_min;   /* the level's 3D scale constraint s_min^(l) of Eq. 3/4 */
+} flod_gaussians;
+
+typedef struct {
+  flod_camera cam;
+  int set;                    /* index into the `sets` array when sel == NULL */
+  const uint32_t *sel;        /* optional selection entries (set << 28) | index */
+  const uint32_t *sel_count;  /* device count of valid entries of sel (with sel) */
+  uint32_t sel_capacity;      /* entries reserved for sel (the units of this view) */
+} flod_view;
+
+typedef struct {
+  int tile_w, tile_h; /* 8x8, 16x16 or 32x8 pixels */
+  int batch;          /* Gaussians staged per shared-memory batch: 32, 64, 128 or 256 */
+  float dilation;     /* px^2 added to the 2D covariance diagonal (default 0.3) */
+  float z_near;       /* cull t_z <= z_near (default 0.2) */
+  float bg[3];        /* background colour (default black) */
+  int extent_rule;    /* 0: opacity-aware exact support (default); 1: 3 sigma */
+  int persistent;     /* render with persistent CTAs over a largest-first tile queue */
+} flod_raster_config;
+
+/* Gradient outputs of one set, same shapes as the parameters; accumulated with +=. */
+typedef struct {
+  float *means, *quats, *s_opt, *opacity_logit, *sh;
+} flod_grads;
+
+/* Byte offsets of the workspace's regions (see flod_workspace_layout). */
+typedef struct {
+  size_t total;         /* bytes required */
+  size_t status;        /* uint32 status bits */
+  size_t pair_count;    /* uint64 pairs emitted by the last flod_bin_sort */
+  size_t plan;          /* uint32[64] radix-sort plan; plan[63] = buffer index of the result;
+                           uint64 at plan[48] / plan[50]: running count of (pixel, Gaussian)
+                           evaluations of the blending forward / backward kernels */
+  size_t xy;            /* float2 [units] projected mean (u, v) */
+  size_t depth;         /* float [units] view-space z */
+  size_t conic_o;       /* float4 [units] (a, b, c, opacity), q = a dx^2 + 2b dx dy + c dy^2 */
+  size_t rgb;           /* float4 [units] (r, g, b, 0) */
+  size_t radius;        /* float [units] extent radius in pixels */
+  size_t tiles_touched; /* uint32 [units], 0 when culled */
+  size_t block_sums;    /* uint64 [units/1024 + 1] exclusive pair offsets per 1024 units */
+  size_t keys[2];       /* uint64 [pair_capacity] x 2 (emission buffer is keys[0]) */
+  size_t vals[2];       /* uint32 [pair_capacity] x 2 */
+  size_t hist;          /* radix-sort digit histograms */
+  size_t lookback;      /* radix-sort decoupled look-back tables */
+  size_t ranges;        /* uint32x2 [tiles] [start, end) in the sorted pair list */
+  size_t grad2d;        /* float4 [units][3]: (du, dv, dopacity, 0), (da, db, dc, 0), (dr, dg, db, 0) */
+  size_t queue;         /* uint32 [tiles + 64] persistent render work order */
+  uint64_t units;       /* total units (each view's capacity rounded up to 1024) */
+  uint64_t tiles;       /* total tiles over all views */
+  uint64_t pixels;      /* total pixels over all views */
+  uint64_t pair_capacity;
+} flod_ws_layout;
+
+/* Fill *cfg with the defaults: 16x16 tiles, batch 256, dilation 0.3, z_near 0.2, black
+ * background, opacity-aware extent, one CTA per tile. */
+void flod_default_config(flod_raster_config *cfg);
+
+/* Workspace bytes for a batch of views; the pair capacity bounds the (Gaussian, tile)
+ * pairs of all views together (<= FLOD_MAX_PAIRS). Returns 0 on invalid arguments. */
+size_t flod_workspace_size(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                           int n_views, uint64_t pair_capacity, const flod_raster_config *cfg);
+
+/* Offsets of every workspace region, plus the per-view unit, tile and pixel offsets
+ * (arrays of n_views + 1 entries each, may be NULL). Pure host computation.
+ * The stage calls below all take the same (sets, views, cfg, pair_capacity) description,
+ * which must not change between the calls of one frame: the workspace layout is a function
+ * of it alone, and ws must be 256-byte aligned and at least flod_workspace_size() bytes. */
+flod_status flod_workspace_layout(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                                  int n_views, uint64_t pair_capacity,
+                                  const flod_raster_config *cfg, flod_ws_layout *out,
+                                  uint64_t *unit_offset, uint64_t *tile_offset,
+                                  uint64_t *pixel_offset);
+
+/* Eq. 4 + Eq. 1 + Eq. 2 projection + SH colour per (view, Gaussian): fills the unit
+ * arrays of the workspace (xy, depth, conic_o, rgb, radius, tiles_touched) and clears the
+ * status word. A unit is culled (tiles_touched = 0) when t_z <= z_near, when its 2D
+ * covariance is not positive definite, when opacity < 1/255 (opacity-aware extent) or when
+ * its rectangle misses the image. */
+flod_status flod_preprocess(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                            int n_views, const flod_raster_config *cfg, void *ws,
+                            size_t ws_bytes, uint64_t pair_capacity, flod_stream stream);
+
+/* (tile, depth) binning and sort: key = (global tile << 32) | float bits of t_z for every
+ * (unit, covered tile), emitted in unit order; a stable LSD radix sort (onesweep, decoupled
+ * look-back) orders them, so ties in depth keep unit order; then the [start, end) range of
+ * every tile. Writes the pair total to *d_pair_count (device, may be NULL) and to the
+ * workspace. Pairs beyond pair_capacity are dropped and FLOD_DEV_CAPACITY is set. */
+flod_status flod_bin_sort(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                          int n_views, const flod_raster_config *cfg, void *ws, size_t ws_bytes,
+                          uint64_t pair_capacity, uint64_t *d_pair_count, flod_stream stream);
+
+/* Front-to-back blending per pixel of every view. Outputs (device, planar per view, views
+ * concatenated at their pixel offsets): out_rgb [3][H][W] per view, out_T [H][W] final
+ * transmittance, out_ncontrib [H][W] 1-based position of the last blended Gaussian in the
+ * tile's sorted list. alpha = min(0.99, o exp(-q/2)); alpha < 1/255 is skipped; blending
+ * stops before the Gaussian that would take T below 1e-4. out_T and out_ncontrib are
+ * needed by flod_render_bwd. */
+flod_status flod_render_fwd(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                            int n_views, const flod_raster_config *cfg, void *ws, size_t ws_bytes,
+                            uint64_t pair_capacity, float *out_rgb, float *out_T,
+                            uint32_t *out_ncontrib, flod_stream stream);
+
+/* Gradient of L = sum(dL_drgb * rgb) through blending, projection, SH, Eq. 1 and Eq. 4,
+ * accumulated (+=) into grads[set] for every set that a view renders (grads has n_sets
+ * entries; a NULL member skips that parameter). Re-walks every pixel back to front from
+ * out_T / out_ncontrib of the forward; the workspace must still hold the forward's state.
+ * Gradients go through non-atomic read-modify-write when a set is rendered by one view
+ * only, else through atomics; a selection list must not repeat an entry. */
+flod_status flod_render_bwd(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                            int n_views, const flod_raster_config *cfg, void *ws,
+                            size_t ws_bytes, uint64_t pair_capacity, const float *dL_drgb,
+                            const float *fwd_T,
+                            const uint32_t *fwd_ncontrib, const flod_grads *grads,
+                            flod_stream stream);
+
+/* The two halves of flod_render_bwd, for callers that time or use them separately.
+ * flod_blend_bwd clears the per-unit 2D gradient accumulators of the workspace and runs the
+ * blending backward (per-unit dL/d(u, v, conic, opacity, rgb), see flod_ws_layout.grad2d);
+ * flod_preprocess_bwd chains them to the parameters (+= into grads, as flod_render_bwd). */
+flod_status flod_blend_bwd(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                           int n_views, const flod_raster_config *cfg, void *ws, size_t ws_bytes,
+                           uint64_t pair_capacity, const float *dL_drgb, const float *fwd_T,
+                           const uint32_t *fwd_ncontrib, flod_stream stream);
+flod_status flod_preprocess_bwd(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                                int n_views, const flod_raster_config *cfg, void *ws,
+                                size_t ws_bytes, uint64_t pair_capacity, const flod_grads *grads,
+                                flod_stream stream);
+
+/* Eq. 6 with the thresholds of Eq. 7. levels[0..n_levels-1] are given coarse to fine.
+ * d_thresh (host array of n_levels-1 floats, descending) gives d_proj of each level but the
+ * last; if NULL, d_proj = s_min * focal / gamma (Eq. 7). The last level's band ends at 0 and
+ * the first level's at infinity. A Gaussian of level k is kept iff
+ * d_thresh[k-1] > d >= d_thresh[k], d = ||mean - origin|| in float32. Writes the kept
+ * entries (k << 28) | i to out_sel in (level, index) order and their number to *d_count
+ * (device). scratch: device bytes of flod_select_scratch_size(). */
+size_t flod_select_scratch_size(const flod_gaussians *levels, int n_levels);
+flod_status flod_select_levels(const flod_gaussians *levels, int n_levels, const float *d_thresh,
+                               float gamma, float focal, const float origin[3],
+                               uint32_t *out_sel, uint32_t sel_capacity, uint32_t *d_count,
+                               void *scratch, size_t scratch_bytes, flod_stream stream);
+
+/* Eq. 5: s_opt <- log(exp(s_opt) + s_min_cur - s_min_next) in place, so that the scale of
+ * Eq. 4 at the next level equals the current one. Requires s_min_cur >= s_min_next. */
+flod_status flod_adjust_scale(float *s_opt, int64_t n, float s_min_cur, float s_min_next,
+                              flod_stream stream);
+
+/* Copies the workspace status bits to *out (waits for `stream`). */
+flod_status flod_read_status(const void *ws, uint32_t *out, flod_stream stream);
+
+/* Human-readable name of a status code (static string). */
+const char *flod_status_string(flod_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLOD_H */

@@ -1,0 +1,511 @@
+// C ABI of the splatting path: argument checks, workspace layout, per-call parameter
+// tables and kernel launches. See include/flod.h for the contract of every entry point.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace flod {
+uint32_t select_blocks(const int* ns, int n_levels);
+}
+
+using namespace flod;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+struct DevInfo {
+  bool init = false;
+  flod_status st = FLOD_OK;
+  int sms = 0;
+  int res_sort = 0;    // resident CTAs of the radix-sort pass kernel
+  int res_small = 0;   // grid of the grid-stride helper kernels
+};
+DevInfo g_dev[64];
+std::mutex g_mu;
+
+flod_status device_info(DevInfo** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FLOD_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevInfo& d = g_dev[dev];
+  if (!d.init) {
+    d.init = true;
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (major != 10 || minor != 3) {
+      d.st = FLOD_ERR_UNSUPPORTED;
+    } else if (sort_kernel_prepare() != cudaSuccess) {
+      d.st = FLOD_ERR_CUDA;
+    } else {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_kernel_ptr(), kSortThreads,
+                                                        sort_kernel_smem_bytes()) != cudaSuccess ||
+          per_sm < 1)
+        per_sm = 1;
+      d.res_sort = per_sm * d.sms;
+      d.res_small = 8 * d.sms;
+      d.st = FLOD_OK;
+    }
+  }
+  *out = &d;
+  return d.st;
+}
+
+bool cfg_ok(const flod_raster_config* c) {
+  if (!c) return false;
+  const bool shape = (c->tile_w == 8 && c->tile_h == 8) || (c->tile_w == 16 && c->tile_h == 16) ||
+                     (c->tile_w == 32 && c->tile_h == 8);
+  const bool batch = c->batch == 32 || c->batch == 64 || c->batch == 128 || c->batch == 256;
+  return shape && batch && c->dilation >= 0.f && c->z_near > 0.f &&
+         (c->extent_rule == 0 || c->extent_rule == 1) && isfinite(c->dilation) &&
+         isfinite(c->z_near);
+}
+
+struct Plan {
+  flod_ws_layout L;
+  uint64_t unit_off[FLOD_MAX_VIEWS + 1];
+  uint64_t tile_off[FLOD_MAX_VIEWS + 1];
+  uint64_t pix_off[FLOD_MAX_VIEWS + 1];
+  uint32_t tiles_x[FLOD_MAX_VIEWS], tiles_y[FLOD_MAX_VIEWS], cap[FLOD_MAX_VIEWS];
+  uint32_t max_parts;
+  int n_passes;
+};
+
+flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* views, int n_views,
+                      uint64_t pair_capacity, const flod_raster_config* cfg, Plan& P) {
+  if (!sets || !views || n_sets < 1 || n_sets > FLOD_MAX_SETS || n_views < 1 ||
+      n_views > FLOD_MAX_VIEWS || pair_capacity > FLOD_MAX_PAIRS || !cfg_ok(cfg))
+    return FLOD_ERR_INVALID_ARG;
+  for (int s = 0; s < n_sets; ++s) {
+    const flod_gaussians& g = sets[s];
+    if (g.n < 0 || g.n >= (1 << FLOD_SEL_SHIFT) || g.sh_degree < 0 || g.sh_degree > 3 ||
+        !(g.s_min >= 0.f) || !isfinite(g.s_min))
+      return FLOD_ERR_INVALID_ARG;
+    if (g.n > 0 && (!g.means || !g.quats || !g.s_opt || !g.opacity_logit || !g.sh))
+      return FLOD_ERR_INVALID_ARG;
+    if (g.n > 0 && (reinterpret_cast<uintptr_t>(g.quats) & 15u)) return FLOD_ERR_INVALID_ARG;
+    if (g.n > 0 && g.sh_degree == 3 && (reinterpret_cast<uintptr_t>(g.sh) & 15u))
+      return FLOD_ERR_INVALID_ARG;
+  }
+  uint64_t u = 0, t = 0, p = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const flod_view& V = views[v];
+    const flod_camera& C = V.cam;
+    if (C.width <= 0 || C.height <= 0 || C.width > 16384 || C.height > 16384 || !(C.fx > 0.f) ||
+        !(C.fy > 0.f))
+      return FLOD_ERR_INVALID_ARG;
+    for (int k = 0; k < 12; ++k)
+      if (!isfinite(C.viewmat[k])) return FLOD_ERR_INVALID_ARG;
+    uint64_t cap;
+    if (V.sel) {
+      if (!V.sel_count) return FLOD_ERR_INVALID_ARG;
+      cap = V.sel_capacity;
+    } else {
+      if (V.set < 0 || V.set >= n_sets) return FLOD_ERR_INVALID_ARG;
+      cap = (uint64_t)sets[V.set].n;
+    }
+    P.cap[v] = (uint32_t)cap;
+    P.unit_off[v] = u;
+    P.tile_off[v] = t;
+    P.pix_off[v] = p;
+    P.tiles_x[v] = (uint32_t)((C.width + cfg->tile_w - 1) / cfg->tile_w);
+    P.tiles_y[v] = (uint32_t)((C.height + cfg->tile_h - 1) / cfg->tile_h);
+    u += (cap + kScanBlock - 1) / kScanBlock * kScanBlock;
+    t += (uint64_t)P.tiles_x[v] * P.tiles_y[v];
+    p += (uint64_t)C.width * C.height;
+  }
+  P.unit_off[n_views] = u;
+  P.tile_off[n_views] = t;
+  P.pix_off[n_views] = p;
+  if (u >= (1ull << 32) || t >= (1ull << 31)) return FLOD_ERR_INVALID_ARG;
+  int tile_bits = 1;
+  while (tile_bits < 31 && (1ull << tile_bits) < t) ++tile_bits;
+  P.n_passes = (32 + tile_bits + 7) / 8;
+  P.max_parts = (uint32_t)((pair_capacity + kSortPart - 1) / kSortPart);
+  if (P.max_parts == 0) P.max_parts = 1;
+
+  flod_ws_layout& L = P.L;
+  memset(&L, 0, sizeof(L));
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  L.status = take(4);
+  L.pair_count = take(8);
+  L.plan = take(64 * 4);
+  L.xy = take(8 * u);
+  L.depth = take(4 * u);
+  L.conic_o = take(16 * u);
+  L.rgb = take(16 * u);
+  L.radius = take(4 * u);
+  L.tiles_touched = take(4 * u);
+  L.block_sums = take(8 * (u / kScanBlock + 1));
+  L.keys[0] = take(8 * pair_capacity);
+  L.keys[1] = take(8 * pair_capacity);
+  L.vals[0] = take(4 * pair_capacity);
+  L.vals[1] = take(4 * pair_capacity);
+  L.hist = take(4 * kPlanPasses * 256);
+  L.lookback = take(4ull * 2 * P.max_parts * 256);
+  L.ranges = take(8 * t);
+  L.grad2d = take(48 * u);
+  L.queue = take(4 * (t + 64));
+  L.total = off;
+  L.units = u;
+  L.tiles = t;
+  L.pixels = p;
+  L.pair_capacity = pair_capacity;
+  return FLOD_OK;
+}
+
+Ws ws_ptrs(void* base, const Plan& P) {
+  unsigned char* b = static_cast<unsigned char*>(base);
+  const flod_ws_layout& L = P.L;
+  Ws w;
+  w.status = reinterpret_cast<uint32_t*>(b + L.status);
+  w.pair_count = reinterpret_cast<unsigned long long*>(b + L.pair_count);
+  w.plan = reinterpret_cast<uint32_t*>(b + L.plan);
+  w.xy = reinterpret_cast<float2*>(b + L.xy);
+  w.depth = reinterpret_cast<float*>(b + L.depth);
+  w.conic_o = reinterpret_cast<float4*>(b + L.conic_o);
+  w.rgb = reinterpret_cast<float4*>(b + L.rgb);
+  w.radius = reinterpret_cast<float*>(b + L.radius);
+  w.tiles_touched = reinterpret_cast<uint32_t*>(b + L.tiles_touched);
+  w.block_sums = reinterpret_cast<unsigned long long*>(b + L.block_sums);
+  for (int i = 0; i < 2; ++i) {
+    w.keys[i] = reinterpret_cast<unsigned long long*>(b + L.keys[i]);
+    w.vals[i] = reinterpret_cast<uint32_t*>(b + L.vals[i]);
+  }
+  w.hist = reinterpret_cast<uint32_t*>(b + L.hist);
+  w.lookback = reinterpret_cast<uint32_t*>(b + L.lookback);
+  w.ranges = reinterpret_cast<uint2*>(b + L.ranges);
+  w.grad2d = reinterpret_cast<float4*>(b + L.grad2d);
+  w.queue = reinterpret_cast<uint32_t*>(b + L.queue);
+  w.pair_capacity = L.pair_capacity;
+  w.max_parts = P.max_parts;
+  return w;
+}
+
+template <int MAXV>
+void fill_batch(Batch<MAXV>& B, const flod_gaussians* sets, int n_sets, const flod_view* views,
+                int n_views, const flod_raster_config* cfg, const Plan& P) {
+  memset(&B, 0, sizeof(B));
+  B.n_views = n_views;
+  B.n_sets = n_sets;
+  B.units = (uint32_t)P.L.units;
+  B.tiles = (uint32_t)P.L.tiles;
+  B.cfg.tile_w = cfg->tile_w;
+  B.cfg.tile_h = cfg->tile_h;
+  B.cfg.batch = cfg->batch;
+  B.cfg.extent_rule = cfg->extent_rule;
+  B.cfg.dilation = cfg->dilation;
+  B.cfg.z_near = cfg->z_near;
+  for (int c = 0; c < 3; ++c) B.cfg.bg[c] = cfg->bg[c];
+  for (int s = 0; s < n_sets; ++s) {
+    const flod_gaussians& g = sets[s];
+    B.sets[s] = SetP{g.means, g.quats, g.s_opt, g.opacity_logit, g.sh, g.n, g.sh_degree, g.s_min};
+  }
+  for (int v = 0; v < n_views; ++v) {
+    const flod_view& V = views[v];
+    ViewP& O = B.views[v];
+    memcpy(O.vm, V.cam.viewmat, sizeof(O.vm));
+    O.fx = V.cam.fx;
+    O.fy = V.cam.fy;
+    O.cx = V.cam.cx;
+    O.cy = V.cam.cy;
+    O.width = V.cam.width;
+    O.height = V.cam.height;
+    O.cpx = V.cam.cam_pos[0];
+    O.cpy = V.cam.cam_pos[1];
+    O.cpz = V.cam.cam_pos[2];
+    O.set = V.sel ? 0 : V.set;
+    O.sel = V.sel;
+    O.sel_count = V.sel_count;
+    O.cap = P.cap[v];
+    O.unit_off = (uint32_t)P.unit_off[v];
+    O.tile_off = (uint32_t)P.tile_off[v];
+    O.tiles_x = P.tiles_x[v];
+    O.tiles_y = P.tiles_y[v];
+    O.pix_off = P.pix_off[v];
+    B.unit_end[v] = (uint32_t)P.unit_off[v + 1];
+    B.tile_end[v] = (uint32_t)P.tile_off[v + 1];
+  }
+}
+
+// The kernel parameter table is large for big batches; small batches use a small table.
+template <typename F>
+flod_status with_batch(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                       int n_views, const flod_raster_config* cfg, const Plan& P, F&& f) {
+  cudaError_t e;
+  if (n_views <= kMaxViewsSmall) {
+    static thread_local BatchS B;
+    fill_batch(B, sets, n_sets, views, n_views, cfg, P);
+    e = f(B);
+  } else {
+    static thread_local BatchL B;
+    fill_batch(B, sets, n_sets, views, n_views, cfg, P);
+    e = f(B);
+  }
+  return e == cudaSuccess ? FLOD_OK : FLOD_ERR_CUDA;
+}
+
+flod_status common_checks(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                          int n_views, uint64_t cap, const flod_raster_config* cfg, void* ws,
+                          size_t ws_bytes, Plan& P, DevInfo** dev) {
+  flod_status s = make_plan(sets, n_sets, views, n_views, cap, cfg, P);
+  if (s != FLOD_OK) return s;
+  if (!ws) return FLOD_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) & 255u) return FLOD_ERR_INVALID_ARG;
+  if (ws_bytes < P.L.total) return FLOD_ERR_WORKSPACE;
+  return device_info(dev);
+}
+
+}  // namespace
+
+extern "C" {
+
+void flod_default_config(flod_raster_config* c) {
+  if (!c) return;
+  c->tile_w = 16;
+  c->tile_h = 16;
+  c->batch = 256;
+  c->dilation = 0.3f;
+  c->z_near = 0.2f;
+  c->bg[0] = c->bg[1] = c->bg[2] = 0.f;
+  c->extent_rule = 0;
+  c->persistent = 0;
+}
+
+size_t flod_workspace_size(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                           int n_views, uint64_t pair_capacity, const flod_raster_config* cfg) {
+  static thread_local Plan P;
+  if (make_plan(sets, n_sets, views, n_views, pair_capacity, cfg, P) != FLOD_OK) return 0;
+  return P.L.total;
+}
+
+flod_status flod_workspace_layout(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                                  int n_views, uint64_t pair_capacity,
+                                  const flod_raster_config* cfg, flod_ws_layout* out,
+                                  uint64_t* unit_offset, uint64_t* tile_offset,
+                                  uint64_t* pixel_offset) {
+  static thread_local Plan P;
+  if (!out) return FLOD_ERR_INVALID_ARG;
+  flod_status s = make_plan(sets, n_sets, views, n_views, pair_capacity, cfg, P);
+  if (s != FLOD_OK) return s;
+  *out = P.L;
+  for (int v = 0; v <= n_views; ++v) {
+    if (unit_offset) unit_offset[v] = P.unit_off[v];
+    if (tile_offset) tile_offset[v] = P.tile_off[v];
+    if (pixel_offset) pixel_offset[v] = P.pix_off[v];
+  }
+  return FLOD_OK;
+}
+
+flod_status flod_preprocess(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                            int n_views, const flod_raster_config* cfg, void* ws,
+                            size_t ws_bytes, uint64_t pair_capacity, flod_stream stream) {
+  static thread_local Plan P;
+  DevInfo* dev = nullptr;
+  flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
+  if (s != FLOD_OK) return s;
+  const Ws w = ws_ptrs(ws, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(w.status, 0, 4, st) != cudaSuccess) return FLOD_ERR_CUDA;
+  return with_batch(sets, n_sets, views, n_views, cfg, P,
+                    [&](const auto& B) { return launch_preprocess(B, w, st); });
+}
+
+flod_status flod_bin_sort(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                          int n_views, const flod_raster_config* cfg, void* ws, size_t ws_bytes,
+                          uint64_t pair_capacity, uint64_t* d_pair_count, flod_stream stream) {
+  static thread_local Plan P;
+  DevInfo* dev = nullptr;
+  flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
+  if (s != FLOD_OK) return s;
+  const Ws w = ws_ptrs(ws, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int n_passes = P.n_passes;
+  return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {
+    return launch_binning(B, w, n_passes, dev->res_sort, dev->res_small,
+                          reinterpret_cast<unsigned long long*>(d_pair_count), st);
+  });
+}
+
+flod_status flod_render_fwd(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                            int n_views, const flod_raster_config* cfg, void* ws, size_t ws_bytes,
+                            uint64_t pair_capacity, float* out_rgb, float* out_T, uint32_t* out_nc,
+                            flod_stream stream) {
+  static thread_local Plan P;
+  DevInfo* dev = nullptr;
+  if (!out_rgb || !out_T || !out_nc) return FLOD_ERR_INVALID_ARG;
+  flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
+  if (s != FLOD_OK) return s;
+  const Ws w = ws_ptrs(ws, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool pers = cfg->persistent != 0;
+  return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {
+    return launch_render_fwd(B, w, out_rgb, out_T, out_nc, dev->sms, pers, st);
+  });
+}
+
+namespace {
+GradTable grad_table(const flod_view* views, int n_views, int n_sets, const flod_grads* grads) {
+  GradTable gt;
+  memset(&gt, 0, sizeof(gt));
+  int direct[FLOD_MAX_SETS] = {0};
+  int n_sel = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (views[v].sel) ++n_sel;
+    else ++direct[views[v].set];
+  }
+  for (int k = 0; k < n_sets; ++k) {
+    gt.g[k] = grads[k];
+    gt.shared[k] = (direct[k] + n_sel) > 1 ? 1 : 0;
+  }
+  return gt;
+}
+}  // namespace
+
+flod_status flod_blend_bwd(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                           int n_views, const flod_raster_config* cfg, void* ws, size_t ws_bytes,
+                           uint64_t pair_capacity, const float* dL_drgb, const float* fwd_T,
+                           const uint32_t* fwd_nc, flod_stream stream) {
+  static thread_local Plan P;
+  DevInfo* dev = nullptr;
+  if (!dL_drgb || !fwd_T || !fwd_nc) return FLOD_ERR_INVALID_ARG;
+  flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
+  if (s != FLOD_OK) return s;
+  const Ws w = ws_ptrs(ws, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (P.L.units && cudaMemsetAsync(w.grad2d, 0, 48 * P.L.units, st) != cudaSuccess)
+    return FLOD_ERR_CUDA;
+  const bool pers = cfg->persistent != 0;
+  return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {
+    return launch_render_bwd(B, w, dL_drgb, fwd_T, fwd_nc, dev->sms, pers, st);
+  });
+}
+
+flod_status flod_preprocess_bwd(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                                int n_views, const flod_raster_config* cfg, void* ws,
+                                size_t ws_bytes, uint64_t pair_capacity, const flod_grads* grads,
+                                flod_stream stream) {
+  static thread_local Plan P;
+  DevInfo* dev = nullptr;
+  if (!grads) return FLOD_ERR_INVALID_ARG;
+  flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
+  if (s != FLOD_OK) return s;
+  const GradTable gt = grad_table(views, n_views, n_sets, grads);
+  const Ws w = ws_ptrs(ws, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return with_batch(sets, n_sets, views, n_views, cfg, P,
+                    [&](const auto& B) { return launch_preprocess_bwd(B, w, gt, st); });
+}
+
+flod_status flod_render_bwd(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                            int n_views, const flod_raster_config* cfg, void* ws,
+                            size_t ws_bytes, uint64_t pair_capacity, const float* dL_drgb,
+                            const float* fwd_T, const uint32_t* fwd_nc, const flod_grads* grads,
+                            flod_stream stream) {
+  if (!grads) return FLOD_ERR_INVALID_ARG;
+  flod_status s = flod_blend_bwd(sets, n_sets, views, n_views, cfg, ws, ws_bytes, pair_capacity,
+                                 dL_drgb, fwd_T, fwd_nc, stream);
+  if (s != FLOD_OK) return s;
+  return flod_preprocess_bwd(sets, n_sets, views, n_views, cfg, ws, ws_bytes, pair_capacity, grads,
+                             stream);
+}
+
+size_t flod_select_scratch_size(const flod_gaussians* levels, int n_levels) {
+  if (!levels || n_levels < 1 || n_levels > FLOD_MAX_SETS) return 0;
+  int ns[FLOD_MAX_SETS];
+  for (int l = 0; l < n_levels; ++l) ns[l] = levels[l].n < 0 ? 0 : levels[l].n;
+  return 4 * (size_t)(select_blocks(ns, n_levels) + 1);
+}
+
+flod_status flod_select_levels(const flod_gaussians* levels, int n_levels, const float* d_thresh,
+                               float gamma, float focal, const float origin[3], uint32_t* out_sel,
+                               uint32_t sel_capacity, uint32_t* d_count, void* scratch,
+                               size_t scratch_bytes, flod_stream stream) {
+  if (!levels || n_levels < 1 || n_levels > FLOD_MAX_SETS || !origin || !d_count ||
+      (!out_sel && sel_capacity > 0))
+    return FLOD_ERR_INVALID_ARG;
+  SetP lv[FLOD_MAX_SETS];
+  int ns[FLOD_MAX_SETS];
+  for (int l = 0; l < n_levels; ++l) {
+    const flod_gaussians& g = levels[l];
+    if (g.n < 0 || g.n >= (1 << FLOD_SEL_SHIFT) || (g.n > 0 && !g.means)) return FLOD_ERR_INVALID_ARG;
+    lv[l] = SetP{g.means, g.quats, g.s_opt, g.opacity_logit, g.sh, g.n, g.sh_degree, g.s_min};
+    ns[l] = g.n;
+  }
+  float th[FLOD_MAX_SETS];
+  for (int l = 0; l + 1 < n_levels; ++l) {
+    if (d_thresh) {
+      th[l] = d_thresh[l];
+    } else {
+      if (!(gamma > 0.f) || !(focal > 0.f)) return FLOD_ERR_INVALID_ARG;
+      th[l] = (float)((double)levels[l].s_min * (double)focal / (double)gamma);   // Eq. 7
+    }
+    if (!(th[l] >= 0.f)) return FLOD_ERR_INVALID_ARG;
+    if (l > 0 && th[l] > th[l - 1]) return FLOD_ERR_INVALID_ARG;
+  }
+  float lo[FLOD_MAX_SETS], hi[FLOD_MAX_SETS];
+  for (int l = 0; l < n_levels; ++l) {
+    hi[l] = l == 0 ? INFINITY : th[l - 1];
+    lo[l] = l == n_levels - 1 ? 0.f : th[l];
+  }
+  const uint32_t nb = select_blocks(ns, n_levels);
+  if (nb && (!scratch || scratch_bytes < 4 * (size_t)(nb + 1))) return FLOD_ERR_WORKSPACE;
+  DevInfo* dev = nullptr;
+  flod_status s = device_info(&dev);
+  if (s != FLOD_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_select(lv, n_levels, lo, hi, origin, out_sel, sel_capacity, d_count,
+                                static_cast<uint32_t*>(scratch), nb, st);
+  return e == cudaSuccess ? FLOD_OK : FLOD_ERR_CUDA;
+}
+
+flod_status flod_adjust_scale(float* s_opt, int64_t n, float s_min_cur, float s_min_next,
+                              flod_stream stream) {
+  if (n < 0 || (n > 0 && !s_opt) || !(s_min_cur >= s_min_next) || !(s_min_next >= 0.f))
+    return FLOD_ERR_INVALID_ARG;
+  DevInfo* dev = nullptr;
+  flod_status s = device_info(&dev);
+  if (s != FLOD_OK) return s;
+  return launch_adjust_scale(s_opt, n, s_min_cur, s_min_next,
+                             reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FLOD_OK
+             : FLOD_ERR_CUDA;
+}
+
+flod_status flod_read_status(const void* ws, uint32_t* out, flod_stream stream) {
+  if (!ws || !out) return FLOD_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  if (cudaMemcpyAsync(&v, ws, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return FLOD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FLOD_ERR_CUDA;
+  *out = v;
+  return FLOD_OK;
+}
+
+const char* flod_status_string(flod_status s) {
+  switch (s) {
+    case FLOD_OK: return "ok";
+    case FLOD_ERR_INVALID_ARG: return "invalid argument";
+    case FLOD_ERR_CAPACITY: return "pair capacity exceeded";
+    case FLOD_ERR_TIMEOUT: return "device wait timed out";
+    case FLOD_ERR_CUDA: return "CUDA error";
+    case FLOD_ERR_UNSUPPORTED: return "unsupported device (needs sm_103)";
+    case FLOD_ERR_WORKSPACE: return "workspace too small";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

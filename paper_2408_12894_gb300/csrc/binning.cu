@@ -1,0 +1,167 @@
+// Tile binning: per-1024-unit pair counts, their exclusive scan, key emission, and the
+// per-tile [start, end) ranges of the sorted list.
+//
+// Keys are (global tile id << 32) | float bits of the view-space depth t_z (t_z > z_near > 0,
+// so the bits order like the values); every unit emits its tiles in row-major order and
+// units are emitted in index order, so the stable radix sort that follows breaks depth
+// ties by unit index. Pair counts never leave the device: the scan writes the total and
+// the partition count that the sort kernels read.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace flod {
+
+__global__ void __launch_bounds__(256) k_block_sums(const uint32_t* __restrict__ touched,
+                                                    unsigned long long* __restrict__ bsum) {
+  __shared__ uint32_t red[8];
+  const uint4 v = reinterpret_cast<const uint4*>(touched)[blockIdx.x * 256u + threadIdx.x];
+  uint32_t s = v.x + v.y + v.z + v.w;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// One CTA: exclusive scan of the block sums, pair total, partition count, counters reset.
+__global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
+                                                      unsigned long long* user_count) {
+  __shared__ unsigned long long warp_tot[32];
+  __shared__ unsigned long long carry_s;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) carry_s = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < nblocks; base += 1024) {
+    const uint32_t i = base + tid;
+    unsigned long long v = i < nblocks ? ws.block_sums[i] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long w = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      warp_tot[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    const unsigned long long carry = carry_s;
+    const unsigned long long excl = carry + (wid ? warp_tot[wid - 1] : 0ull) + x - v;
+    if (i < nblocks) ws.block_sums[i] = excl;
+    __syncthreads();
+    if (tid == 1023) carry_s = excl + v;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const unsigned long long P = carry_s;
+    *ws.pair_count = P;
+    if (user_count) *user_count = P;
+    unsigned long long pe = P;
+    if (P > ws.pair_capacity) {
+      set_status(ws.status, FLOD_DEV_CAPACITY);
+      pe = ws.pair_capacity;
+    }
+    uint32_t nparts = (uint32_t)((pe + kSortPart - 1) / kSortPart);
+    ws.plan[kPlanNParts] = nparts;
+#pragma unroll
+    for (int p = 0; p < kPlanPasses; ++p) ws.plan[kPlanCounter + p] = 0;
+    ws.plan[kPlanQueue] = 0;
+    ws.plan[kPlanQueue + 1] = 0;
+  }
+}
+
+template <int MAXV>
+__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  __shared__ uint32_t warp_tot[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t unit0 = blockIdx.x * (uint32_t)kScanBlock;
+  const ViewP& V = b.views[view_of_unit(b, unit0)];
+  const uint4 tt = reinterpret_cast<const uint4*>(ws.tiles_touched)[blockIdx.x * 256u + tid];
+  const uint32_t s = tt.x + tt.y + tt.z + tt.w;
+  uint32_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  uint32_t wpre = 0;
+  for (int w = 0; w < wid; ++w) wpre += warp_tot[w];
+  unsigned long long pos = ws.block_sums[blockIdx.x] + wpre + x - s;
+  const uint32_t cnt[4] = {tt.x, tt.y, tt.z, tt.w};
+  const unsigned long long cap = ws.pair_capacity;
+  unsigned long long* keys = ws.keys[0];
+  uint32_t* vals = ws.vals[0];
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t n = cnt[j];
+    if (n == 0) continue;
+    const uint32_t u = unit0 + 4u * tid + j;
+    const float2 xy = ws.xy[u];
+    const float r = ws.radius[u];
+    const unsigned long long dbits = __float_as_uint(ws.depth[u]);
+    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+    tile_rect(xy.x, xy.y, r, V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0, tx1, ty0, ty1);
+    uint32_t k = 0;
+    for (int ty = ty0; ty <= ty1 && k < n; ++ty) {
+      const unsigned long long rowkey = (unsigned long long)(V.tile_off + (uint32_t)ty * V.tiles_x);
+      for (int tx = tx0; tx <= tx1 && k < n; ++tx, ++k) {
+        const unsigned long long p = pos + k;
+        if (p >= cap) break;
+        keys[p] = ((rowkey + (unsigned long long)tx) << 32) | dbits;
+        vals[p] = u;
+      }
+    }
+    pos += n;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ranges(Ws ws) {
+  const unsigned long long P0 = *ws.pair_count;
+  const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
+  const unsigned long long* keys = ws.keys[ws.plan[kPlanFinal]];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ws.ranges[t].x = i;
+    if (i == P - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ws.ranges[t].y = i + 1;
+  }
+}
+
+template <int MAXV>
+cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int resident_sort,
+                           int resident_small, unsigned long long* d_pair_count, cudaStream_t st) {
+  const uint32_t nblocks = b.units / kScanBlock;
+  cudaError_t e;
+  if (b.tiles) {
+    e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * b.tiles, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (nblocks) {
+    k_block_sums<<<nblocks, 256, 0, st>>>(ws.tiles_touched, ws.block_sums);
+  }
+  k_scan_blocks<<<1, 1024, 0, st>>>(ws, nblocks, d_pair_count);
+  if (nblocks) k_emit<MAXV><<<nblocks, 256, 0, st>>>(b, ws);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_radix_sort(ws, n_passes, resident_small, resident_sort, st)) != cudaSuccess) return e;
+  k_ranges<<<resident_small, 256, 0, st>>>(ws);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_binning<kMaxViewsSmall>(const BatchS&, const Ws&, int, int, int,
+                                                    unsigned long long*, cudaStream_t);
+template cudaError_t launch_binning<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, int, int, int,
+                                                    unsigned long long*, cudaStream_t);
+
+}  // namespace flod

@@ -1,0 +1,166 @@
+// Internal definitions shared by the CUDA translation units of the FLoD splatting path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/flod.h"
+
+namespace flod {
+
+// ---------------------------------------------------------------------------------------
+// constants of the blending rule (Sec. 3, after Eq. 2; 3DGS prior art)
+// ---------------------------------------------------------------------------------------
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kClampFov = 1.3f;        // Jacobian off-screen guard, x tan(half fov)
+
+constexpr int kScanBlock = 1024;         // units per block-sum entry; view capacities are
+                                         // rounded up to a multiple of it
+constexpr int kMaxViewsSmall = 8;        // views carried in the small parameter table
+
+// ---------------------------------------------------------------------------------------
+// per-view / per-set tables, passed by value as __grid_constant__ kernel parameters
+// ---------------------------------------------------------------------------------------
+struct ViewP {
+  float vm[12];
+  float fx, fy, cx, cy;
+  int width, height;
+  float cpx, cpy, cpz;
+  int set;
+  const uint32_t* sel;
+  const uint32_t* sel_count;
+  uint32_t cap;        // units reserved (not rounded)
+  uint32_t unit_off;   // first unit of the view (multiple of kScanBlock)
+  uint32_t tile_off;   // first global tile id
+  uint32_t tiles_x, tiles_y;
+  uint64_t pix_off;    // first pixel of the view in the concatenated outputs
+};
+
+struct SetP {
+  const float* means;
+  const float* quats;
+  const float* s_opt;
+  const float* logit;
+  const float* sh;
+  int n, deg;
+  float s_min;
+};
+
+struct CfgP {
+  int tile_w, tile_h, batch, extent_rule;
+  float dilation, z_near;
+  float bg[3];
+};
+
+template <int MAXV>
+struct Batch {
+  int n_views, n_sets;
+  uint32_t units, tiles;
+  CfgP cfg;
+  SetP sets[FLOD_MAX_SETS];
+  ViewP views[MAXV];
+  uint32_t unit_end[MAXV];  // exclusive prefix ends, for unit -> view lookup
+  uint32_t tile_end[MAXV];
+};
+
+using BatchS = Batch<kMaxViewsSmall>;
+using BatchL = Batch<FLOD_MAX_VIEWS>;
+
+// workspace pointers derived from the layout
+struct Ws {
+  uint32_t* status;
+  unsigned long long* pair_count;
+  uint32_t* plan;
+  float2* xy;
+  float* depth;
+  float4* conic_o;
+  float4* rgb;
+  float* radius;
+  uint32_t* tiles_touched;
+  unsigned long long* block_sums;
+  unsigned long long* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;
+  uint32_t* lookback;
+  uint2* ranges;
+  float4* grad2d;
+  uint32_t* queue;
+  uint64_t pair_capacity;
+  uint32_t max_parts;
+};
+
+// radix-sort plan words (uint32 plan[64])
+constexpr int kPlanPasses = 8;       // at most 8 digit passes of 8 bits over 64-bit keys
+constexpr int kPlanActive = 0;       // plan[kPlanActive + p] = 1 if pass p moves keys
+constexpr int kPlanSrc = 8;          // plan[kPlanSrc + p] = source buffer of pass p
+constexpr int kPlanLb = 16;          // plan[kPlanLb + p] = look-back table of pass p
+constexpr int kPlanCounter = 24;     // plan[kPlanCounter + p] = partition ticket counter
+constexpr int kPlanNParts = 40;      // number of partitions
+constexpr int kPlanQueue = 41;       // render work-queue ticket counter (x2: fwd, bwd)
+constexpr int kPlanEvalFwd = 48;     // uint64 running count of forward evaluations
+constexpr int kPlanEvalBwd = 50;     // uint64 running count of backward evaluations
+constexpr int kPlanFinal = 63;       // buffer holding the sorted result
+
+constexpr int kSortThreads = 256;
+constexpr int kSortKeysPerThread = 16;
+constexpr int kSortPart = kSortThreads * kSortKeysPerThread;   // 4096 keys per partition
+
+template <int MAXV>
+__device__ __forceinline__ int view_of_unit(const Batch<MAXV>& b, uint32_t u) {
+  int lo = 0, hi = b.n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (u < b.unit_end[mid]) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+template <int MAXV>
+__device__ __forceinline__ int view_of_tile(const Batch<MAXV>& b, uint32_t t) {
+  int lo = 0, hi = b.n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (t < b.tile_end[mid]) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// The pixel rectangle rule, every step rounded to nearest in float32 so that a float32
+// reference takes the same decisions: columns ceil((u - r) - 0.5) .. floor((u + r) - 0.5),
+// clamped to the image; then tiles. Returns false if empty.
+__device__ __forceinline__ bool tile_rect(float u, float v, float r, int W, int H, int tw,
+                                          int th, int& tx0, int& tx1, int& ty0, int& ty1) {
+  float x0 = ceilf(__fsub_rn(__fsub_rn(u, r), 0.5f));
+  float x1 = floorf(__fsub_rn(__fadd_rn(u, r), 0.5f));
+  float y0 = ceilf(__fsub_rn(__fsub_rn(v, r), 0.5f));
+  float y1 = floorf(__fsub_rn(__fadd_rn(v, r), 0.5f));
+  // NaN compares false: treat as empty
+  if (!(x0 <= x1) || !(y0 <= y1)) return false;
+  x0 = fmaxf(x0, 0.f);
+  y0 = fmaxf(y0, 0.f);
+  x1 = fminf(x1, (float)(W - 1));
+  y1 = fminf(y1, (float)(H - 1));
+  if (x0 > x1 || y0 > y1) return false;
+  tx0 = (int)x0 / tw;
+  tx1 = (int)x1 / tw;
+  ty0 = (int)y0 / th;
+  ty1 = (int)y1 / th;
+  return true;
+}
+
+// Per-pixel opacity of a splat: alpha = min(0.99, o * exp(-q/2)) with
+// q = a dx^2 + 2 b dx dy + c dy^2, dx = px - u. Written with explicit roundings so that
+// the forward and the backward pass recompute bit-identical values.
+__device__ __forceinline__ float splat_alpha(float dx, float dy, float4 co, float& g) {
+  float q = __fmaf_rn(co.x * dx, dx, __fmaf_rn(2.f * co.y * dx, dy, __fmul_rn(co.z * dy, dy)));
+  g = __expf(-0.5f * q);
+  return fminf(kAlphaMax, __fmul_rn(co.w, g));
+}
+
+__device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {
+  atomicOr(status, bits);
+}
+
+}  // namespace flod

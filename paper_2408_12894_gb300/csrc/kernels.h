@@ -1,0 +1,50 @@
+// Launchers of the kernels, one group per translation unit; called by the C-ABI layer.
+#pragma once
+
+#include "common.cuh"
+
+namespace flod {
+
+struct GradTable {
+  flod_grads g[FLOD_MAX_SETS];
+  int shared[FLOD_MAX_SETS];   // 1: several units may update one Gaussian -> atomics
+};
+
+// preprocess.cu
+template <int MAXV>
+cudaError_t launch_preprocess(const Batch<MAXV>& b, const Ws& ws, cudaStream_t st);
+template <int MAXV>
+cudaError_t launch_preprocess_bwd(const Batch<MAXV>& b, const Ws& ws, const GradTable& gt,
+                                  cudaStream_t st);
+
+// binning.cu: block sums -> scan -> emit -> (sort) -> ranges
+template <int MAXV>
+cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int resident_sort,
+                           int resident_small, unsigned long long* d_pair_count, cudaStream_t st);
+
+// sort.cu
+cudaError_t launch_radix_sort(const Ws& ws, int n_passes, int resident_hist, int resident_sort,
+                              cudaStream_t st);
+int sort_kernel_smem_bytes();
+cudaError_t sort_kernel_prepare();           // opt-in shared memory size
+const void* sort_kernel_ptr();
+
+// render.cu
+template <int MAXV>
+cudaError_t launch_render_fwd(const Batch<MAXV>& b, const Ws& ws, float* out_rgb, float* out_T,
+                              uint32_t* out_nc, int resident, bool persistent, cudaStream_t st);
+template <int MAXV>
+cudaError_t launch_render_bwd(const Batch<MAXV>& b, const Ws& ws, const float* dL,
+                              const float* fwd_T, const uint32_t* fwd_nc, int resident,
+                              bool persistent, cudaStream_t st);
+
+// select.cu
+cudaError_t launch_select(const SetP* levels, int n_levels, const float* thresh_lo,
+                          const float* thresh_hi, const float origin[3], uint32_t* out,
+                          uint32_t cap, uint32_t* d_count, uint32_t* scratch, uint32_t n_blocks,
+                          cudaStream_t st);
+uint32_t select_blocks(const int* ns, int n_levels);
+cudaError_t launch_adjust_scale(float* s_opt, int64_t n, float s_cur, float s_next,
+                                cudaStream_t st);
+
+}  // namespace flod

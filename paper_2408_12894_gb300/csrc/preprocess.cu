@@ -1,0 +1,366 @@
+// Per-(view, Gaussian) preprocess and its backward.
+//
+// Forward (one thread per unit): Eq. 4 constrained scale s = exp(s_opt) + s_min (Sec. 4.1),
+// Eq. 1 covariance through M = R diag(s) (Sigma = M M^T, Sec. 3), the local-affine
+// projection of Eq. 2 (Sigma' = (J W M)(J W M)^T + dilation I), conic, opacity, the
+// opacity-aware extent, the tile rectangle and the SH colour.
+//
+// Backward (one thread per unit): the chain rule of the same steps, from the per-unit
+// gradient of (u, v, conic, opacity, rgb) that the blending backward accumulated, to the
+// parameters (means, quats, s_opt, opacity_logit, sh).
+#include "common.cuh"
+#include "kernels.h"
+#include "sh.cuh"
+
+namespace flod {
+
+template <int MAXV>
+__device__ __forceinline__ bool unit_source(const Batch<MAXV>& b, const ViewP& V, uint32_t local,
+                                            int& si, uint32_t& gi) {
+  if (V.sel) {
+    uint32_t cnt = *V.sel_count;
+    if (local >= cnt || local >= V.cap) return false;
+    uint32_t e = V.sel[local];
+    si = (int)(e >> FLOD_SEL_SHIFT);
+    gi = e & ((1u << FLOD_SEL_SHIFT) - 1u);
+    return si < b.n_sets && gi < (uint32_t)b.sets[si].n;
+  }
+  if (local >= V.cap) return false;
+  si = V.set;
+  gi = local;
+  return gi < (uint32_t)b.sets[si].n;
+}
+
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float* R) {
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Shared forward geometry of one unit (used by both passes).
+struct Geom {
+  float qn[4], qinv;          // normalised quaternion, 1 / |q|
+  float R[9], s[3], es[3];    // rotation, constrained scale, exp(s_opt)
+  float t[3], itz;            // view-space mean, 1 / t_z
+  float kx, ky;               // clamped t_x/t_z, t_y/t_z used by the Jacobian
+  bool ckx, cky;              // whether the clamps were active
+  float T[6];                 // J W (2x3)
+  float P[6];                 // J W M (2x3)
+  float A, B, C, det;         // Sigma' entries (dilated) and determinant
+};
+
+__device__ __forceinline__ void geometry(const SetP& S, uint32_t gi, const ViewP& V,
+                                         const CfgP& cfg, Geom& G) {
+  const float* mu = S.means + 3ull * gi;
+  const float4 q = __ldg(reinterpret_cast<const float4*>(S.quats) + gi);
+  const float* so = S.s_opt + 3ull * gi;
+  float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  G.qinv = 1.f / sqrtf(qq);
+  G.qn[0] = q.x * G.qinv; G.qn[1] = q.y * G.qinv; G.qn[2] = q.z * G.qinv; G.qn[3] = q.w * G.qinv;
+  quat_rot(G.qn[0], G.qn[1], G.qn[2], G.qn[3], G.R);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    G.es[k] = expf(__ldg(so + k));
+    G.s[k] = G.es[k] + S.s_min;
+  }
+  const float mx = __ldg(mu), my = __ldg(mu + 1), mz = __ldg(mu + 2);
+  const float* W = V.vm;
+  G.t[0] = W[0] * mx + W[1] * my + W[2] * mz + W[3];
+  G.t[1] = W[4] * mx + W[5] * my + W[6] * mz + W[7];
+  G.t[2] = W[8] * mx + W[9] * my + W[10] * mz + W[11];
+  const float tz = G.t[2];
+  G.itz = 1.f / tz;
+  const float limx = kClampFov * 0.5f * (float)V.width / V.fx;
+  const float limy = kClampFov * 0.5f * (float)V.height / V.fy;
+  const float rx = G.t[0] * G.itz, ry = G.t[1] * G.itz;
+  G.kx = fminf(fmaxf(rx, -limx), limx);
+  G.ky = fminf(fmaxf(ry, -limy), limy);
+  G.ckx = (rx < -limx) || (rx > limx);
+  G.cky = (ry < -limy) || (ry > limy);
+  // J = [[fx/tz, 0, -fx kx/tz], [0, fy/tz, -fy ky/tz]]; T = J W
+  const float j00 = V.fx * G.itz, j02 = -V.fx * G.kx * G.itz;
+  const float j11 = V.fy * G.itz, j12 = -V.fy * G.ky * G.itz;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    G.T[k] = j00 * W[k] + j02 * W[8 + k];
+    G.T[3 + k] = j11 * W[4 + k] + j12 * W[8 + k];
+  }
+  // P = T M, M = R diag(s)
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      G.P[3 * r + k] = (G.T[3 * r] * G.R[k] + G.T[3 * r + 1] * G.R[3 + k] + G.T[3 * r + 2] * G.R[6 + k]) * G.s[k];
+  G.A = G.P[0] * G.P[0] + G.P[1] * G.P[1] + G.P[2] * G.P[2] + cfg.dilation;
+  G.B = G.P[0] * G.P[3] + G.P[1] * G.P[4] + G.P[2] * G.P[5];
+  G.C = G.P[3] * G.P[3] + G.P[4] * G.P[4] + G.P[5] * G.P[5] + cfg.dilation;
+  G.det = G.A * G.C - G.B * G.B;
+}
+
+// Colour of a unit (and the pre-clamp value), SH of degree deg.
+__device__ __forceinline__ void sh_colour(const SetP& S, uint32_t gi, const ViewP& V, float* Y,
+                                          float dir[3], float& dlen, float raw[3]) {
+  const float* mu = S.means + 3ull * gi;
+  float dx = __ldg(mu) - V.cpx, dy = __ldg(mu + 1) - V.cpy, dz = __ldg(mu + 2) - V.cpz;
+  dlen = sqrtf(dx * dx + dy * dy + dz * dz);
+  float il = 1.f / dlen;
+  dir[0] = dx * il; dir[1] = dy * il; dir[2] = dz * il;
+  const int K = (S.deg + 1) * (S.deg + 1);
+  sh_basis(S.deg, dir[0], dir[1], dir[2], Y);
+  raw[0] = raw[1] = raw[2] = 0.5f;
+  const float* c = S.sh + 3ull * K * gi;
+  if (S.deg == 3) {
+    const float4* c4 = reinterpret_cast<const float4*>(c);
+    float cf[48];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      float4 v = __ldg(c4 + i);
+      cf[4 * i] = v.x; cf[4 * i + 1] = v.y; cf[4 * i + 2] = v.z; cf[4 * i + 3] = v.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      raw[0] += Y[k] * cf[3 * k];
+      raw[1] += Y[k] * cf[3 * k + 1];
+      raw[2] += Y[k] * cf[3 * k + 2];
+    }
+  } else {
+    for (int k = 0; k < K; ++k) {
+      raw[0] += Y[k] * __ldg(c + 3 * k);
+      raw[1] += Y[k] * __ldg(c + 3 * k + 1);
+      raw[2] += Y[k] * __ldg(c + 3 * k + 2);
+    }
+  }
+}
+
+template <int MAXV>
+__global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  const uint32_t u = blockIdx.x * 256u + threadIdx.x;
+  if (u >= b.units) return;
+  const ViewP& V = b.views[view_of_unit(b, u)];
+  int si = 0;
+  uint32_t gi = 0;
+  bool ok = unit_source(b, V, u - V.unit_off, si, gi);
+  float2 xy = make_float2(0.f, 0.f);
+  float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 rgb = make_float4(0.f, 0.f, 0.f, 0.f);
+  float depth = 0.f, rad = 0.f;
+  uint32_t touched = 0;
+  if (ok) {
+    const SetP& S = b.sets[si];
+    Geom G;
+    geometry(S, gi, V, b.cfg, G);
+    ok = G.t[2] > b.cfg.z_near && G.det > 0.f;
+    float o = 1.f / (1.f + expf(-__ldg(S.logit + gi)));
+    if (ok) {
+      float lmax = 0.5f * (G.A + G.C) + sqrtf(fmaxf(0.25f * (G.A - G.C) * (G.A - G.C) + G.B * G.B, 0.f));
+      if (b.cfg.extent_rule == 0) {
+        ok = o >= kAlphaMin;
+        rad = sqrtf(fmaxf(2.f * logf(255.f * o) * lmax, 0.f));
+      } else {
+        rad = 3.f * sqrtf(lmax);
+      }
+    }
+    if (ok) {
+      xy.x = V.fx * G.t[0] * G.itz + V.cx;
+      xy.y = V.fy * G.t[1] * G.itz + V.cy;
+      int tx0, tx1, ty0, ty1;
+      ok = tile_rect(xy.x, xy.y, rad, V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0, tx1, ty0, ty1);
+      if (ok) touched = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    }
+    if (ok) {
+      float id = 1.f / G.det;
+      co = make_float4(G.C * id, -G.B * id, G.A * id, o);
+      depth = G.t[2];
+      float Y[16], dir[3], dlen, raw[3];
+      sh_colour(S, gi, V, Y, dir, dlen, raw);
+      rgb = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), 0.f);
+    } else {
+      xy = make_float2(0.f, 0.f);
+      rad = 0.f;
+    }
+  }
+  ws.xy[u] = xy;
+  ws.depth[u] = depth;
+  ws.conic_o[u] = co;
+  ws.rgb[u] = rgb;
+  ws.radius[u] = rad;
+  ws.tiles_touched[u] = touched;
+}
+
+// ---------------------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void add_grad(float* p, float v, bool atomic) {
+  if (v == 0.f) return;
+  if (atomic) atomicAdd(p, v); else *p += v;
+}
+
+template <int MAXV>
+__global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ Batch<MAXV> b,
+                                                        Ws ws, GradTable gt) {
+  const uint32_t u = blockIdx.x * 128u + threadIdx.x;
+  if (u >= b.units) return;
+  if (ws.tiles_touched[u] == 0) return;
+  const int vi = view_of_unit(b, u);
+  const ViewP& V = b.views[vi];
+  int si = 0;
+  uint32_t gi = 0;
+  if (!unit_source(b, V, u - V.unit_off, si, gi)) return;
+  const float4 g0 = ws.grad2d[3ull * u];      // du, dv, dopacity
+  const float4 g1 = ws.grad2d[3ull * u + 1];  // da, db, dc
+  const float4 g2 = ws.grad2d[3ull * u + 2];  // dr, dg, db
+  const SetP& S = b.sets[si];
+  const flod_grads& GR = gt.g[si];
+  const bool atomic = gt.shared[si] != 0;
+  Geom G;
+  geometry(S, gi, V, b.cfg, G);
+
+  // ---- colour -> SH coefficients and view direction
+  float Y[16], dir[3], dlen, raw[3];
+  sh_colour(S, gi, V, Y, dir, dlen, raw);
+  float drgb[3] = {raw[0] > 0.f ? g2.x : 0.f, raw[1] > 0.f ? g2.y : 0.f, raw[2] > 0.f ? g2.z : 0.f};
+  const int K = (S.deg + 1) * (S.deg + 1);
+  float dmu[3] = {0.f, 0.f, 0.f};
+  if (drgb[0] != 0.f || drgb[1] != 0.f || drgb[2] != 0.f) {
+    const float* c = S.sh + 3ull * K * gi;
+    float wk[16];
+    for (int k = 0; k < K; ++k)
+      wk[k] = __ldg(c + 3 * k) * drgb[0] + __ldg(c + 3 * k + 1) * drgb[1] + __ldg(c + 3 * k + 2) * drgb[2];
+    if (GR.sh) {
+      float* gs = GR.sh + 3ull * K * gi;
+      for (int k = 0; k < K; ++k) {
+        add_grad(gs + 3 * k, Y[k] * drgb[0], atomic);
+        add_grad(gs + 3 * k + 1, Y[k] * drgb[1], atomic);
+        add_grad(gs + 3 * k + 2, Y[k] * drgb[2], atomic);
+      }
+    }
+    float gx, gy, gz;
+    sh_grad_dir(S.deg, dir[0], dir[1], dir[2], wk, gx, gy, gz);
+    float proj = gx * dir[0] + gy * dir[1] + gz * dir[2];
+    float il = 1.f / dlen;
+    dmu[0] += (gx - proj * dir[0]) * il;
+    dmu[1] += (gy - proj * dir[1]) * il;
+    dmu[2] += (gz - proj * dir[2]) * il;
+  }
+
+  // ---- opacity
+  const float o = 1.f / (1.f + expf(-__ldg(S.logit + gi)));
+  if (GR.opacity_logit) add_grad(GR.opacity_logit + gi, g0.z * o * (1.f - o), atomic);
+
+  // ---- conic (a, b, c) -> Sigma' (A, B, C)
+  const float A = G.A, B = G.B, C = G.C;
+  const float id = 1.f / G.det, id2 = id * id;
+  const float da = g1.x, db = g1.y, dc = g1.z;
+  const float dA = (-C * C * da + B * C * db - B * B * dc) * id2;
+  const float dB = (2.f * B * C * da - (A * C + B * B) * db + 2.f * A * B * dc) * id2;
+  const float dC = (-B * B * da + A * B * db - A * A * dc) * id2;
+  // ---- Sigma' = P P^T  ->  dP
+  float dP[6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dP[k] = 2.f * dA * G.P[k] + dB * G.P[3 + k];
+    dP[3 + k] = dB * G.P[k] + 2.f * dC * G.P[3 + k];
+  }
+  // ---- P = T M -> dT, dM ; M = R diag(s)
+  float dT[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float dM[9];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float Mjk = G.R[3 * j + k] * G.s[k];
+      dT[j] += dP[k] * Mjk;
+      dT[3 + j] += dP[3 + k] * Mjk;
+      dM[3 * j + k] = G.T[j] * dP[k] + G.T[3 + j] * dP[3 + k];
+    }
+  float dR[9], ds[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dR[3 * j + k] = dM[3 * j + k] * G.s[k];
+      ds[k] += dM[3 * j + k] * G.R[3 * j + k];
+    }
+  if (GR.s_opt) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) add_grad(GR.s_opt + 3ull * gi + k, ds[k] * G.es[k], atomic);
+  }
+  // ---- R(q_n) -> dq_n -> dq
+  if (GR.quats) {
+    const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
+    float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    float dx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] - 2.f * x * dR[8]);
+    float dy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] - 2.f * y * dR[8]);
+    float dz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
+    float dot = w * dw + x * dx + y * dy + z * dz;
+    float* gq = GR.quats + 4ull * gi;
+    add_grad(gq, (dw - w * dot) * G.qinv, atomic);
+    add_grad(gq + 1, (dx - x * dot) * G.qinv, atomic);
+    add_grad(gq + 2, (dy - y * dot) * G.qinv, atomic);
+    add_grad(gq + 3, (dz - z * dot) * G.qinv, atomic);
+  }
+  // ---- T = J W -> dJ -> dt ; mean2d -> dt
+  const float* W = V.vm;
+  float dJ00 = 0.f, dJ02 = 0.f, dJ11 = 0.f, dJ12 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dJ00 += dT[k] * W[k];
+    dJ02 += dT[k] * W[8 + k];
+    dJ11 += dT[3 + k] * W[4 + k];
+    dJ12 += dT[3 + k] * W[8 + k];
+  }
+  const float itz = G.itz, itz2 = itz * itz;
+  const float tx = G.t[0], ty = G.t[1];
+  float dt0 = 0.f, dt1 = 0.f, dt2 = 0.f;
+  dt2 += -V.fx * itz2 * dJ00 - V.fy * itz2 * dJ11;
+  dt2 += dJ02 * V.fx * G.kx * itz2 + dJ12 * V.fy * G.ky * itz2;
+  if (!G.ckx) {
+    dt0 += -V.fx * itz2 * dJ02;
+    dt2 += dJ02 * V.fx * tx * itz2 * itz;
+  }
+  if (!G.cky) {
+    dt1 += -V.fy * itz2 * dJ12;
+    dt2 += dJ12 * V.fy * ty * itz2 * itz;
+  }
+  dt0 += g0.x * V.fx * itz;
+  dt1 += g0.y * V.fy * itz;
+  dt2 += -(g0.x * V.fx * tx + g0.y * V.fy * ty) * itz2;
+  dmu[0] += W[0] * dt0 + W[4] * dt1 + W[8] * dt2;
+  dmu[1] += W[1] * dt0 + W[5] * dt1 + W[9] * dt2;
+  dmu[2] += W[2] * dt0 + W[6] * dt1 + W[10] * dt2;
+  if (GR.means) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) add_grad(GR.means + 3ull * gi + k, dmu[k], atomic);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+template <int MAXV>
+cudaError_t launch_preprocess(const Batch<MAXV>& b, const Ws& ws, cudaStream_t st) {
+  if (b.units == 0) return cudaSuccess;
+  k_preprocess<MAXV><<<(b.units + 255) / 256, 256, 0, st>>>(b, ws);
+  return cudaGetLastError();
+}
+
+template <int MAXV>
+cudaError_t launch_preprocess_bwd(const Batch<MAXV>& b, const Ws& ws, const GradTable& gt,
+                                  cudaStream_t st) {
+  if (b.units == 0) return cudaSuccess;
+  k_preprocess_bwd<MAXV><<<(b.units + 127) / 128, 128, 0, st>>>(b, ws, gt);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_preprocess<kMaxViewsSmall>(const BatchS&, const Ws&, cudaStream_t);
+template cudaError_t launch_preprocess<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, cudaStream_t);
+template cudaError_t launch_preprocess_bwd<kMaxViewsSmall>(const BatchS&, const Ws&, const GradTable&, cudaStream_t);
+template cudaError_t launch_preprocess_bwd<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, const GradTable&, cudaStream_t);
+
+}  // namespace flod

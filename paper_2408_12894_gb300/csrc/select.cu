@@ -1,0 +1,184 @@
+// Level selection (Eq. 6 with the thresholds of Eq. 7, Sec. 5.2) and AdjustScale (Eq. 5,
+// Sec. 4.2).
+//
+// Selection is a stream compaction over the concatenation of the levels: a Gaussian of
+// level k is kept iff lo_k <= d < hi_k with d = ||mean - origin|| in float32 (each
+// difference, square and sum rounded to nearest, then a correctly rounded square root), so
+// that the decision is reproducible by any float32 implementation. Three launches: per-block
+// counts, one-CTA scan of the counts, ordered write. The output is in (level, index) order.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace flod {
+
+constexpr int kSelThreads = 256;
+constexpr int kSelPerThread = 8;
+constexpr int kSelBlock = kSelThreads * kSelPerThread;   // 2048 Gaussians per block
+
+struct SelP {
+  SetP lv[FLOD_MAX_SETS];
+  float lo[FLOD_MAX_SETS], hi[FLOD_MAX_SETS];
+  uint32_t start[FLOD_MAX_SETS + 1];   // first global index of each level (block aligned)
+  int n_levels;
+  float ox, oy, oz;
+  uint32_t total_blocks;
+};
+
+__device__ __forceinline__ bool sel_keep(const SelP& s, int lv, uint32_t i) {
+  const float* m = s.lv[lv].means + 3ull * i;
+  const float dx = __fsub_rn(__ldg(m), s.ox);
+  const float dy = __fsub_rn(__ldg(m + 1), s.oy);
+  const float dz = __fsub_rn(__ldg(m + 2), s.oz);
+  const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  const float d = __fsqrt_rn(d2);
+  return d >= s.lo[lv] && d < s.hi[lv];
+}
+
+__device__ __forceinline__ int level_of_block(const SelP& s, uint32_t blk) {
+  const uint32_t g = blk * (uint32_t)kSelBlock;
+  int lv = 0;
+  while (lv + 1 < s.n_levels && g >= s.start[lv + 1]) ++lv;
+  return lv;
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_count(const __grid_constant__ SelP s,
+                                                           uint32_t* counts) {
+  __shared__ uint32_t red[kSelThreads / 32];
+  const int lv = level_of_block(s, blockIdx.x);
+  const uint32_t i0 = blockIdx.x * (uint32_t)kSelBlock - s.start[lv];
+  const uint32_t n = (uint32_t)s.lv[lv].n;
+  uint32_t c = 0;
+#pragma unroll
+  for (int j = 0; j < kSelPerThread; ++j) {
+    const uint32_t i = i0 + j * kSelThreads + threadIdx.x;
+    if (i < n && sel_keep(s, lv, i)) ++c;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) t += red[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_sel_scan(uint32_t* counts, uint32_t nblocks,
+                                                   uint32_t* d_count) {
+  __shared__ uint32_t wt[32];
+  __shared__ uint32_t carry_s;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) carry_s = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < nblocks; base += 1024) {
+    const uint32_t i = base + tid;
+    const uint32_t v = i < nblocks ? counts[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = wt[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wt[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = carry_s + (wid ? wt[wid - 1] : 0u) + x - v;
+    if (i < nblocks) counts[i] = excl;
+    __syncthreads();
+    if (tid == 1023) carry_s = excl + v;
+    __syncthreads();
+  }
+  if (tid == 0) *d_count = carry_s;
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_write(const __grid_constant__ SelP s,
+                                                           const uint32_t* offsets, uint32_t* out,
+                                                           uint32_t cap) {
+  __shared__ uint32_t wcnt[kSelThreads / 32];
+  __shared__ uint32_t base_s;
+  const int lv = level_of_block(s, blockIdx.x);
+  const uint32_t i0 = blockIdx.x * (uint32_t)kSelBlock - s.start[lv];
+  const uint32_t n = (uint32_t)s.lv[lv].n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base_s = offsets[blockIdx.x];
+  // rounds of 256 consecutive Gaussians; inside a round, order = thread order
+  for (int j = 0; j < kSelPerThread; ++j) {
+    const uint32_t i = i0 + j * kSelThreads + threadIdx.x;
+    const bool keep = i < n && sel_keep(s, lv, i);
+    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    uint32_t pre = base_s;
+    for (int w = 0; w < wid; ++w) pre += wcnt[w];
+    pre += __popc(bal & ((1u << lane) - 1u));
+    if (keep && pre < cap) out[pre] = ((uint32_t)lv << FLOD_SEL_SHIFT) | i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t t = 0;
+      for (int w = 0; w < kSelThreads / 32; ++w) t += wcnt[w];
+      base_s += t;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_select(const SetP* levels, int n_levels, const float* lo, const float* hi,
+                          const float origin[3], uint32_t* out, uint32_t cap, uint32_t* d_count,
+                          uint32_t* scratch, uint32_t n_blocks, cudaStream_t st) {
+  SelP s{};
+  s.n_levels = n_levels;
+  uint32_t g = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    s.lv[l] = levels[l];
+    s.lo[l] = lo[l];
+    s.hi[l] = hi[l];
+    s.start[l] = g;
+    g += (uint32_t)((levels[l].n + kSelBlock - 1) / kSelBlock) * kSelBlock;
+  }
+  s.start[n_levels] = g;
+  s.ox = origin[0];
+  s.oy = origin[1];
+  s.oz = origin[2];
+  s.total_blocks = n_blocks;
+  if (n_blocks == 0) {
+    return cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
+  }
+  k_sel_count<<<n_blocks, kSelThreads, 0, st>>>(s, scratch);
+  k_sel_scan<<<1, 1024, 0, st>>>(scratch, n_blocks, d_count);
+  k_sel_write<<<n_blocks, kSelThreads, 0, st>>>(s, scratch, out, cap);
+  return cudaGetLastError();
+}
+
+uint32_t select_blocks(const int* ns, int n_levels) {
+  uint32_t b = 0;
+  for (int l = 0; l < n_levels; ++l) b += (uint32_t)((ns[l] + kSelBlock - 1) / kSelBlock);
+  return b;
+}
+
+// Eq. 5 in float32 with the library exp/log (full precision).
+__global__ void k_adjust_scale(float* s_opt, int64_t n, float s_cur, float s_next) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s_opt[i] = logf(expf(s_opt[i]) + (s_cur - s_next));
+}
+
+cudaError_t launch_adjust_scale(float* s_opt, int64_t n, float s_cur, float s_next,
+                                cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_adjust_scale<<<(unsigned)blocks, 256, 0, st>>>(s_opt, n, s_cur, s_next);
+  return cudaGetLastError();
+}
+
+}  // namespace flod

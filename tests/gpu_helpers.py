@@ -1,0 +1,133 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI, read and
+write workspace regions, and compare against the FP64 oracle.
+
+Inputs always come from the seeded generators or from the oracle; nothing computed by the
+CUDA path is ever fed to the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from oracle import projection as OP
+from oracle import raster as R
+from paper_2408_12894_gb300 import flod, synth
+
+# tolerances (float32 path vs float64 oracle)
+IMG_MAX_ABS = 2e-4      # per pixel and channel, on >= 99.9% of pixels
+IMG_FRAC = 0.999
+IMG_MEAN_ABS = 1e-5     # per channel
+GRAD_REL = 1e-3         # ||g_gpu - g_ref|| / ||g_ref|| per parameter tensor
+
+
+def rasterizer(sets_np, cams, s_mins, view_sets=None, cfg=None, pair_capacity=None):
+    sets = [flod.GaussianSet.from_numpy(g, s) for g, s in zip(sets_np, s_mins)]
+    view_sets = view_sets if view_sets is not None else [0] * len(cams)
+    views = [flod.view_struct(c, vs) for c, vs in zip(cams, view_sets)]
+    return flod.Rasterizer(sets, views, cfg, pair_capacity)
+
+
+def oracle_cfg(cfg) -> R.Config:
+    return R.Config(tile_w=cfg.tile_w, tile_h=cfg.tile_h, dilation=float(cfg.dilation),
+                    z_near=float(cfg.z_near), bg=tuple(float(x) for x in cfg.bg),
+                    extent_rule=cfg.extent_rule)
+
+
+def oracle_pre(g, s_min, cam, ocfg):
+    with torch.no_grad():
+        return R.preprocess(R.params(g), g["sh_degree"], s_min, cam, ocfg)
+
+
+def units(rast, view: int, n: int) -> dict:
+    """The preprocess outputs of the first n units of a view, as numpy arrays."""
+    u0 = rast.unit_off[view]
+    U = rast.layout.units
+    out = {
+        "xy": rast.region("xy", torch.float32, 2 * U).view(-1, 2)[u0:u0 + n],
+        "depth": rast.region("depth", torch.float32, U)[u0:u0 + n],
+        "conic_o": rast.region("conic_o", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n],
+        "rgb": rast.region("rgb", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n],
+        "radius": rast.region("radius", torch.float32, U)[u0:u0 + n],
+        "tiles_touched": rast.region("tiles_touched", torch.int32, U)[u0:u0 + n],
+    }
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def sorted_pairs(rast):
+    """(keys uint64, vals uint32, ranges [tiles,2], pair_count, status) after bin_sort."""
+    torch.cuda.synchronize()
+    P = int(rast.pair_count.item())
+    plan = rast.region("plan", torch.int32, 64).cpu().numpy()
+    fin = int(plan[63])
+    cap = rast.pair_capacity
+    Pe = min(P, cap)
+    keys = rast.region("keys", torch.int64, cap, fin)[:Pe].cpu().numpy().view(np.uint64)
+    vals = rast.region("vals", torch.int32, cap, fin)[:Pe].cpu().numpy().view(np.uint32)
+    ranges = rast.region("ranges", torch.int32, 2 * rast.layout.tiles).view(-1, 2).cpu().numpy()
+    status = flod.flod_read_status(rast.ws)
+    return keys, vals, ranges.astype(np.int64), P, status
+
+
+def image_compare(gpu_img: np.ndarray, ref_img: np.ndarray):
+    """Returns (fraction of pixels within IMG_MAX_ABS, per-channel mean abs error)."""
+    d = np.abs(gpu_img.astype(np.float64) - ref_img)
+    per_pixel = d.max(axis=0)
+    return float((per_pixel <= IMG_MAX_ABS).mean()), d.reshape(3, -1).mean(axis=1)
+
+
+def assert_image_close(gpu_img, ref_img):
+    frac, mean = image_compare(gpu_img, ref_img)
+    assert frac >= IMG_FRAC, f"only {frac:.5f} of pixels within {IMG_MAX_ABS}"
+    assert np.all(mean <= IMG_MEAN_ABS), f"mean abs error per channel {mean}"
+
+
+def rect_boundary_distance(u, v, r):
+    """FP64 distance of the four rectangle edges (u +- r - 0.5, v +- r - 0.5) to the nearest
+    integer: the decisions a float32 pipeline may take differently."""
+    u, v, r = (np.asarray(a, dtype=np.float64) for a in (u, v, r))
+    ds = []
+    for c in (u, v):
+        for s in (-1.0, 1.0):
+            x = c + s * r - 0.5
+            ds.append(np.abs(x - np.round(x)))
+    return np.minimum.reduce(ds)
+
+
+def oracle_units_f32(pre, cam, ocfg):
+    """The oracle's FP64 preprocess rounded to float32, with tiles_touched decided in float32
+    by the same rectangle rule (so an integer stage fed with it has one exact answer)."""
+    valid = pre["valid"].numpy()
+    u = pre["mean2d"][:, 0].detach().numpy().astype(np.float32)
+    v = pre["mean2d"][:, 1].detach().numpy().astype(np.float32)
+    r = pre["radius"].numpy().astype(np.float32)
+    u, v, r = (np.where(valid, a, np.float32(0)) for a in (u, v, r))
+    px = OP.pixel_rect_f32(u, v, r, cam["width"], cam["height"])
+    tr = OP.tile_rect(px, ocfg.tile_w, ocfg.tile_h, valid)
+    return {"u": u, "v": v, "r": r, "depth": pre["depth"].detach().numpy().astype(np.float32),
+            "conic": pre["conic"].detach().numpy().astype(np.float32),
+            "opacity": pre["opacity"].detach().numpy().astype(np.float32),
+            "rgb": pre["rgb"].detach().numpy().astype(np.float32),
+            "valid": valid & (tr[4] > 0), "tile_rect": tr[:4], "tiles_touched": tr[4]}
+
+
+def inject_units(rast, view: int, f: dict):
+    """Write oracle-made per-unit values into the workspace of a view."""
+    n = f["u"].shape[0]
+    u0 = rast.unit_off[view]
+    U = rast.layout.units
+    dev = rast.ws.device
+    xy = np.stack([f["u"], f["v"]], 1).astype(np.float32)
+    rast.region("xy", torch.float32, 2 * U).view(-1, 2)[u0:u0 + n] = torch.as_tensor(xy, device=dev)
+    rast.region("depth", torch.float32, U)[u0:u0 + n] = torch.as_tensor(f["depth"], device=dev)
+    rast.region("radius", torch.float32, U)[u0:u0 + n] = torch.as_tensor(f["r"], device=dev)
+    tt = np.where(f["valid"], f["tiles_touched"], 0).astype(np.int32)
+    rast.region("tiles_touched", torch.int32, U)[u0:u0 + n] = torch.as_tensor(tt, device=dev)
+    if "conic" in f:
+        co = np.concatenate([f["conic"], f["opacity"][:, None]], 1).astype(np.float32)
+        rast.region("conic_o", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n] = torch.as_tensor(co, device=dev)
+        rgb = np.concatenate([f["rgb"], np.zeros((n, 1), np.float32)], 1)
+        rast.region("rgb", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n] = torch.as_tensor(rgb, device=dev)
+
+
+def clear_units(rast):
+    U = rast.layout.units
+    rast.region("tiles_touched", torch.int32, U).zero_()

@@ -1,0 +1,74 @@
+"""GPU backward (blend backward + preprocess backward, behind torch.autograd) vs the
+oracle's analytic gradient (autograd of the FP64 forward, itself pinned to central finite
+differences in test_oracle_raster)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import GRAD_REL, rasterizer
+from oracle import raster as R
+from paper_2408_12894_gb300 import flod, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_grads(g, cams, s_min, dL, cfg=None):
+    rast = rasterizer([g], cams, [s_min], cfg=cfg)
+    for f in flod.GaussianSet.FIELDS:
+        getattr(rast.sets[0], f).requires_grad_(True)
+    rgb, T, nc = flod.rasterize(rast)
+    (rgb * torch.as_tensor(dL, device=rgb.device)).sum().backward()
+    out = {f: getattr(rast.sets[0], f).grad.cpu().numpy().astype(np.float64)
+           for f in flod.GaussianSet.FIELDS}
+    assert flod.flod_read_status(rast.ws) == 0
+    return out, rgb.detach().cpu().numpy()
+
+
+def _oracle_grads(g, cams, s_min, dL, cfg=R.Config()):
+    tot = None
+    off = 0
+    for c in cams:
+        n = 3 * c["width"] * c["height"]
+        go = dL[off:off + n].reshape(3, c["height"], c["width"]).astype(np.float64)
+        off += n
+        _, _, _, gr = R.forward_backward(g, g["sh_degree"], s_min, c, cfg, go)
+        tot = gr if tot is None else {k: tot[k] + gr[k] for k in tot}
+    return tot
+
+
+def _compare(got, ref):
+    names = {"means": "means", "quats": "quats", "s_opt": "s_opt",
+             "opacity_logit": "opacity_logit", "sh": "sh"}
+    for k in names:
+        a, b = got[k].reshape(-1), ref[k].reshape(-1)
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel <= GRAD_REL, f"{k}: relative L2 error {rel:.2e}"
+
+
+@pytest.mark.parametrize("views", [1, 2])
+def test_backward_matches_oracle(views):
+    g = synth.gaussian_set(9, 2500, k=8, radius=1.0, sh_degree=3, s_mean=-3.0)
+    cams = [synth.camera((0.4, 0.2, -3.0), 96, 72), synth.camera((-2.0, 0.5, -2.2), 80, 80)][:views]
+    s_min = 0.01
+    dL = synth.upstream_gradient(11, cams)
+    got, _ = _gpu_grads(g, cams, s_min, dL)
+    ref = _oracle_grads(g, cams, s_min, dL)
+    _compare(got, ref)
+
+
+def test_backward_small_tiles_and_batches():
+    g = synth.gaussian_set(10, 1500, k=4, radius=1.0, sh_degree=2, s_mean=-2.7)
+    cams = [synth.camera((0.1, -0.3, -2.8), 72, 56)]
+    dL = synth.upstream_gradient(12, cams)
+    cfg = flod.default_config(tile_w=8, tile_h=8, batch=32)
+    got, _ = _gpu_grads(g, cams, 0.0, dL, cfg)
+    ref = _oracle_grads(g, cams, 0.0, dL, R.Config(tile_w=8, tile_h=8))
+    _compare(got, ref)
+
+
+def test_backward_zero_upstream_gives_zero():
+    g = synth.gaussian_set(11, 500, sh_degree=1)
+    cams = [synth.camera((0.0, 0.0, -3.0), 64, 64)]
+    got, _ = _gpu_grads(g, cams, 0.0, np.zeros(3 * 64 * 64, np.float32))
+    for v in got.values():
+        assert np.all(v == 0)
