@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kSortThreads) k_pass(Ws ws, int pass) {
             set_status(ws.status, FLOD_DEV_TIMEOUT);
             break;
           }
+          if (spins > 32) __nanosleep(64);
           continue;
         }
         excl += w & kValMask;

@@ -26,15 +26,15 @@ def _stage_render(g, cam, cfg, s_min=0.0):
     ocfg = oracle_cfg(cfg)
     pre = oracle_pre(g, s_min, cam, ocfg)
     f = oracle_units_f32(pre, cam, ocfg)
-    rast = rasterizer([g], [cam], [s_min], cfg=cfg)
-    clear_units(rast)
-    inject_units(rast, 0, f)
     tx = -(-cam["width"] // cfg.tile_w)
     ty = -(-cam["height"] // cfg.tile_h)
     tt = np.where(f["valid"], f["tiles_touched"], 0)
     k, v = R.bin_pairs(f["tile_rect"], tt, f["depth"], tx, tx * ty)
     k, v = R.sort_pairs(k, v)
     rg = R.tile_ranges(k, tx * ty)
+    rast = rasterizer([g], [cam], [s_min], cfg=cfg, pair_capacity=max(k.size, 1024))
+    clear_units(rast)
+    inject_units(rast, 0, f)
     _inject_lists(rast, k, v, rg)
     rgb, T, nc = rast.new_outputs()
     rast.render_fwd(rgb, T, nc)
