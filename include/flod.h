@@ -223,6 +223,31 @@ flod_status flod_select_levels(const flod_gaussians *levels, int n_levels, const
                                uint32_t *out_sel, uint32_t sel_capacity, uint32_t *d_count,
                                void *scratch, size_t scratch_bytes, flod_stream stream);
 
+/* flod_select_levels without caller-provided scratch (no counterpart in the paper: this
+ * is a deployment variant). Some callers cannot allocate device memory at all: a plugin
+ * running inside a host application that owns every device allocation through its own
+ * pool, or a real-time loop that must not take cudaMalloc's device-wide synchronisation
+ * and latency. This entry point allocates nothing: the per-block counts that
+ * flod_select_levels keeps in `scratch` live instead in a fixed array of
+ * FLOD_SELECT_NOALLOC_MAX_BLOCKS + 1 uint32 words (64 KiB + 4 bytes) compiled into the
+ * library, which every GPU that loads the library holds until the process exits. The
+ * caller still provides out_sel and d_count; arguments and results are those of
+ * flod_select_levels.
+ * - Limit: sum over levels of ceil(n / 2048) <= FLOD_SELECT_NOALLOC_MAX_BLOCKS (at most
+ *   2^25 = 33,554,432 Gaussians over all levels); larger inputs are rejected with
+ *   FLOD_ERR_INVALID_ARG before anything is enqueued.
+ * - The first call on a device looks up the array's device address (with that device
+ *   current) and caches it; make that first call before any stream capture.
+ * - Every call on a device shares the one array and leaves its contents behind. Nothing in
+ *   it needs to start at zero (each call writes every word it reads), but two calls whose
+ *   work overlaps on the GPU (other streams, other threads) race on it: order them. */
+#define FLOD_SELECT_NOALLOC_MAX_BLOCKS 16384
+flod_status flod_select_levels_noalloc(const flod_gaussians *levels, int n_levels,
+                                       const float *d_thresh, float gamma, float focal,
+                                       const float origin[3], uint32_t *out_sel,
+                                       uint32_t sel_capacity, uint32_t *d_count,
+                                       flod_stream stream);
+
 /* Eq. 5: s_opt <- log(exp(s_opt) + s_min_cur - s_min_next) in place, so that the scale of
  * Eq. 4 at the next level equals the current one. Requires s_min_cur >= s_min_next. */
 flod_status flod_adjust_scale(float *s_opt, int64_t n, float s_min_cur, float s_min_next,

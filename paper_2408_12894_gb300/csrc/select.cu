@@ -6,6 +6,8 @@
 // difference, square and sum rounded to nearest, then a correctly rounded square root), so
 // that the decision is reproducible by any float32 implementation. Three launches: per-block
 // counts, one-CTA scan of the counts, ordered write. The output is in (level, index) order.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -182,3 +184,55 @@ cudaError_t launch_adjust_scale(float* s_opt, int64_t n, float s_cur, float s_ne
 }
 
 }  // namespace flod
+
+// ---------------------------------------------------------------------------------------
+// allocation-free variant of the selection: the block-count scratch is a fixed array in
+// the library's device image instead of caller memory
+// ---------------------------------------------------------------------------------------
+static __device__ __align__(256) uint32_t g_select_scratch[FLOD_SELECT_NOALLOC_MAX_BLOCKS + 1];
+
+namespace {
+std::mutex g_scratch_mu;
+bool g_scratch_ready[64];
+void* g_scratch_ptr[64];
+
+// Device address of g_select_scratch for the current device (looked up once per device,
+// with that device current). In host code the array's name is only a host-side stand-in.
+cudaError_t static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ready[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_select_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+    g_scratch_ready[dev] = true;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" flod_status flod_select_levels_noalloc(const flod_gaussians* levels, int n_levels,
+                                                  const float* d_thresh, float gamma,
+                                                  float focal, const float origin[3],
+                                                  uint32_t* out_sel, uint32_t sel_capacity,
+                                                  uint32_t* d_count, flod_stream stream) {
+  if (!levels || n_levels < 1 || n_levels > FLOD_MAX_SETS) return FLOD_ERR_INVALID_ARG;
+  int ns[FLOD_MAX_SETS];
+  for (int l = 0; l < n_levels; ++l) {
+    if (levels[l].n < 0 || levels[l].n >= (1 << FLOD_SEL_SHIFT)) return FLOD_ERR_INVALID_ARG;
+    ns[l] = levels[l].n;
+  }
+  // too many Gaussians for the fixed scratch: refuse before anything is enqueued
+  if (flod::select_blocks(ns, n_levels) > (uint32_t)FLOD_SELECT_NOALLOC_MAX_BLOCKS)
+    return FLOD_ERR_INVALID_ARG;
+  void* scratch = nullptr;
+  if (static_scratch(&scratch) != cudaSuccess) return FLOD_ERR_CUDA;
+  return flod_select_levels(levels, n_levels, d_thresh, gamma, focal, origin, out_sel,
+                            sel_capacity, d_count, scratch,
+                            sizeof(uint32_t) * (FLOD_SELECT_NOALLOC_MAX_BLOCKS + 1), stream);
+}

@@ -100,13 +100,15 @@ def lib() -> C.CDLL:
         L.flod_select_scratch_size.restype = SZ
         L.flod_select_levels.argtypes = [P, I, P, C.c_float, C.c_float, P, P, C.c_uint32, P, P,
                                          SZ, P]
+        L.flod_select_levels_noalloc.argtypes = [P, I, P, C.c_float, C.c_float, P, P,
+                                                 C.c_uint32, P, P]
         L.flod_adjust_scale.argtypes = [P, C.c_int64, C.c_float, C.c_float, P]
         L.flod_read_status.argtypes = [P, P, P]
         L.flod_status_string.argtypes = [I]
         L.flod_status_string.restype = C.c_char_p
         for name in ("flod_workspace_layout", "flod_preprocess", "flod_bin_sort",
                      "flod_render_fwd", "flod_render_bwd", "flod_blend_bwd",
-                     "flod_preprocess_bwd", "flod_select_levels",
+                     "flod_preprocess_bwd", "flod_select_levels", "flod_select_levels_noalloc",
                      "flod_adjust_scale", "flod_read_status"):
             getattr(L, name).restype = I
         _lib = L
@@ -274,6 +276,29 @@ def flod_select_levels(levels, origin, out_sel: torch.Tensor, d_count: torch.Ten
     _check(lib().flod_select_levels(arr, len(levels), th, gamma, focal, org, out_sel.data_ptr(),
                                     out_sel.numel(), d_count.data_ptr(), scratch.data_ptr(),
                                     scratch.numel(), _stream(stream)), "flod_select_levels")
+
+
+SELECT_NOALLOC_MAX_BLOCKS = 16384
+
+
+def flod_select_levels_noalloc(levels, origin, out_sel: torch.Tensor, d_count: torch.Tensor,
+                               d_thresh=None, gamma: float = 1.0, focal: float = 0.0,
+                               stream=None):
+    """flod_select_levels for callers that cannot allocate device memory: the library's own
+    fixed scratch replaces the caller's (at most 2^25 Gaussians over all levels; calls that
+    overlap on the GPU race on that scratch). The first call on a device looks the scratch up;
+    make it before any stream capture."""
+    arr = _array(Gaussians, [g.struct() if isinstance(g, GaussianSet) else g for g in levels])
+    blocks = sum(-(-int(g.n) // 2048) for g in arr)
+    if blocks > SELECT_NOALLOC_MAX_BLOCKS:
+        raise FlodError(f"flod_select_levels_noalloc: {blocks} blocks of 2048 Gaussians exceed the "
+                        f"fixed scratch ({SELECT_NOALLOC_MAX_BLOCKS} blocks)")
+    th = None if d_thresh is None else _array(C.c_float, [float(x) for x in d_thresh])
+    org = _array(C.c_float, [float(x) for x in origin])
+    _check(lib().flod_select_levels_noalloc(arr, len(levels), th, gamma, focal, org,
+                                            out_sel.data_ptr(), out_sel.numel(),
+                                            d_count.data_ptr(), _stream(stream)),
+           "flod_select_levels_noalloc")
 
 
 def flod_adjust_scale(s_opt: torch.Tensor, s_min_cur: float, s_min_next: float, stream=None):
