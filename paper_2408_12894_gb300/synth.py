@@ -210,7 +210,7 @@ def camera_path(seed: int = 3, n_frames: int = 32, width: int = 1920, height: in
 
 
 def batched_jobs(seed: int = 4, n_cams: int = 64, n_levels: int = 5, radius: float = 40.0,
-                 selective_radius: float = 200.0):
+                 selective_radius: float = 120.0):
     """The batched multi-view mix: for each camera a resolution drawn uniformly from
     BATCH_RESOLUTIONS and a job drawn uniformly from {level 1..n_levels, selective}
     (job index n_levels means selective). Positions uniform on a sphere of ``radius``
