@@ -82,13 +82,24 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
   }
 }
 
+// One CTA per 1024 units. The CTA scans its units' pair counts, stores each unit's tile
+// rectangle and depth bits in shared memory, then its threads walk the CTA's contiguous
+// range of output positions: position p belongs to the unit whose prefix range holds it
+// (binary search), and its tile is the (p - start)-th tile of that unit's rectangle in
+// row-major order. Writes are coalesced and a unit with thousands of tiles is spread over
+// the whole CTA.
 template <int MAXV>
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  __shared__ uint32_t s_pre[kScanBlock + 1];
+  __shared__ uint32_t s_rect[kScanBlock];     // tx0 | (rect width << 16)
+  __shared__ uint32_t s_row[kScanBlock];      // ty0
+  __shared__ uint32_t s_depth[kScanBlock];
   __shared__ uint32_t warp_tot[8];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t unit0 = blockIdx.x * (uint32_t)kScanBlock;
   const ViewP& V = b.views[view_of_unit(b, unit0)];
   const uint4 tt = reinterpret_cast<const uint4*>(ws.tiles_touched)[blockIdx.x * 256u + tid];
+  const uint32_t cnt[4] = {tt.x, tt.y, tt.z, tt.w};
   const uint32_t s = tt.x + tt.y + tt.z + tt.w;
   uint32_t x = s;
 #pragma unroll
@@ -98,33 +109,47 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
   }
   if (lane == 31) warp_tot[wid] = x;
   __syncthreads();
-  uint32_t wpre = 0;
-  for (int w = 0; w < wid; ++w) wpre += warp_tot[w];
-  unsigned long long pos = ws.block_sums[blockIdx.x] + wpre + x - s;
-  const uint32_t cnt[4] = {tt.x, tt.y, tt.z, tt.w};
+  uint32_t run = 0;
+  for (int w = 0; w < wid; ++w) run += warp_tot[w];
+  run += x - s;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int ul = 4 * tid + j;
+    s_pre[ul] = run;
+    if (cnt[j]) {
+      const uint32_t u = unit0 + ul;
+      const float2 xy = ws.xy[u];
+      int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+      tile_rect(xy.x, xy.y, ws.radius[u], V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0, tx1,
+                ty0, ty1);
+      s_rect[ul] = (uint32_t)tx0 | ((uint32_t)(tx1 - tx0 + 1) << 16);
+      s_row[ul] = (uint32_t)ty0;
+      s_depth[ul] = __float_as_uint(ws.depth[u]);
+    }
+    run += cnt[j];
+  }
+  if (tid == 255) s_pre[kScanBlock] = run;
+  __syncthreads();
+  const uint32_t total = s_pre[kScanBlock];
+  const unsigned long long base = ws.block_sums[blockIdx.x];
   const unsigned long long cap = ws.pair_capacity;
   unsigned long long* keys = ws.keys[0];
   uint32_t* vals = ws.vals[0];
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t n = cnt[j];
-    if (n == 0) continue;
-    const uint32_t u = unit0 + 4u * tid + j;
-    const float2 xy = ws.xy[u];
-    const float r = ws.radius[u];
-    const unsigned long long dbits = __float_as_uint(ws.depth[u]);
-    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-    tile_rect(xy.x, xy.y, r, V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0, tx1, ty0, ty1);
-    uint32_t k = 0;
-    for (int ty = ty0; ty <= ty1 && k < n; ++ty) {
-      const unsigned long long rowkey = (unsigned long long)(V.tile_off + (uint32_t)ty * V.tiles_x);
-      for (int tx = tx0; tx <= tx1 && k < n; ++tx, ++k) {
-        const unsigned long long p = pos + k;
-        if (p >= cap) break;
-        keys[p] = ((rowkey + (unsigned long long)tx) << 32) | dbits;
-        vals[p] = u;
-      }
+  for (uint32_t p = tid; p < total; p += 256) {
+    if (base + p >= cap) break;
+    int lo = 0, hi = kScanBlock - 1;          // last unit with s_pre[u] <= p
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_pre[mid] <= p) lo = mid; else hi = mid - 1;
     }
-    pos += n;
+    const uint32_t k = p - s_pre[lo];
+    const uint32_t r = s_rect[lo];
+    const uint32_t w = r >> 16;
+    const uint32_t tx = (r & 0xffffu) + k % w;
+    const uint32_t ty = s_row[lo] + k / w;
+    const unsigned long long tile = (unsigned long long)(V.tile_off + ty * V.tiles_x + tx);
+    keys[base + p] = (tile << 32) | s_depth[lo];
+    vals[base + p] = unit0 + (uint32_t)lo;
   }
 }
 

@@ -116,43 +116,101 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-template <int MAXV>
-__global__ void __launch_bounds__(256) k_render_bwd(const __grid_constant__ Batch<MAXV> b, Ws ws,
-                                                    const float* __restrict__ dL,
-                                                    const float* __restrict__ fwd_T,
-                                                    const uint32_t* __restrict__ fwd_nc) {
+// Sums nine per-lane values over the warp and adds each total to its slot of a unit's
+// 2D-gradient record (du, dv, dop | da, db, dc | dr, dg, db). A transposing butterfly: at
+// each shuffle distance a lane keeps one half of its values, sends the other half to its
+// partner and adds what it receives, so after distances 16, 8, 4, 2 every lane holds one
+// partial sum; distance 1 completes it. 12 shuffles instead of 45.
+__device__ __forceinline__ void warp_reduce_add9(float (&v)[9], float4* rec) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float w[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {                 // 10 slots (slot 9 is empty) -> 5
+    const float lo = v[i], hi = i < 4 ? v[5 + i] : 0.f;
+    const float send = b4 ? lo : hi;
+    w[i] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float x[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {                 // 6 slots (slot 5 empty) -> 3
+    const float lo = w[i], hi = i < 2 ? w[3 + i] : 0.f;
+    const float send = b3 ? lo : hi;
+    x[i] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float y[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {                 // 4 slots (slot 3 empty) -> 2
+    const float lo = x[i], hi = i < 1 ? x[2 + i] : 0.f;
+    const float send = b2 ? lo : hi;
+    y[i] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  float z;
+  {
+    const float send = b1 ? y[0] : y[1];
+    z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+  // which of the nine values this lane now holds
+  const int i3 = (b2 ? 2 : 0) + (b1 ? 1 : 0);   // index into x (valid < 3)
+  const int i2 = (b3 ? 3 : 0) + i3;             // index into w (valid < 5)
+  const int i1 = (b4 ? 5 : 0) + i2;             // original index (valid < 9)
+  if ((lane & 1) == 0 && i3 < 3 && i2 < 5 && i1 < 9 && z != 0.f)
+    atomicAdd(reinterpret_cast<float*>(rec) + i1 + i1 / 3, z);
+}
+
+// PIX pixels per thread, stacked vertically: thread t owns column t % tile_w and rows
+// (t / tile_w) * PIX + j.
+template <int MAXV, int PIX>
+__global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant__ Batch<MAXV> b,
+                                                          Ws ws, const float* __restrict__ dL,
+                                                          const float* __restrict__ fwd_T,
+                                                          const uint32_t* __restrict__ fwd_nc) {
   __shared__ uint32_t s_id[256];
   __shared__ float2 s_xy[256];
   __shared__ float4 s_co[256];
   __shared__ float4 s_rgb[256];
   __shared__ uint32_t s_max;
   const uint32_t tile = blockIdx.x;
-  int vi, px, py;
-  tile_pixel(b, tile, vi, px, py);
+  const int vi = view_of_tile(b, tile);
   const ViewP& V = b.views[vi];
-  const int nthr = blockDim.x;
+  const uint32_t lt = tile - V.tile_off;
+  const int tw = b.cfg.tile_w;
   const int tid = threadIdx.x;
-  const bool inside = px < V.width && py < V.height;
+  const int nthr = blockDim.x;
+  const int px = (int)(lt % V.tiles_x) * tw + tid % tw;
+  const int py0 = (int)(lt / V.tiles_x) * b.cfg.tile_h + (tid / tw) * PIX;
   const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
   const uint2 rg = ws.ranges[tile];
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const float fx = (float)px + 0.5f;
   const int batch = b.cfg.batch;
   const uint64_t npix = (uint64_t)V.width * V.height;
-  const uint64_t p = inside ? (uint64_t)py * V.width + px : 0;
-  float T = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  uint32_t last = 0;
-  if (inside) {
-    T = fwd_T[V.pix_off + p];
-    last = fwd_nc[V.pix_off + p];
-    g0 = dL[3 * V.pix_off + p];
-    g1 = dL[3 * V.pix_off + npix + p];
-    g2 = dL[3 * V.pix_off + 2 * npix + p];
+  float T[PIX], g0[PIX], g1[PIX], g2[PIX], S0[PIX], S1[PIX], S2[PIX], fy[PIX];
+  uint32_t last[PIX];
+  uint32_t my_max = 0, evals = 0;
+#pragma unroll
+  for (int j = 0; j < PIX; ++j) {
+    const int py = py0 + j;
+    fy[j] = (float)py + 0.5f;
+    T[j] = g0[j] = g1[j] = g2[j] = 0.f;
+    last[j] = 0;
+    if (px < V.width && py < V.height) {
+      const uint64_t p = (uint64_t)py * V.width + px;
+      T[j] = fwd_T[V.pix_off + p];
+      last[j] = fwd_nc[V.pix_off + p];
+      g0[j] = dL[3 * V.pix_off + p];
+      g1[j] = dL[3 * V.pix_off + npix + p];
+      g2[j] = dL[3 * V.pix_off + 2 * npix + p];
+    }
+    S0[j] = T[j] * b.cfg.bg[0];
+    S1[j] = T[j] * b.cfg.bg[1];
+    S2[j] = T[j] * b.cfg.bg[2];
+    my_max = max(my_max, last[j]);
+    evals += last[j];
   }
-  const float Tf = T;
-  float S0 = Tf * b.cfg.bg[0], S1 = Tf * b.cfg.bg[1], S2 = Tf * b.cfg.bg[2];
   if (tid == 0) s_max = 0;
   __syncthreads();
-  if (last) atomicMax(&s_max, last);
+  if (my_max) atomicMax(&s_max, my_max);
   __syncthreads();
   const uint32_t end = rg.x + s_max;
   for (uint32_t bend = end; bend > rg.x;) {
@@ -171,60 +229,49 @@ __global__ void __launch_bounds__(256) k_render_bwd(const __grid_constant__ Batc
       const uint32_t pos = bstart - rg.x + (uint32_t)k + 1u;
       const float2 m = s_xy[k];
       const float4 co = s_co[k];
-      const float dx = fx - m.x, dy = fy - m.y;
-      float gg = 0.f, a = 0.f;
-      bool on = inside && pos <= last;
-      if (on) {
-        a = splat_alpha(dx, dy, co, gg);
-        on = a >= kAlphaMin;
-      }
-      float du = 0.f, dv = 0.f, dop = 0.f, dca = 0.f, dcb = 0.f, dcc = 0.f;
-      float dr = 0.f, dg = 0.f, dbl = 0.f;
-      if (on) {
-        const float4 c = s_rgb[k];
-        const float om = 1.f - a;
-        T = T / om;
-        const float w = a * T;
-        dr = w * g0;
-        dg = w * g1;
-        dbl = w * g2;
-        const float ioma = 1.f / om;
-        const float dalpha = g0 * (c.x * T - S0 * ioma) + g1 * (c.y * T - S1 * ioma) +
-                             g2 * (c.z * T - S2 * ioma);
-        S0 += c.x * w;
-        S1 += c.y * w;
-        S2 += c.z * w;
+      const float dx = fx - m.x;
+      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool any = false;
+      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+      bool have_c = false;
+#pragma unroll
+      for (int j = 0; j < PIX; ++j) {
+        if (pos > last[j]) continue;
+        const float dy = fy[j] - m.y;
+        float gg;
+        const float a = splat_alpha(dx, dy, co, gg);
+        if (a < kAlphaMin) continue;
+        if (!have_c) {
+          c = s_rgb[k];
+          have_c = true;
+        }
+        any = true;
+        const float ioma = __frcp_rn(1.f - a);
+        T[j] *= ioma;
+        const float w = a * T[j];
+        acc[6] += w * g0[j];
+        acc[7] += w * g1[j];
+        acc[8] += w * g2[j];
+        const float dalpha = g0[j] * (c.x * T[j] - S0[j] * ioma) + g1[j] * (c.y * T[j] - S1[j] * ioma) +
+                             g2[j] * (c.z * T[j] - S2[j] * ioma);
+        S0[j] += c.x * w;
+        S1[j] += c.y * w;
+        S2[j] += c.z * w;
         if (co.w * gg < kAlphaMax) {
-          dop = gg * dalpha;
+          acc[2] += gg * dalpha;
           const float dq = -0.5f * co.w * gg * dalpha;   // dL/dq
-          dca = dq * dx * dx;
-          dcb = dq * 2.f * dx * dy;
-          dcc = dq * dy * dy;
-          du = -dq * 2.f * (co.x * dx + co.y * dy);
-          dv = -dq * 2.f * (co.y * dx + co.z * dy);
+          acc[3] += dq * dx * dx;
+          acc[4] += dq * 2.f * dx * dy;
+          acc[5] += dq * dy * dy;
+          acc[0] -= dq * 2.f * (co.x * dx + co.y * dy);
+          acc[1] -= dq * 2.f * (co.y * dx + co.z * dy);
         }
       }
-      if (__any_sync(0xffffffffu, on)) {
-        du = warp_sum(du);
-        dv = warp_sum(dv);
-        dop = warp_sum(dop);
-        dca = warp_sum(dca);
-        dcb = warp_sum(dcb);
-        dcc = warp_sum(dcc);
-        dr = warp_sum(dr);
-        dg = warp_sum(dg);
-        dbl = warp_sum(dbl);
-        if ((tid & 31) == 0) {
-          float4* gp = ws.grad2d + 3ull * s_id[k];
-          atomicAdd(gp, make_float4(du, dv, dop, 0.f));
-          atomicAdd(gp + 1, make_float4(dca, dcb, dcc, 0.f));
-          atomicAdd(gp + 2, make_float4(dr, dg, dbl, 0.f));
-        }
-      }
+      if (__any_sync(0xffffffffu, any)) warp_reduce_add9(acc, ws.grad2d + 3ull * s_id[k]);
     }
     bend = bstart;
   }
-  add_evals(ws.plan + kPlanEvalBwd, last);
+  add_evals(ws.plan + kPlanEvalBwd, evals);
 }
 
 template <int MAXV>
@@ -244,7 +291,11 @@ cudaError_t launch_render_bwd(const Batch<MAXV>& b, const Ws& ws, const float* d
   (void)resident;
   (void)persistent;
   if (b.tiles == 0) return cudaSuccess;
-  k_render_bwd<MAXV><<<b.tiles, b.cfg.tile_w * b.cfg.tile_h, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
+  const int px = b.cfg.tile_w * b.cfg.tile_h;
+  if (px >= 128)
+    k_render_bwd<MAXV, 4><<<b.tiles, px / 4, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
+  else
+    k_render_bwd<MAXV, 2><<<b.tiles, px / 2, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
   return cudaGetLastError();
 }
 
