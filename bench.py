@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="flod", choices=["flod", "reference"])
     ap.add_argument("--small", action="store_true", help="300k-Gaussian level (smoke runs)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="multiply every level count (profiling cases; not a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -56,15 +58,16 @@ def parse():
 # workload
 # ---------------------------------------------------------------------------------------
 
-def level_counts(small: bool):
+def level_counts(small: bool, scale: float = 1.0):
     from paper_2408_12894_gb300 import synth
-    return (2_000, 8_000, 30_000, 100_000, 300_000) if small else synth.LEVEL_COUNTS
+    base = (2_000, 8_000, 30_000, 100_000, 300_000) if small else synth.LEVEL_COUNTS
+    return tuple(int(round(c * scale)) for c in base)
 
 
-def make_level(small: bool):
+def make_level(small: bool, scale: float = 1.0):
     """Numpy arrays of the finest level (s_opt as drawn: Eq. 5 is applied on the device)."""
     from paper_2408_12894_gb300 import synth
-    levels = synth.level_scene(counts=level_counts(small))
+    levels = synth.level_scene(counts=level_counts(small, scale))
     return levels[-1][0]
 
 
@@ -191,8 +194,8 @@ def run_reference(a):
         return
     import torch
     from paper_2408_12894_gb300 import synth
-    g = make_level(a.small)
-    g["s_opt"] = adjust_chain_numpy(g["s_opt"], level_counts(a.small))
+    g = make_level(a.small, a.scale)
+    g["s_opt"] = adjust_chain_numpy(g["s_opt"], level_counts(a.small, a.scale))
     cam = synth.level_camera()
     ost = OracleStep(g, cam, synth.LEVEL_SMIN[-1], slice_n=20_000, tiles=3)
     for _ in range(a.warmup):
@@ -241,8 +244,8 @@ def run_flod(a):
         dist.init_process_group("nccl")
     from paper_2408_12894_gb300 import _build, flod, synth
     _build.build()
-    counts = level_counts(a.small)
-    g = make_level(a.small)
+    counts = level_counts(a.small, a.scale)
+    g = make_level(a.small, a.scale)
     gs = flod.GaussianSet.from_numpy(g, synth.LEVEL_SMIN[-1])
     for l in range(4):   # level-by-level initialisation (Eq. 5), on the device
         flod.flod_adjust_scale(gs.s_opt[:counts[l]], synth.LEVEL_SMIN[l], synth.LEVEL_SMIN[l + 1])

@@ -122,6 +122,7 @@ typedef struct {
   size_t radius;        /* float [units] extent radius in pixels */
   size_t tiles_touched; /* uint32 [units], 0 when culled */
   size_t block_sums;    /* uint64 [units/1024 + 1] exclusive pair offsets per 1024 units */
+  size_t slices;        /* uint32 [units/1024 + 1] exclusive count of 4096-pair emission slices */
   size_t keys[2];       /* uint64 [pair_capacity] x 2 (emission buffer is keys[0]) */
   size_t vals[2];       /* uint32 [pair_capacity] x 2 */
   size_t hist;          /* radix-sort digit histograms */

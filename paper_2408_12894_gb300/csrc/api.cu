@@ -150,6 +150,7 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   L.radius = take(4 * u);
   L.tiles_touched = take(4 * u);
   L.block_sums = take(8 * (u / kScanBlock + 1));
+  L.slices = take(4 * (u / kScanBlock + 1));
   L.keys[0] = take(8 * pair_capacity);
   L.keys[1] = take(8 * pair_capacity);
   L.vals[0] = take(4 * pair_capacity);
@@ -181,6 +182,7 @@ Ws ws_ptrs(void* base, const Plan& P) {
   w.radius = reinterpret_cast<float*>(b + L.radius);
   w.tiles_touched = reinterpret_cast<uint32_t*>(b + L.tiles_touched);
   w.block_sums = reinterpret_cast<unsigned long long*>(b + L.block_sums);
+  w.slices = reinterpret_cast<uint32_t*>(b + L.slices);
   for (int i = 0; i < 2; ++i) {
     w.keys[i] = reinterpret_cast<unsigned long long*>(b + L.keys[i]);
     w.vals[i] = reinterpret_cast<uint32_t*>(b + L.vals[i]);

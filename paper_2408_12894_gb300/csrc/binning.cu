@@ -32,36 +32,63 @@ __global__ void __launch_bounds__(256) k_block_sums(const uint32_t* __restrict__
 __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
                                                       unsigned long long* user_count) {
   __shared__ unsigned long long warp_tot[32];
+  __shared__ uint32_t warp_sl[32];
   __shared__ unsigned long long carry_s;
+  __shared__ uint32_t carry_sl;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) carry_s = 0;
+  if (tid == 0) {
+    carry_s = 0;
+    carry_sl = 0;
+  }
   __syncthreads();
   for (uint32_t base = 0; base < nblocks; base += 1024) {
     const uint32_t i = base + tid;
     unsigned long long v = i < nblocks ? ws.block_sums[i] : 0ull;
+    const uint32_t sl = (uint32_t)((v + kEmitSlice - 1) / kEmitSlice);   // emission slices
     unsigned long long x = v;
+    uint32_t xs = sl;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      uint32_t ys = __shfl_up_sync(0xffffffffu, xs, o);
+      if (lane >= o) {
+        x += y;
+        xs += ys;
+      }
     }
-    if (lane == 31) warp_tot[wid] = x;
+    if (lane == 31) {
+      warp_tot[wid] = x;
+      warp_sl[wid] = xs;
+    }
     __syncthreads();
     if (wid == 0) {
       unsigned long long w = warp_tot[lane];
+      uint32_t ws_ = warp_sl[lane];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
+        uint32_t ys = __shfl_up_sync(0xffffffffu, ws_, o);
+        if (lane >= o) {
+          w += y;
+          ws_ += ys;
+        }
       }
       warp_tot[lane] = w;   // inclusive over warps
+      warp_sl[lane] = ws_;
     }
     __syncthreads();
     const unsigned long long carry = carry_s;
     const unsigned long long excl = carry + (wid ? warp_tot[wid - 1] : 0ull) + x - v;
-    if (i < nblocks) ws.block_sums[i] = excl;
+    const uint32_t excl_sl = carry_sl + (wid ? warp_sl[wid - 1] : 0u) + xs - sl;
+    if (i < nblocks) {
+      ws.block_sums[i] = excl;
+      ws.slices[i] = excl_sl;
+    }
     __syncthreads();
-    if (tid == 1023) carry_s = excl + v;
+    if (tid == 1023) {
+      carry_s = excl + v;
+      carry_sl = excl_sl + sl;
+    }
     __syncthreads();
   }
   if (tid == 0) {
@@ -79,77 +106,99 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
     for (int p = 0; p < kPlanPasses; ++p) ws.plan[kPlanCounter + p] = 0;
     ws.plan[kPlanQueue] = 0;
     ws.plan[kPlanQueue + 1] = 0;
+    ws.plan[kPlanSlices] = carry_sl;
   }
 }
 
-// One CTA per 1024 units. The CTA scans its units' pair counts, stores each unit's tile
-// rectangle and depth bits in shared memory, then its threads walk the CTA's contiguous
-// range of output positions: position p belongs to the unit whose prefix range holds it
-// (binary search), and its tile is the (p - start)-th tile of that unit's rectangle in
-// row-major order. Writes are coalesced and a unit with thousands of tiles is spread over
-// the whole CTA.
+// Key emission, load-balanced over output positions. Each 1024-unit block's contiguous
+// range of pairs is cut into slices of kEmitSlice positions; persistent CTAs take slices in
+// turn. For its slice a CTA rescans the block's 1024 pair counts in shared memory, fetches
+// the tile rectangle and depth of the units that overlap the slice, and its threads walk
+// the slice's positions: position p belongs to the unit whose prefix range holds it
+// (binary search in shared memory) and its tile is the (p - start)-th tile of that unit's
+// rectangle in row-major order. Writes are coalesced, and a block of huge splats is spread
+// over many CTAs.
 template <int MAXV>
-__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV> b, Ws ws,
+                                              uint32_t nblocks) {
   __shared__ uint32_t s_pre[kScanBlock + 1];
   __shared__ uint32_t s_rect[kScanBlock];     // tx0 | (rect width << 16)
   __shared__ uint32_t s_row[kScanBlock];      // ty0
   __shared__ uint32_t s_depth[kScanBlock];
   __shared__ uint32_t warp_tot[8];
+  __shared__ uint32_t s_blk;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t unit0 = blockIdx.x * (uint32_t)kScanBlock;
-  const ViewP& V = b.views[view_of_unit(b, unit0)];
-  const uint4 tt = reinterpret_cast<const uint4*>(ws.tiles_touched)[blockIdx.x * 256u + tid];
-  const uint32_t cnt[4] = {tt.x, tt.y, tt.z, tt.w};
-  const uint32_t s = tt.x + tt.y + tt.z + tt.w;
-  uint32_t x = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_tot[wid] = x;
-  __syncthreads();
-  uint32_t run = 0;
-  for (int w = 0; w < wid; ++w) run += warp_tot[w];
-  run += x - s;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int ul = 4 * tid + j;
-    s_pre[ul] = run;
-    if (cnt[j]) {
-      const uint32_t u = unit0 + ul;
-      const float2 xy = ws.xy[u];
-      int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-      tile_rect(xy.x, xy.y, ws.radius[u], V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0, tx1,
-                ty0, ty1);
-      s_rect[ul] = (uint32_t)tx0 | ((uint32_t)(tx1 - tx0 + 1) << 16);
-      s_row[ul] = (uint32_t)ty0;
-      s_depth[ul] = __float_as_uint(ws.depth[u]);
-    }
-    run += cnt[j];
-  }
-  if (tid == 255) s_pre[kScanBlock] = run;
-  __syncthreads();
-  const uint32_t total = s_pre[kScanBlock];
-  const unsigned long long base = ws.block_sums[blockIdx.x];
+  const uint32_t n_slices = ws.plan[kPlanSlices];
   const unsigned long long cap = ws.pair_capacity;
   unsigned long long* keys = ws.keys[0];
   uint32_t* vals = ws.vals[0];
-  for (uint32_t p = tid; p < total; p += 256) {
-    if (base + p >= cap) break;
-    int lo = 0, hi = kScanBlock - 1;          // last unit with s_pre[u] <= p
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_pre[mid] <= p) lo = mid; else hi = mid - 1;
+  for (uint32_t w = blockIdx.x; w < n_slices; w += gridDim.x) {
+    if (tid == 0) {                       // the block holding slice w
+      uint32_t lo = 0, hi = nblocks - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (ws.slices[mid] <= w) lo = mid; else hi = mid - 1;
+      }
+      s_blk = lo;
     }
-    const uint32_t k = p - s_pre[lo];
-    const uint32_t r = s_rect[lo];
-    const uint32_t w = r >> 16;
-    const uint32_t tx = (r & 0xffffu) + k % w;
-    const uint32_t ty = s_row[lo] + k / w;
-    const unsigned long long tile = (unsigned long long)(V.tile_off + ty * V.tiles_x + tx);
-    keys[base + p] = (tile << 32) | s_depth[lo];
-    vals[base + p] = unit0 + (uint32_t)lo;
+    __syncthreads();
+    const uint32_t blk = s_blk;
+    const uint32_t r0 = (w - ws.slices[blk]) * (uint32_t)kEmitSlice;
+    const uint32_t unit0 = blk * (uint32_t)kScanBlock;
+    const ViewP& V = b.views[view_of_unit(b, unit0)];
+    const uint4 tt = reinterpret_cast<const uint4*>(ws.tiles_touched)[blk * 256u + tid];
+    const uint32_t cnt[4] = {tt.x, tt.y, tt.z, tt.w};
+    const uint32_t s = tt.x + tt.y + tt.z + tt.w;
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    uint32_t run = 0;
+    for (int q = 0; q < wid; ++q) run += warp_tot[q];
+    run += x - s;
+    const uint32_t r1_full = r0 + (uint32_t)kEmitSlice;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ul = 4 * tid + j;
+      s_pre[ul] = run;
+      if (cnt[j] && run < r1_full && run + cnt[j] > r0) {
+        const uint32_t u = unit0 + ul;
+        const float2 xy = ws.xy[u];
+        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+        tile_rect(xy.x, xy.y, ws.radius[u], V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0,
+                  tx1, ty0, ty1);
+        s_rect[ul] = (uint32_t)tx0 | ((uint32_t)(tx1 - tx0 + 1) << 16);
+        s_row[ul] = (uint32_t)ty0;
+        s_depth[ul] = __float_as_uint(ws.depth[u]);
+      }
+      run += cnt[j];
+    }
+    if (tid == 255) s_pre[kScanBlock] = run;
+    __syncthreads();
+    const uint32_t total = s_pre[kScanBlock];
+    const uint32_t r1 = min(r1_full, total);
+    const unsigned long long base = ws.block_sums[blk];
+    for (uint32_t p = r0 + tid; p < r1; p += 256) {
+      if (base + p >= cap) break;
+      int lo = 0, hi = kScanBlock - 1;        // last unit with s_pre[u] <= p
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pre[mid] <= p) lo = mid; else hi = mid - 1;
+      }
+      const uint32_t k = p - s_pre[lo];
+      const uint32_t r = s_rect[lo];
+      const uint32_t wdt = r >> 16;
+      const uint32_t tx = (r & 0xffffu) + k % wdt;
+      const uint32_t ty = s_row[lo] + k / wdt;
+      const unsigned long long tile = (unsigned long long)(V.tile_off + ty * V.tiles_x + tx);
+      keys[base + p] = (tile << 32) | s_depth[lo];
+      vals[base + p] = unit0 + (uint32_t)lo;
+    }
+    __syncthreads();
   }
 }
 
@@ -177,7 +226,7 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
     k_block_sums<<<nblocks, 256, 0, st>>>(ws.tiles_touched, ws.block_sums);
   }
   k_scan_blocks<<<1, 1024, 0, st>>>(ws, nblocks, d_pair_count);
-  if (nblocks) k_emit<MAXV><<<nblocks, 256, 0, st>>>(b, ws);
+  if (nblocks) k_emit<MAXV><<<resident_small, 256, 0, st>>>(b, ws, nblocks);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_radix_sort(ws, n_passes, resident_small, resident_sort, st)) != cudaSuccess) return e;
   k_ranges<<<resident_small, 256, 0, st>>>(ws);

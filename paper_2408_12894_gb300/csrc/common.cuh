@@ -80,6 +80,7 @@ struct Ws {
   float* radius;
   uint32_t* tiles_touched;
   unsigned long long* block_sums;
+  uint32_t* slices;
   unsigned long long* keys[2];
   uint32_t* vals[2];
   uint32_t* hist;
@@ -99,12 +100,14 @@ constexpr int kPlanLb = 16;          // plan[kPlanLb + p] = look-back table of p
 constexpr int kPlanCounter = 24;     // plan[kPlanCounter + p] = partition ticket counter
 constexpr int kPlanNParts = 40;      // number of partitions
 constexpr int kPlanQueue = 41;       // render work-queue ticket counter (x2: fwd, bwd)
+constexpr int kPlanSlices = 43;      // number of key-emission slices
+constexpr int kEmitSlice = 4096;     // output positions per emission slice
 constexpr int kPlanEvalFwd = 48;     // uint64 running count of forward evaluations
 constexpr int kPlanEvalBwd = 50;     // uint64 running count of backward evaluations
 constexpr int kPlanFinal = 63;       // buffer holding the sorted result
 
-constexpr int kSortThreads = 256;
-constexpr int kSortKeysPerThread = 16;
+constexpr int kSortThreads = 512;
+constexpr int kSortKeysPerThread = 8;
 constexpr int kSortPart = kSortThreads * kSortKeysPerThread;   // 4096 keys per partition
 
 template <int MAXV>
@@ -151,12 +154,27 @@ __device__ __forceinline__ bool tile_rect(float u, float v, float r, int W, int 
 }
 
 // Per-pixel opacity of a splat: alpha = min(0.99, o * exp(-q/2)) with
-// q = a dx^2 + 2 b dx dy + c dy^2, dx = px - u. Written with explicit roundings so that
-// the forward and the backward pass recompute bit-identical values.
-__device__ __forceinline__ float splat_alpha(float dx, float dy, float4 co, float& g) {
-  float q = __fmaf_rn(co.x * dx, dx, __fmaf_rn(2.f * co.y * dx, dy, __fmul_rn(co.z * dy, dy)));
-  g = __expf(-0.5f * q);
-  return fminf(kAlphaMax, __fmul_rn(co.w, g));
+// q = a dx^2 + 2 b dx dy + c dy^2, dx = px - u. The conic arrives pre-scaled by -log2(e)/2
+// (see scale_conic), so exp(-q/2) = 2^(q') with one hardware ex2. Written with explicit
+// roundings so that the forward and the backward pass recompute bit-identical values.
+constexpr float kNegHalfLog2e = -0.5f * 1.4426950408889634f;
+
+// (a, b, c, o) -> (a k, 2 b k, c k, o) with k = -log2(e)/2
+__device__ __forceinline__ float4 scale_conic(float4 co) {
+  return make_float4(co.x * kNegHalfLog2e, 2.f * co.y * kNegHalfLog2e, co.z * kNegHalfLog2e, co.w);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float splat_alpha(float dx, float dy, float4 cs, float& g) {
+  const float qs = __fmaf_rn(__fmul_rn(cs.x, dx), dx,
+                             __fmaf_rn(__fmul_rn(cs.y, dx), dy, __fmul_rn(__fmul_rn(cs.z, dy), dy)));
+  g = ex2_approx(qs);
+  return fminf(kAlphaMax, __fmul_rn(cs.w, g));
 }
 
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {

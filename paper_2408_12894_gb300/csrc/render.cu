@@ -30,71 +30,104 @@ __device__ __forceinline__ void tile_pixel(const Batch<MAXV>& b, uint32_t tile, 
   py = ty * b.cfg.tile_h + (int)(threadIdx.x / (unsigned)b.cfg.tile_w);
 }
 
-template <int MAXV>
-__global__ void __launch_bounds__(256) k_render_fwd(const __grid_constant__ Batch<MAXV> b, Ws ws,
-                                                    float* __restrict__ out_rgb,
-                                                    float* __restrict__ out_T,
-                                                    uint32_t* __restrict__ out_nc) {
+// PIX pixels per thread, stacked vertically: thread t owns column t % tile_w and rows
+// (t / tile_w) * PIX + j. A batch of the tile's sorted Gaussians is staged in shared memory
+// (mean, pre-scaled conic with opacity, colour); each staged Gaussian serves PIX pixels.
+template <int MAXV, int PIX>
+__global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant__ Batch<MAXV> b,
+                                                          Ws ws, float* __restrict__ out_rgb,
+                                                          float* __restrict__ out_T,
+                                                          uint32_t* __restrict__ out_nc) {
   __shared__ float2 s_xy[256];
-  __shared__ float4 s_co[256];
+  __shared__ float4 s_cs[256];
   __shared__ float4 s_rgb[256];
   const uint32_t tile = blockIdx.x;
-  int vi, px, py;
-  tile_pixel(b, tile, vi, px, py);
+  const int vi = view_of_tile(b, tile);
   const ViewP& V = b.views[vi];
-  const int nthr = blockDim.x;
+  const uint32_t lt = tile - V.tile_off;
+  const int tw = b.cfg.tile_w;
   const int tid = threadIdx.x;
-  const bool inside = px < V.width && py < V.height;
+  const int nthr = blockDim.x;
+  const int px = (int)(lt % V.tiles_x) * tw + tid % tw;
+  const int py0 = (int)(lt / V.tiles_x) * b.cfg.tile_h + (tid / tw) * PIX;
   const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
   const uint2 rg = ws.ranges[tile];
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const float fx = (float)px + 0.5f;
   const int batch = b.cfg.batch;
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  uint32_t last = 0, evals = 0;
-  bool done = !inside;
+  float T[PIX], c0[PIX], c1[PIX], c2[PIX], fy[PIX];
+  uint32_t last[PIX];
+  bool live[PIX];
+  uint32_t evals = 0;
+  bool done = true;
+#pragma unroll
+  for (int j = 0; j < PIX; ++j) {
+    T[j] = 1.f;
+    c0[j] = c1[j] = c2[j] = 0.f;
+    last[j] = 0;
+    fy[j] = (float)(py0 + j) + 0.5f;
+    live[j] = px < V.width && py0 + j < V.height;
+    done = done && !live[j];
+  }
   for (uint32_t start = rg.x; start < rg.y; start += batch) {
     if (__syncthreads_count(done) == nthr) break;
     const int cnt = (int)min((uint32_t)batch, rg.y - start);
     for (int k = tid; k < cnt; k += nthr) {
       const uint32_t id = vals[start + k];
       s_xy[k] = ws.xy[id];
-      s_co[k] = ws.conic_o[id];
+      s_cs[k] = scale_conic(ws.conic_o[id]);
       s_rgb[k] = ws.rgb[id];
     }
     __syncthreads();
     if (!done) {
-      int k = 0;
-      for (; k < cnt; ++k) {
+      for (int k = 0; k < cnt; ++k) {
         const float2 m = s_xy[k];
-        float g;
-        const float a = splat_alpha(fx - m.x, fy - m.y, s_co[k], g);
-        if (a < kAlphaMin) continue;
-        const float Tn = T * (1.f - a);
-        if (Tn < kTMin) {
+        const float4 cs = s_cs[k];
+        const float dx = fx - m.x;
+        bool any_live = false;
+#pragma unroll
+        for (int j = 0; j < PIX; ++j) {
+          if (!live[j]) continue;
+          ++evals;
+          float g;
+          const float a = splat_alpha(dx, fy[j] - m.y, cs, g);
+          if (a < kAlphaMin) {
+            any_live = true;
+            continue;
+          }
+          const float Tn = T[j] * (1.f - a);
+          if (Tn < kTMin) {
+            live[j] = false;
+            continue;
+          }
+          any_live = true;
+          const float4 c = s_rgb[k];
+          const float w = a * T[j];
+          c0[j] += w * c.x;
+          c1[j] += w * c.y;
+          c2[j] += w * c.z;
+          T[j] = Tn;
+          last[j] = start - rg.x + (uint32_t)k + 1u;
+        }
+        if (!any_live) {
           done = true;
-          ++k;
           break;
         }
-        const float4 c = s_rgb[k];
-        const float w = a * T;
-        c0 += w * c.x;
-        c1 += w * c.y;
-        c2 += w * c.z;
-        T = Tn;
-        last = start - rg.x + (uint32_t)k + 1u;
       }
-      evals += (uint32_t)k;
     }
   }
   add_evals(ws.plan + kPlanEvalFwd, evals);
-  if (inside) {
-    const uint64_t npix = (uint64_t)V.width * V.height;
-    const uint64_t p = (uint64_t)py * V.width + px;
-    out_rgb[3 * V.pix_off + p] = c0 + T * b.cfg.bg[0];
-    out_rgb[3 * V.pix_off + npix + p] = c1 + T * b.cfg.bg[1];
-    out_rgb[3 * V.pix_off + 2 * npix + p] = c2 + T * b.cfg.bg[2];
-    out_T[V.pix_off + p] = T;
-    out_nc[V.pix_off + p] = last;
+  const uint64_t npix = (uint64_t)V.width * V.height;
+#pragma unroll
+  for (int j = 0; j < PIX; ++j) {
+    const int py = py0 + j;
+    if (px < V.width && py < V.height) {
+      const uint64_t p = (uint64_t)py * V.width + px;
+      out_rgb[3 * V.pix_off + p] = c0[j] + T[j] * b.cfg.bg[0];
+      out_rgb[3 * V.pix_off + npix + p] = c1[j] + T[j] * b.cfg.bg[1];
+      out_rgb[3 * V.pix_off + 2 * npix + p] = c2[j] + T[j] * b.cfg.bg[2];
+      out_T[V.pix_off + p] = T[j];
+      out_nc[V.pix_off + p] = last[j];
+    }
   }
 }
 
@@ -169,6 +202,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
   __shared__ uint32_t s_id[256];
   __shared__ float2 s_xy[256];
   __shared__ float4 s_co[256];
+  __shared__ float4 s_cs[256];
   __shared__ float4 s_rgb[256];
   __shared__ uint32_t s_max;
   const uint32_t tile = blockIdx.x;
@@ -221,7 +255,9 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
       const uint32_t id = vals[bstart + k];
       s_id[k] = id;
       s_xy[k] = ws.xy[id];
-      s_co[k] = ws.conic_o[id];
+      const float4 co = ws.conic_o[id];
+      s_co[k] = co;
+      s_cs[k] = scale_conic(co);
       s_rgb[k] = ws.rgb[id];
     }
     __syncthreads();
@@ -229,6 +265,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
       const uint32_t pos = bstart - rg.x + (uint32_t)k + 1u;
       const float2 m = s_xy[k];
       const float4 co = s_co[k];
+      const float4 cs = s_cs[k];
       const float dx = fx - m.x;
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool any = false;
@@ -239,7 +276,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         if (pos > last[j]) continue;
         const float dy = fy[j] - m.y;
         float gg;
-        const float a = splat_alpha(dx, dy, co, gg);
+        const float a = splat_alpha(dx, dy, cs, gg);
         if (a < kAlphaMin) continue;
         if (!have_c) {
           c = s_rgb[k];
@@ -280,7 +317,11 @@ cudaError_t launch_render_fwd(const Batch<MAXV>& b, const Ws& ws, float* out_rgb
   (void)resident;
   (void)persistent;
   if (b.tiles == 0) return cudaSuccess;
-  k_render_fwd<MAXV><<<b.tiles, b.cfg.tile_w * b.cfg.tile_h, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
+  const int px = b.cfg.tile_w * b.cfg.tile_h;
+  if (px >= 128)
+    k_render_fwd<MAXV, 2><<<b.tiles, px / 2, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
+  else
+    k_render_fwd<MAXV, 2><<<b.tiles, px / 2, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
   return cudaGetLastError();
 }
 

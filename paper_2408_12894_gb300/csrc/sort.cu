@@ -24,6 +24,7 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kWindow = 8;         // predecessors read per look-back step
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
   uint32_t v;
@@ -91,17 +92,23 @@ __global__ void __launch_bounds__(256) k_plan(Ws ws, int n_passes) {
   if (d == 0) ws.plan[kPlanFinal] = (uint32_t)src;
 }
 
+constexpr int kSortWarps = kSortThreads / 32;
+
 struct SortSmem {
   unsigned long long keys[kSortPart];
   uint32_t vals[kSortPart];
-  uint32_t whist[8][256];   // per-warp digit counts, then per-warp exclusive prefixes
+  uint32_t whist[kSortWarps][256];   // per-warp digit counts, then per-warp exclusive prefixes
   uint32_t local_start[256];
   uint32_t gbase[256];
   uint32_t wsum[8];
   uint32_t part;
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_pass(Ws ws, int pass) {
+// One digit pass. kSortThreads threads, kSortKeysPerThread keys each: warp w ranks the
+// 32 * kSortKeysPerThread consecutive keys starting at w * 32 * kSortKeysPerThread, round by
+// round, so (warp, round, lane) order is input order and the ranking is stable. The
+// first 256 threads then own one digit each for the partition-level steps.
+__global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
   if (!ws.plan[kPlanActive + pass]) return;
@@ -123,30 +130,25 @@ __global__ void __launch_bounds__(kSortThreads) k_pass(Ws ws, int pass) {
 
   for (;;) {
     if (tid == 0) sm.part = atomicAdd(&ws.plan[kPlanCounter + pass], 1u);
-    for (int i = tid; i < 8 * 256; i += kSortThreads) (&sm.whist[0][0])[i] = 0;
+    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&sm.whist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t part = sm.part;
     if (part >= nparts) break;
     const uint32_t base = part * (uint32_t)kSortPart;
+    const uint32_t wbase = base + wid * (32 * kSortKeysPerThread) + lane;
 
     unsigned long long k[kSortKeysPerThread];
     uint32_t v[kSortKeysPerThread];
     uint32_t rank[kSortKeysPerThread];
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
-      const uint32_t idx = base + wid * (32 * kSortKeysPerThread) + r * 32 + lane;
-      if (idx < P) {
-        k[r] = kin[idx];
-        v[r] = vin[idx];
-      } else {
-        k[r] = ~0ull;
-        v[r] = 0;
-      }
+      const uint32_t idx = wbase + r * 32;
+      k[r] = idx < P ? kin[idx] : ~0ull;
+      v[r] = idx < P ? vin[idx] : 0u;
     }
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
-      const uint32_t idx = base + wid * (32 * kSortKeysPerThread) + r * 32 + lane;
-      const bool valid = idx < P;
+      const bool valid = wbase + r * 32 < P;
       const uint32_t d = (uint32_t)(k[r] >> shift) & 255u;
       uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
@@ -162,65 +164,84 @@ __global__ void __launch_bounds__(kSortThreads) k_pass(Ws ws, int pass) {
       rank[r] = before + __popc(peers & lt_mask);
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps and the partition's digit total
-    const int d = tid;
-    uint32_t total = 0;
+    uint32_t total = 0, x = 0;
+    if (tid < 256) {
+      const int d = tid;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      const uint32_t c = sm.whist[w][d];
-      sm.whist[w][d] = total;
-      total += c;
-    }
-    // publish the aggregate (or the inclusive prefix for the first partition)
-    if (part == 0) st_relaxed(lb + d, kFlagInc | total);
-    else st_relaxed(lb + (size_t)part * 256u + d, kFlagAgg | total);
-    lb_next[(size_t)part * 256u + d] = 0;
-    // exclusive scan of the digit totals within the partition
-    uint32_t x = total;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) sm.wsum[wid] = x;
-    // look back
-    uint32_t excl = 0;
-    if (part > 0) {
-      int q = (int)part - 1;
-      uint32_t spins = 0;
-      while (q >= 0) {
-        const uint32_t w = ld_relaxed(lb + (size_t)q * 256u + d);
-        const uint32_t flag = w & ~kValMask;
-        if (flag == 0) {
-          if (++spins > kSpinLimit) {
-            set_status(ws.status, FLOD_DEV_TIMEOUT);
-            break;
-          }
-          if (spins > 32) __nanosleep(64);
-          continue;
-        }
-        excl += w & kValMask;
-        if (flag == kFlagInc) break;
-        --q;
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = sm.whist[w][d];
+        sm.whist[w][d] = total;
+        total += c;
       }
-      st_relaxed(lb + (size_t)part * 256u + d, kFlagInc | ((excl + total) & kValMask));
+      // publish the aggregate (or the inclusive prefix for the first partition)
+      if (part == 0) st_relaxed(lb + d, kFlagInc | total);
+      else st_relaxed(lb + (size_t)part * 256u + d, kFlagAgg | total);
+      lb_next[(size_t)part * 256u + d] = 0;
+      x = total;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) sm.wsum[wid] = x;
     }
-    sm.gbase[d] = goff[d] + excl;
     __syncthreads();
-    uint32_t pre = 0;
-    for (int w = 0; w < wid; ++w) pre += sm.wsum[w];
-    sm.local_start[d] = pre + x - total;
+    if (tid < 256) {
+      uint32_t pre = 0;
+      for (int w = 0; w < wid; ++w) pre += sm.wsum[w];
+      sm.local_start[tid] = pre + x - total;
+    }
     __syncthreads();
-    // reorder the partition in shared memory
+    // reorder the partition in shared memory (needs no global offset)
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
-      const uint32_t idx = base + wid * (32 * kSortKeysPerThread) + r * 32 + lane;
-      if (idx < P) {
+      if (wbase + r * 32 < P) {
         const uint32_t dd = (uint32_t)(k[r] >> shift) & 255u;
         const uint32_t pos = sm.local_start[dd] + sm.whist[wid][dd] + rank[r];
         sm.keys[pos] = k[r];
         sm.vals[pos] = v[r];
       }
+    }
+    // windowed look-back: read up to kWindow predecessors at once, nearest first; sum their
+    // aggregates up to the nearest inclusive prefix; re-poll from the first one not ready
+    if (tid < 256) {
+      const int d = tid;
+      uint32_t excl = 0;
+      if (part > 0) {
+        int q = (int)part - 1;
+        uint32_t spins = 0;
+        bool done = false;
+        while (!done && q >= 0) {
+          uint32_t wv[kWindow];
+#pragma unroll
+          for (int i = 0; i < kWindow; ++i)
+            wv[i] = (q - i >= 0) ? ld_relaxed(lb + (size_t)(q - i) * 256u + d) : kFlagInc;
+          int consumed = 0;
+          bool stalled = false;
+#pragma unroll
+          for (int i = 0; i < kWindow; ++i) {
+            if (done || stalled) continue;
+            const uint32_t flag = wv[i] & ~kValMask;
+            if (flag == 0) {
+              stalled = true;
+              continue;
+            }
+            if (q - i >= 0) excl += wv[i] & kValMask;
+            ++consumed;
+            if (flag == kFlagInc) done = true;
+          }
+          q -= consumed;
+          if (stalled && !done) {
+            if (++spins > kSpinLimit) {
+              set_status(ws.status, FLOD_DEV_TIMEOUT);
+              break;
+            }
+            if (spins > 8) __nanosleep(64);
+          }
+        }
+        st_relaxed(lb + (size_t)part * 256u + d, kFlagInc | ((excl + total) & kValMask));
+      }
+      sm.gbase[d] = goff[d] + excl;
     }
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortPart, P - base);
