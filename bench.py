@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0,
                     help="multiply every level count (profiling cases; not a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-selective", action="store_true", help="skip the selective-rendering section")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-view section")
+    ap.add_argument("--batched-views", type=int, default=64)
     return ap.parse_args()
 
 
@@ -390,6 +393,10 @@ def run_flod(a):
             "gpu_launches": launches_per_step * a.steps,
             "clocks": clocks,
         }
+        if not a.no_selective:
+            line["selective"] = selective_section(a)
+        if not a.no_batched:
+            line["batched"] = batched_section(a)
         if not a.no_cpu_baseline and world == 1:
             try:
                 g_np = dict(g)
@@ -405,6 +412,139 @@ def run_flod(a):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def timed(fn, steps, warmup):
+    """Mean ms of fn() over `steps` calls on the current stream (CUDA events)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def selective_sets(scale: float = 1.0):
+    """The selective scene: the 5-level scene stretched x5 (positions and minimum scales)."""
+    from paper_2408_12894_gb300 import flod, synth
+    counts = tuple(int(round(c * scale)) for c in synth.LEVEL_COUNTS)
+    levels = synth.stretch_levels(synth.level_scene(counts=counts), 5.0)
+    sets = [flod.GaussianSet.from_numpy(g, 5.0 * s) for (g, _), s in zip(levels, synth.LEVEL_SMIN)]
+    for l in range(4):
+        flod.flod_adjust_scale(sets[4].s_opt[:counts[l]], 5 * synth.LEVEL_SMIN[l], 5 * synth.LEVEL_SMIN[l + 1])
+        for k in range(l + 1, 4):
+            flod.flod_adjust_scale(sets[k].s_opt[:counts[l]], 5 * synth.LEVEL_SMIN[l], 5 * synth.LEVEL_SMIN[l + 1])
+    return sets
+
+
+def selective_section(a):
+    """Per-view selective rendering (Eq. 6 per frame from the camera position) along the
+    32-frame path, forward only, at 1920x1080 and 3840x2160."""
+    import torch
+    from paper_2408_12894_gb300 import flod, multiview, synth
+    sets = selective_sets(a.scale)
+    th = list(synth.SELECTIVE_THRESHOLDS[::-1])
+    out = {"workload": "5-level scene x5 (radius 100), thresholds {10,25,50,100}, 32-frame path, "
+                       "per-view selection every frame, forward", "resolutions": {}}
+    for (w, h) in ((1920, 1080), (3840, 2160)):
+        path = synth.camera_path(width=w, height=h)
+        st = multiview.BatchedStep(sets, [multiview.Job(path[0], levels=[0, 1, 2, 3, 4], thresholds=th)],
+                                   flod.default_config())
+        # size the pairs for the whole path and record the selected working set per frame
+        need, sel = 0, []
+        for cam in path:
+            st.set_camera(0, cam)
+            need = max(need, st.size_capacity())
+            sel.append(st.selected_count(0))
+        st.rast.pair_capacity = int(need * 1.1) + 4096
+        st.rast._alloc()
+        st.set_camera(0, path[0])
+        frames = [0]
+
+        def frame():
+            st.set_camera(0, path[frames[0] % len(path)])
+            frames[0] += 1
+            st.run()
+        ms = timed(frame, max(a.steps, len(path)), 3)
+        units = st.rast.layout.units
+        per_frame_bytes = [int(n * 236 + units * 52 + st.rast.pair_capacity * 24 + w * h * 20)
+                           for n in sel]
+        out["resolutions"][f"{w}x{h}"] = {
+            "fps": 1e3 / ms, "ms_per_frame": ms,
+            "selected_per_frame": {"min": min(sel), "max": max(sel), "mean": sum(sel) / len(sel)},
+            "selected_param_bytes_per_frame_mean": 236 * sum(sel) / len(sel),
+            "working_set_bytes_per_frame_max": max(per_frame_bytes),
+            "all_levels_param_bytes": 236 * sum(s.n for s in sets)}
+        del st
+        torch.cuda.empty_cache()
+    del sets
+    torch.cuda.empty_cache()
+    return out
+
+
+def batched_section(a):
+    """64 cameras of mixed resolution, each rendering one level of the 5-level scene or the
+    per-view selective mix of the stretched scene, forward+backward: one autotuned,
+    persistent, graph-captured batch vs the same jobs as 64 per-view calls (16x16 tiles,
+    one CTA per tile, eager)."""
+    import torch
+    from paper_2408_12894_gb300 import flod, multiview, synth
+    sel_sets = selective_sets(a.scale)
+    counts = tuple(int(round(c * a.scale)) for c in synth.LEVEL_COUNTS)
+    levels = synth.level_scene(counts=counts)
+    lvl_sets = []
+    for li, (g, _) in enumerate(levels):
+        s = flod.GaussianSet.from_numpy(g, synth.LEVEL_SMIN[li])
+        for l in range(li):
+            flod.flod_adjust_scale(s.s_opt[:counts[l]], synth.LEVEL_SMIN[l], synth.LEVEL_SMIN[l + 1])
+        lvl_sets.append(s)
+    sets = sel_sets + lvl_sets
+    cams, job_ids = synth.batched_jobs(n_cams=a.batched_views)
+    th = list(synth.SELECTIVE_THRESHOLDS[::-1])
+    jobs = [multiview.Job(c, levels=[0, 1, 2, 3, 4], thresholds=th) if j == 5
+            else multiview.Job(c, set_index=5 + j) for c, j in zip(cams, job_ids)]
+    dL = torch.as_tensor(synth.upstream_gradient(11, cams), device="cuda")
+    t0 = time.perf_counter()
+    cfg, times = multiview.autotune(sets, jobs, backward=True, dL=dL, steps=2)
+    tune_s = time.perf_counter() - t0
+    st = multiview.BatchedStep(sets, jobs, cfg, backward=True, dL=dL)
+    pairs = st.size_capacity()
+    st.capture()
+    ms_batched = timed(st.replay, max(3, a.steps // 4), 2)
+    del st
+    torch.cuda.empty_cache()
+    # the same jobs as per-view calls of the plain rasterizer
+    singles = []
+    off = 0
+    for j in jobs:
+        n = 3 * j.cam["width"] * j.cam["height"]
+        s1 = multiview.BatchedStep(sets, [j], flod.default_config(), backward=True, dL=dL[off:off + n])
+        s1.size_capacity()
+        singles.append(s1)
+        off += n
+
+    def per_view():
+        for s1 in singles:
+            s1.run()
+    ms_single = timed(per_view, max(3, a.steps // 4), 1)
+    res = {"workload": f"{len(jobs)} views, resolutions {{640x480,1280x720,1920x1080,3840x2160}}, "
+                       "jobs {levels 1..5, per-view selective}, fwd+bwd",
+           "views": len(jobs), "pixels": int(sum(c["width"] * c["height"] for c in cams)),
+           "pairs": pairs, "batched_ms": ms_batched, "per_view_ms": ms_single,
+           "batched_views_per_s": len(jobs) * 1e3 / ms_batched,
+           "per_view_views_per_s": len(jobs) * 1e3 / ms_single,
+           "speedup": ms_single / ms_batched,
+           "autotuned": {"tile": f"{cfg.tile_w}x{cfg.tile_h}", "batch": cfg.batch,
+                         "tuning_s": tune_s,
+                         "candidates_ms": {f"{k[0]}x{k[1]}/{k[2]}": round(v, 3) for k, v in times.items()}}}
+    del singles
+    torch.cuda.empty_cache()
+    return res
 
 
 def main():

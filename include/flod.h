@@ -64,7 +64,7 @@ typedef enum {
 #define FLOD_MAX_VIEWS 128
 #define FLOD_MAX_SETS 16
 #define FLOD_SEL_SHIFT 28 /* selection entry = (set << FLOD_SEL_SHIFT) | index */
-#define FLOD_MAX_PAIRS ((1ull << 30) - 1)
+#define FLOD_MAX_PAIRS ((1ull << 32) - 8192)
 
 typedef struct {
   float viewmat[12]; /* world -> camera, row-major [R | t] */
@@ -99,7 +99,8 @@ typedef struct {
   float z_near;       /* cull t_z <= z_near (default 0.2) */
   float bg[3];        /* background colour (default black) */
   int extent_rule;    /* 0: opacity-aware exact support (default); 1: 3 sigma */
-  int persistent;     /* render with persistent CTAs over a largest-first tile queue */
+  int persistent;     /* 1: flod_bin_sort also orders the tiles largest-first (by pair
+                         count) and the renderers run persistent CTAs over that order */
 } flod_raster_config;
 
 /* Gradient outputs of one set, same shapes as the parameters; accumulated with +=. */
@@ -129,7 +130,7 @@ typedef struct {
   size_t lookback;      /* radix-sort decoupled look-back tables */
   size_t ranges;        /* uint32x2 [tiles] [start, end) in the sorted pair list */
   size_t grad2d;        /* float4 [units][3]: (du, dv, dopacity, 0), (da, db, dc, 0), (dr, dg, db, 0) */
-  size_t queue;         /* uint32 [tiles + 64] persistent render work order */
+  size_t queue;         /* uint32 [tiles + 128]: 66 header words, then the largest-first tile order */
   uint64_t units;       /* total units (each view's capacity rounded up to 1024) */
   uint64_t tiles;       /* total tiles over all views */
   uint64_t pixels;      /* total pixels over all views */

@@ -156,10 +156,10 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   L.vals[0] = take(4 * pair_capacity);
   L.vals[1] = take(4 * pair_capacity);
   L.hist = take(4 * kPlanPasses * 256);
-  L.lookback = take(4ull * 2 * P.max_parts * 256);
+  L.lookback = take(8ull * 2 * P.max_parts * 256);
   L.ranges = take(8 * t);
   L.grad2d = take(48 * u);
-  L.queue = take(4 * (t + 64));
+  L.queue = take(4 * (t + 128));
   L.total = off;
   L.units = u;
   L.tiles = t;
@@ -188,7 +188,7 @@ Ws ws_ptrs(void* base, const Plan& P) {
     w.vals[i] = reinterpret_cast<uint32_t*>(b + L.vals[i]);
   }
   w.hist = reinterpret_cast<uint32_t*>(b + L.hist);
-  w.lookback = reinterpret_cast<uint32_t*>(b + L.lookback);
+  w.lookback = reinterpret_cast<unsigned long long*>(b + L.lookback);
   w.ranges = reinterpret_cast<uint2*>(b + L.ranges);
   w.grad2d = reinterpret_cast<float4*>(b + L.grad2d);
   w.queue = reinterpret_cast<uint32_t*>(b + L.queue);
@@ -338,7 +338,8 @@ flod_status flod_bin_sort(const flod_gaussians* sets, int n_sets, const flod_vie
   const int n_passes = P.n_passes;
   return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {
     return launch_binning(B, w, n_passes, dev->res_sort, dev->res_small,
-                          reinterpret_cast<unsigned long long*>(d_pair_count), st);
+                          reinterpret_cast<unsigned long long*>(d_pair_count),
+                          cfg->persistent != 0, st);
   });
 }
 

@@ -213,9 +213,45 @@ __global__ void __launch_bounds__(256) k_ranges(Ws ws) {
   }
 }
 
+// Largest-first render order: every tile goes to bucket floor(log2(pairs)) + 1 (0 for an
+// empty tile), buckets are laid out from the largest down, and tiles land in their bucket
+// in arrival order. Persistent render CTAs then take the most expensive tiles first.
+__global__ void __launch_bounds__(256) k_queue_count(Ws ws, uint32_t n_tiles) {
+  __shared__ uint32_t h[33];
+  if (threadIdx.x < 33) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t t = blockIdx.x * 256u + threadIdx.x; t < n_tiles; t += gridDim.x * 256u) {
+    const uint2 r = ws.ranges[t];
+    const uint32_t n = r.y - r.x;
+    atomicAdd(&h[n ? 32 - __clz(n) : 0], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(&ws.queue[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_queue_offsets(Ws ws) {
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int bkt = 32; bkt >= 0; --bkt) {
+      ws.queue[33 + bkt] = run;
+      run += ws.queue[bkt];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_queue_fill(Ws ws, uint32_t n_tiles) {
+  for (uint32_t t = blockIdx.x * 256u + threadIdx.x; t < n_tiles; t += gridDim.x * 256u) {
+    const uint2 r = ws.ranges[t];
+    const uint32_t n = r.y - r.x;
+    const uint32_t slot = atomicAdd(&ws.queue[33 + (n ? 32 - __clz(n) : 0)], 1u);
+    ws.queue[kQueueHeader + slot] = t;
+  }
+}
+
 template <int MAXV>
 cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int resident_sort,
-                           int resident_small, unsigned long long* d_pair_count, cudaStream_t st) {
+                           int resident_small, unsigned long long* d_pair_count, bool build_queue,
+                           cudaStream_t st) {
   const uint32_t nblocks = b.units / kScanBlock;
   cudaError_t e;
   if (b.tiles) {
@@ -230,12 +266,20 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_radix_sort(ws, n_passes, resident_small, resident_sort, st)) != cudaSuccess) return e;
   k_ranges<<<resident_small, 256, 0, st>>>(ws);
+  if (build_queue && b.tiles) {
+    if ((e = cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t) * kQueueHeader, st)) != cudaSuccess)
+      return e;
+    const uint32_t g = min((uint32_t)resident_small, (b.tiles + 255) / 256);
+    k_queue_count<<<g, 256, 0, st>>>(ws, b.tiles);
+    k_queue_offsets<<<1, 32, 0, st>>>(ws);
+    k_queue_fill<<<g, 256, 0, st>>>(ws, b.tiles);
+  }
   return cudaGetLastError();
 }
 
 template cudaError_t launch_binning<kMaxViewsSmall>(const BatchS&, const Ws&, int, int, int,
-                                                    unsigned long long*, cudaStream_t);
+                                                    unsigned long long*, bool, cudaStream_t);
 template cudaError_t launch_binning<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, int, int, int,
-                                                    unsigned long long*, cudaStream_t);
+                                                    unsigned long long*, bool, cudaStream_t);
 
 }  // namespace flod

@@ -84,7 +84,7 @@ struct Ws {
   unsigned long long* keys[2];
   uint32_t* vals[2];
   uint32_t* hist;
-  uint32_t* lookback;
+  unsigned long long* lookback;
   uint2* ranges;
   float4* grad2d;
   uint32_t* queue;
@@ -102,6 +102,7 @@ constexpr int kPlanNParts = 40;      // number of partitions
 constexpr int kPlanQueue = 41;       // render work-queue ticket counter (x2: fwd, bwd)
 constexpr int kPlanSlices = 43;      // number of key-emission slices
 constexpr int kEmitSlice = 4096;     // output positions per emission slice
+constexpr int kQueueHeader = 66;     // queue[0..32] bucket counts, [33..65] offsets, then tiles
 constexpr int kPlanEvalFwd = 48;     // uint64 running count of forward evaluations
 constexpr int kPlanEvalBwd = 50;     // uint64 running count of backward evaluations
 constexpr int kPlanFinal = 63;       // buffer holding the sorted result
@@ -155,7 +156,7 @@ __device__ __forceinline__ bool tile_rect(float u, float v, float r, int W, int 
 
 // Per-pixel opacity of a splat: alpha = min(0.99, o * exp(-q/2)) with
 // q = a dx^2 + 2 b dx dy + c dy^2, dx = px - u. The conic arrives pre-scaled by -log2(e)/2
-// (see scale_conic), so exp(-q/2) = 2^(q') with one hardware ex2. Written with explicit
+// (see scale_conic), so exp(-q/2) = 2^(q') with one hardware ex2 (splat_alpha_row). Written with explicit
 // roundings so that the forward and the backward pass recompute bit-identical values.
 constexpr float kNegHalfLog2e = -0.5f * 1.4426950408889634f;
 
@@ -170,9 +171,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-__device__ __forceinline__ float splat_alpha(float dx, float dy, float4 cs, float& g) {
-  const float qs = __fmaf_rn(__fmul_rn(cs.x, dx), dx,
-                             __fmaf_rn(__fmul_rn(cs.y, dx), dy, __fmul_rn(__fmul_rn(cs.z, dy), dy)));
+// With t0 = (a' dx) dx and t1 = (2b') dx computed once per Gaussian and column,
+// q' = t0 + dy (t1 + c' dy) for each pixel row of that column.
+__device__ __forceinline__ float splat_alpha_row(float t0, float t1, float dy, float4 cs,
+                                                 float& g) {
+  const float qs = __fmaf_rn(dy, __fmaf_rn(cs.z, dy, t1), t0);
   g = ex2_approx(qs);
   return fminf(kAlphaMax, __fmul_rn(cs.w, g));
 }

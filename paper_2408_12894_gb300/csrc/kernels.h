@@ -20,7 +20,8 @@ cudaError_t launch_preprocess_bwd(const Batch<MAXV>& b, const Ws& ws, const Grad
 // binning.cu: block sums -> scan -> emit -> (sort) -> ranges
 template <int MAXV>
 cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int resident_sort,
-                           int resident_small, unsigned long long* d_pair_count, cudaStream_t st);
+                           int resident_small, unsigned long long* d_pair_count, bool build_queue,
+                           cudaStream_t st);
 
 // sort.cu
 cudaError_t launch_radix_sort(const Ws& ws, int n_passes, int resident_hist, int resident_sort,

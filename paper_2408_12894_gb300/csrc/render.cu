@@ -1,135 +1,26 @@
 // Per-tile alpha blending (Sec. 3, after Eq. 2: the image is the alpha blend of the
 // projected Gaussians in depth order) and its backward.
 //
-// Forward: one CTA per tile (one thread per pixel). The tile's sorted Gaussians are staged
-// into shared memory in batches; every pixel walks them front to back:
+// Forward: a CTA renders one tile; each thread owns PIX pixels of one column. The tile's
+// sorted Gaussians are staged into shared memory in batches (mean, conic pre-scaled by
+// -log2(e)/2 with the opacity, colour); every pixel walks them front to back:
 //   alpha = min(0.99, o exp(-q/2)); skip alpha < 1/255; stop before the Gaussian that
 //   would take T below 1e-4; C += rgb alpha T; T *= 1 - alpha.
-// The CTA leaves as soon as every pixel has stopped (__syncthreads_count).
+// The CTA leaves the tile as soon as every pixel has stopped (__syncthreads_count).
 //
 // Backward: the same tiles, every pixel walking back to front from its last blended
-// Gaussian (n_contrib) and recovering T by division by (1 - alpha), so no per-pair state is
-// stored. d(alpha) = sum_c g_c (rgb_c T - S_c / (1 - alpha)), S = colour behind + T_final bg.
-// The nine per-Gaussian gradients of a warp are reduced with shuffles and one lane adds
-// them with float4 atomics; warps where no pixel touches the Gaussian skip the reduction.
+// Gaussian (n_contrib) and recovering T by multiplying with 1 / (1 - alpha), so no per-pair
+// state is stored. d(alpha) = sum_c g_c (rgb_c T - S_c / (1 - alpha)), S = colour behind +
+// T_final bg. Each thread sums its PIX pixels; a warp then reduces the nine per-Gaussian
+// gradients with a transposing butterfly and the owning lanes add them with atomics;
+// warps where no pixel touches the Gaussian skip the reduction.
+//
+// Launch modes: one CTA per tile in tile order, or persistent CTAs (about the number that
+// fit on the GPU) taking tiles from the largest-first queue that flod_bin_sort builds.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace flod {
-
-__device__ __forceinline__ void add_evals(uint32_t* counter, uint32_t evals);
-
-template <int MAXV>
-__device__ __forceinline__ void tile_pixel(const Batch<MAXV>& b, uint32_t tile, int& vi,
-                                           int& px, int& py) {
-  vi = view_of_tile(b, tile);
-  const ViewP& V = b.views[vi];
-  const uint32_t lt = tile - V.tile_off;
-  const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
-  px = tx * b.cfg.tile_w + (int)(threadIdx.x % (unsigned)b.cfg.tile_w);
-  py = ty * b.cfg.tile_h + (int)(threadIdx.x / (unsigned)b.cfg.tile_w);
-}
-
-// PIX pixels per thread, stacked vertically: thread t owns column t % tile_w and rows
-// (t / tile_w) * PIX + j. A batch of the tile's sorted Gaussians is staged in shared memory
-// (mean, pre-scaled conic with opacity, colour); each staged Gaussian serves PIX pixels.
-template <int MAXV, int PIX>
-__global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant__ Batch<MAXV> b,
-                                                          Ws ws, float* __restrict__ out_rgb,
-                                                          float* __restrict__ out_T,
-                                                          uint32_t* __restrict__ out_nc) {
-  __shared__ float2 s_xy[256];
-  __shared__ float4 s_cs[256];
-  __shared__ float4 s_rgb[256];
-  const uint32_t tile = blockIdx.x;
-  const int vi = view_of_tile(b, tile);
-  const ViewP& V = b.views[vi];
-  const uint32_t lt = tile - V.tile_off;
-  const int tw = b.cfg.tile_w;
-  const int tid = threadIdx.x;
-  const int nthr = blockDim.x;
-  const int px = (int)(lt % V.tiles_x) * tw + tid % tw;
-  const int py0 = (int)(lt / V.tiles_x) * b.cfg.tile_h + (tid / tw) * PIX;
-  const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
-  const uint2 rg = ws.ranges[tile];
-  const float fx = (float)px + 0.5f;
-  const int batch = b.cfg.batch;
-  float T[PIX], c0[PIX], c1[PIX], c2[PIX], fy[PIX];
-  uint32_t last[PIX];
-  bool live[PIX];
-  uint32_t evals = 0;
-  bool done = true;
-#pragma unroll
-  for (int j = 0; j < PIX; ++j) {
-    T[j] = 1.f;
-    c0[j] = c1[j] = c2[j] = 0.f;
-    last[j] = 0;
-    fy[j] = (float)(py0 + j) + 0.5f;
-    live[j] = px < V.width && py0 + j < V.height;
-    done = done && !live[j];
-  }
-  for (uint32_t start = rg.x; start < rg.y; start += batch) {
-    if (__syncthreads_count(done) == nthr) break;
-    const int cnt = (int)min((uint32_t)batch, rg.y - start);
-    for (int k = tid; k < cnt; k += nthr) {
-      const uint32_t id = vals[start + k];
-      s_xy[k] = ws.xy[id];
-      s_cs[k] = scale_conic(ws.conic_o[id]);
-      s_rgb[k] = ws.rgb[id];
-    }
-    __syncthreads();
-    if (!done) {
-      for (int k = 0; k < cnt; ++k) {
-        const float2 m = s_xy[k];
-        const float4 cs = s_cs[k];
-        const float dx = fx - m.x;
-        bool any_live = false;
-#pragma unroll
-        for (int j = 0; j < PIX; ++j) {
-          if (!live[j]) continue;
-          ++evals;
-          float g;
-          const float a = splat_alpha(dx, fy[j] - m.y, cs, g);
-          if (a < kAlphaMin) {
-            any_live = true;
-            continue;
-          }
-          const float Tn = T[j] * (1.f - a);
-          if (Tn < kTMin) {
-            live[j] = false;
-            continue;
-          }
-          any_live = true;
-          const float4 c = s_rgb[k];
-          const float w = a * T[j];
-          c0[j] += w * c.x;
-          c1[j] += w * c.y;
-          c2[j] += w * c.z;
-          T[j] = Tn;
-          last[j] = start - rg.x + (uint32_t)k + 1u;
-        }
-        if (!any_live) {
-          done = true;
-          break;
-        }
-      }
-    }
-  }
-  add_evals(ws.plan + kPlanEvalFwd, evals);
-  const uint64_t npix = (uint64_t)V.width * V.height;
-#pragma unroll
-  for (int j = 0; j < PIX; ++j) {
-    const int py = py0 + j;
-    if (px < V.width && py < V.height) {
-      const uint64_t p = (uint64_t)py * V.width + px;
-      out_rgb[3 * V.pix_off + p] = c0[j] + T[j] * b.cfg.bg[0];
-      out_rgb[3 * V.pix_off + npix + p] = c1[j] + T[j] * b.cfg.bg[1];
-      out_rgb[3 * V.pix_off + 2 * npix + p] = c2[j] + T[j] * b.cfg.bg[2];
-      out_T[V.pix_off + p] = T[j];
-      out_nc[V.pix_off + p] = last[j];
-    }
-  }
-}
 
 // one 64-bit atomic per CTA: the number of (pixel, Gaussian) evaluations of the launch
 __device__ __forceinline__ void add_evals(uint32_t* counter, uint32_t evals) {
@@ -143,11 +34,135 @@ __device__ __forceinline__ void add_evals(uint32_t* counter, uint32_t evals) {
   if (threadIdx.x == 0 && s_ev) atomicAdd(reinterpret_cast<unsigned long long*>(counter), s_ev);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// Next tile for this CTA: the block index (one-shot mode) or a queue ticket (persistent).
+template <bool PERSIST>
+__device__ __forceinline__ bool next_tile(const Ws& ws, uint32_t n_tiles, int counter,
+                                          bool first, uint32_t& tile) {
+  __shared__ uint32_t s_item;
+  if (!PERSIST) {
+    tile = blockIdx.x;
+    return first;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) s_item = atomicAdd(&ws.plan[kPlanQueue + counter], 1u);
+  __syncthreads();
+  const uint32_t item = s_item;
+  if (item >= n_tiles) return false;
+  tile = ws.queue[kQueueHeader + item];
+  return true;
 }
+
+// ---------------------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------------------
+template <int MAXV, int PIX, bool PERSIST>
+__global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant__ Batch<MAXV> b,
+                                                          Ws ws, float* __restrict__ out_rgb,
+                                                          float* __restrict__ out_T,
+                                                          uint32_t* __restrict__ out_nc) {
+  __shared__ float2 s_xy[256];
+  __shared__ float4 s_cs[256];
+  __shared__ float4 s_rgb[256];
+  const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
+  const int tw = b.cfg.tile_w;
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+  const int batch = b.cfg.batch;
+  uint32_t evals = 0;
+  uint32_t tile;
+  for (bool first = true; next_tile<PERSIST>(ws, b.tiles, 0, first, tile); first = false) {
+    const ViewP& V = b.views[view_of_tile(b, tile)];
+    const uint32_t lt = tile - V.tile_off;
+    const int px = (int)(lt % V.tiles_x) * tw + tid % tw;
+    const int py0 = (int)(lt / V.tiles_x) * b.cfg.tile_h + (tid / tw) * PIX;
+    const uint2 rg = ws.ranges[tile];
+    const float fx = (float)px + 0.5f;
+    float T[PIX], c0[PIX], c1[PIX], c2[PIX], fy[PIX];
+    uint32_t last[PIX], stop[PIX];
+    bool live[PIX];
+    bool done = true;
+#pragma unroll
+    for (int j = 0; j < PIX; ++j) {
+      T[j] = 1.f;
+      c0[j] = c1[j] = c2[j] = 0.f;
+      last[j] = 0;
+      stop[j] = 0;
+      fy[j] = (float)(py0 + j) + 0.5f;
+      live[j] = px < V.width && py0 + j < V.height;
+      done = done && !live[j];
+    }
+    uint32_t pos = 0;   // Gaussians of the tile list walked so far
+    for (uint32_t start = rg.x; start < rg.y; start += batch) {
+      if (__syncthreads_count(done) == nthr) break;
+      const int cnt = (int)min((uint32_t)batch, rg.y - start);
+      for (int k = tid; k < cnt; k += nthr) {
+        const uint32_t id = vals[start + k];
+        s_xy[k] = ws.xy[id];
+        s_cs[k] = scale_conic(ws.conic_o[id]);
+        s_rgb[k] = ws.rgb[id];
+      }
+      __syncthreads();
+      if (!done) {
+        for (int k = 0; k < cnt; ++k) {
+          const float2 m = s_xy[k];
+          const float4 cs = s_cs[k];
+          const float dx = fx - m.x;
+          const float t0 = __fmul_rn(__fmul_rn(cs.x, dx), dx);
+          const float t1 = __fmul_rn(cs.y, dx);
+          ++pos;
+          bool any_live = false;
+#pragma unroll
+          for (int j = 0; j < PIX; ++j) {
+            if (!live[j]) continue;
+            float g;
+            const float a = splat_alpha_row(t0, t1, fy[j] - m.y, cs, g);
+            if (a < kAlphaMin) {
+              any_live = true;
+              continue;
+            }
+            const float Tn = T[j] * (1.f - a);
+            if (Tn < kTMin) {
+              live[j] = false;
+              stop[j] = pos;
+              continue;
+            }
+            any_live = true;
+            const float4 c = s_rgb[k];
+            const float w = a * T[j];
+            c0[j] += w * c.x;
+            c1[j] += w * c.y;
+            c2[j] += w * c.z;
+            T[j] = Tn;
+            last[j] = pos;
+          }
+          if (!any_live) {
+            done = true;
+            break;
+          }
+        }
+      }
+    }
+    const uint64_t npix = (uint64_t)V.width * V.height;
+#pragma unroll
+    for (int j = 0; j < PIX; ++j) {
+      const int py = py0 + j;
+      if (px < V.width && py < V.height) {
+        evals += live[j] ? pos : stop[j];
+        const uint64_t p = (uint64_t)py * V.width + px;
+        out_rgb[3 * V.pix_off + p] = c0[j] + T[j] * b.cfg.bg[0];
+        out_rgb[3 * V.pix_off + npix + p] = c1[j] + T[j] * b.cfg.bg[1];
+        out_rgb[3 * V.pix_off + 2 * npix + p] = c2[j] + T[j] * b.cfg.bg[2];
+        out_T[V.pix_off + p] = T[j];
+        out_nc[V.pix_off + p] = last[j];
+      }
+    }
+  }
+  add_evals(ws.plan + kPlanEvalFwd, evals);
+}
+
+// ---------------------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------------------
 
 // Sums nine per-lane values over the warp and adds each total to its slot of a unit's
 // 2D-gradient record (du, dv, dop | da, db, dc | dr, dg, db). A transposing butterfly: at
@@ -192,9 +207,7 @@ __device__ __forceinline__ void warp_reduce_add9(float (&v)[9], float4* rec) {
     atomicAdd(reinterpret_cast<float*>(rec) + i1 + i1 / 3, z);
 }
 
-// PIX pixels per thread, stacked vertically: thread t owns column t % tile_w and rows
-// (t / tile_w) * PIX + j.
-template <int MAXV, int PIX>
+template <int MAXV, int PIX, bool PERSIST>
 __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant__ Batch<MAXV> b,
                                                           Ws ws, const float* __restrict__ dL,
                                                           const float* __restrict__ fwd_T,
@@ -205,139 +218,181 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
   __shared__ float4 s_cs[256];
   __shared__ float4 s_rgb[256];
   __shared__ uint32_t s_max;
-  const uint32_t tile = blockIdx.x;
-  const int vi = view_of_tile(b, tile);
-  const ViewP& V = b.views[vi];
-  const uint32_t lt = tile - V.tile_off;
+  const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
   const int tw = b.cfg.tile_w;
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
-  const int px = (int)(lt % V.tiles_x) * tw + tid % tw;
-  const int py0 = (int)(lt / V.tiles_x) * b.cfg.tile_h + (tid / tw) * PIX;
-  const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
-  const uint2 rg = ws.ranges[tile];
-  const float fx = (float)px + 0.5f;
   const int batch = b.cfg.batch;
-  const uint64_t npix = (uint64_t)V.width * V.height;
-  float T[PIX], g0[PIX], g1[PIX], g2[PIX], S0[PIX], S1[PIX], S2[PIX], fy[PIX];
-  uint32_t last[PIX];
-  uint32_t my_max = 0, evals = 0;
+  uint32_t evals = 0;
+  uint32_t tile;
+  for (bool first = true; next_tile<PERSIST>(ws, b.tiles, 1, first, tile); first = false) {
+    const ViewP& V = b.views[view_of_tile(b, tile)];
+    const uint32_t lt = tile - V.tile_off;
+    const int px = (int)(lt % V.tiles_x) * tw + tid % tw;
+    const int py0 = (int)(lt / V.tiles_x) * b.cfg.tile_h + (tid / tw) * PIX;
+    const uint2 rg = ws.ranges[tile];
+    const float fx = (float)px + 0.5f;
+    const uint64_t npix = (uint64_t)V.width * V.height;
+    float T[PIX], g0[PIX], g1[PIX], g2[PIX], S0[PIX], S1[PIX], S2[PIX], fy[PIX];
+    uint32_t last[PIX];
+    uint32_t my_max = 0;
 #pragma unroll
-  for (int j = 0; j < PIX; ++j) {
-    const int py = py0 + j;
-    fy[j] = (float)py + 0.5f;
-    T[j] = g0[j] = g1[j] = g2[j] = 0.f;
-    last[j] = 0;
-    if (px < V.width && py < V.height) {
-      const uint64_t p = (uint64_t)py * V.width + px;
-      T[j] = fwd_T[V.pix_off + p];
-      last[j] = fwd_nc[V.pix_off + p];
-      g0[j] = dL[3 * V.pix_off + p];
-      g1[j] = dL[3 * V.pix_off + npix + p];
-      g2[j] = dL[3 * V.pix_off + 2 * npix + p];
-    }
-    S0[j] = T[j] * b.cfg.bg[0];
-    S1[j] = T[j] * b.cfg.bg[1];
-    S2[j] = T[j] * b.cfg.bg[2];
-    my_max = max(my_max, last[j]);
-    evals += last[j];
-  }
-  if (tid == 0) s_max = 0;
-  __syncthreads();
-  if (my_max) atomicMax(&s_max, my_max);
-  __syncthreads();
-  const uint32_t end = rg.x + s_max;
-  for (uint32_t bend = end; bend > rg.x;) {
-    const uint32_t bstart = bend - rg.x > (uint32_t)batch ? bend - batch : rg.x;
-    const int cnt = (int)(bend - bstart);
-    __syncthreads();
-    for (int k = tid; k < cnt; k += nthr) {
-      const uint32_t id = vals[bstart + k];
-      s_id[k] = id;
-      s_xy[k] = ws.xy[id];
-      const float4 co = ws.conic_o[id];
-      s_co[k] = co;
-      s_cs[k] = scale_conic(co);
-      s_rgb[k] = ws.rgb[id];
-    }
-    __syncthreads();
-    for (int k = cnt - 1; k >= 0; --k) {
-      const uint32_t pos = bstart - rg.x + (uint32_t)k + 1u;
-      const float2 m = s_xy[k];
-      const float4 co = s_co[k];
-      const float4 cs = s_cs[k];
-      const float dx = fx - m.x;
-      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bool any = false;
-      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-      bool have_c = false;
-#pragma unroll
-      for (int j = 0; j < PIX; ++j) {
-        if (pos > last[j]) continue;
-        const float dy = fy[j] - m.y;
-        float gg;
-        const float a = splat_alpha(dx, dy, cs, gg);
-        if (a < kAlphaMin) continue;
-        if (!have_c) {
-          c = s_rgb[k];
-          have_c = true;
-        }
-        any = true;
-        const float ioma = __frcp_rn(1.f - a);
-        T[j] *= ioma;
-        const float w = a * T[j];
-        acc[6] += w * g0[j];
-        acc[7] += w * g1[j];
-        acc[8] += w * g2[j];
-        const float dalpha = g0[j] * (c.x * T[j] - S0[j] * ioma) + g1[j] * (c.y * T[j] - S1[j] * ioma) +
-                             g2[j] * (c.z * T[j] - S2[j] * ioma);
-        S0[j] += c.x * w;
-        S1[j] += c.y * w;
-        S2[j] += c.z * w;
-        if (co.w * gg < kAlphaMax) {
-          acc[2] += gg * dalpha;
-          const float dq = -0.5f * co.w * gg * dalpha;   // dL/dq
-          acc[3] += dq * dx * dx;
-          acc[4] += dq * 2.f * dx * dy;
-          acc[5] += dq * dy * dy;
-          acc[0] -= dq * 2.f * (co.x * dx + co.y * dy);
-          acc[1] -= dq * 2.f * (co.y * dx + co.z * dy);
-        }
+    for (int j = 0; j < PIX; ++j) {
+      const int py = py0 + j;
+      fy[j] = (float)py + 0.5f;
+      T[j] = g0[j] = g1[j] = g2[j] = 0.f;
+      last[j] = 0;
+      if (px < V.width && py < V.height) {
+        const uint64_t p = (uint64_t)py * V.width + px;
+        T[j] = fwd_T[V.pix_off + p];
+        last[j] = fwd_nc[V.pix_off + p];
+        g0[j] = dL[3 * V.pix_off + p];
+        g1[j] = dL[3 * V.pix_off + npix + p];
+        g2[j] = dL[3 * V.pix_off + 2 * npix + p];
       }
-      if (__any_sync(0xffffffffu, any)) warp_reduce_add9(acc, ws.grad2d + 3ull * s_id[k]);
+      S0[j] = T[j] * b.cfg.bg[0];
+      S1[j] = T[j] * b.cfg.bg[1];
+      S2[j] = T[j] * b.cfg.bg[2];
+      my_max = max(my_max, last[j]);
+      evals += last[j];
     }
-    bend = bstart;
+    if (tid == 0) s_max = 0;
+    __syncthreads();
+    if (my_max) atomicMax(&s_max, my_max);
+    __syncthreads();
+    const uint32_t end = rg.x + s_max;
+    for (uint32_t bend = end; bend > rg.x;) {
+      const uint32_t bstart = bend - rg.x > (uint32_t)batch ? bend - batch : rg.x;
+      const int cnt = (int)(bend - bstart);
+      __syncthreads();
+      for (int k = tid; k < cnt; k += nthr) {
+        const uint32_t id = vals[bstart + k];
+        s_id[k] = id;
+        s_xy[k] = ws.xy[id];
+        const float4 co = ws.conic_o[id];
+        s_co[k] = co;
+        s_cs[k] = scale_conic(co);
+        s_rgb[k] = ws.rgb[id];
+      }
+      __syncthreads();
+      for (int k = cnt - 1; k >= 0; --k) {
+        const uint32_t pos = bstart - rg.x + (uint32_t)k + 1u;
+        const float2 m = s_xy[k];
+        const float4 co = s_co[k];
+        const float4 cs = s_cs[k];
+        const float dx = fx - m.x;
+        const float t0 = __fmul_rn(__fmul_rn(cs.x, dx), dx);
+        const float t1 = __fmul_rn(cs.y, dx);
+        float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool any = false;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool have_c = false;
+#pragma unroll
+        for (int j = 0; j < PIX; ++j) {
+          if (pos > last[j]) continue;
+          const float dy = fy[j] - m.y;
+          float gg;
+          const float a = splat_alpha_row(t0, t1, dy, cs, gg);
+          if (a < kAlphaMin) continue;
+          if (!have_c) {
+            c = s_rgb[k];
+            have_c = true;
+          }
+          any = true;
+          const float ioma = __frcp_rn(1.f - a);
+          T[j] *= ioma;
+          const float w = a * T[j];
+          acc[6] += w * g0[j];
+          acc[7] += w * g1[j];
+          acc[8] += w * g2[j];
+          const float dalpha = g0[j] * (c.x * T[j] - S0[j] * ioma) +
+                               g1[j] * (c.y * T[j] - S1[j] * ioma) +
+                               g2[j] * (c.z * T[j] - S2[j] * ioma);
+          S0[j] += c.x * w;
+          S1[j] += c.y * w;
+          S2[j] += c.z * w;
+          if (co.w * gg < kAlphaMax) {
+            acc[2] += gg * dalpha;
+            const float dq = -0.5f * co.w * gg * dalpha;   // dL/dq
+            acc[3] += dq * dx * dx;
+            acc[4] += dq * 2.f * dx * dy;
+            acc[5] += dq * dy * dy;
+            acc[0] -= dq * 2.f * (co.x * dx + co.y * dy);
+            acc[1] -= dq * 2.f * (co.y * dx + co.z * dy);
+          }
+        }
+        if (__any_sync(0xffffffffu, any)) warp_reduce_add9(acc, ws.grad2d + 3ull * s_id[k]);
+      }
+      bend = bstart;
+    }
   }
   add_evals(ws.plan + kPlanEvalBwd, evals);
 }
 
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+// Persistent grid size: CTAs of `kernel` that fit on the device at once.
+static int resident_ctas(const void* kernel, int threads, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * sms;
+}
+
+template <int MAXV, int PIX>
+static cudaError_t fwd_launch(const Batch<MAXV>& b, const Ws& ws, float* out_rgb, float* out_T,
+                              uint32_t* out_nc, int resident, bool persistent, cudaStream_t st) {
+  const int thr = b.cfg.tile_w * b.cfg.tile_h / PIX;
+  if (persistent) {
+    cudaError_t e = cudaMemsetAsync(ws.plan + kPlanQueue, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    static int cached = 0;
+    if (!cached) cached = resident_ctas((const void*)k_render_fwd<MAXV, PIX, true>, thr, resident);
+    const uint32_t grid = min((uint32_t)cached, b.tiles);
+    k_render_fwd<MAXV, PIX, true><<<grid, thr, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
+  } else {
+    k_render_fwd<MAXV, PIX, false><<<b.tiles, thr, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
+  }
+  return cudaGetLastError();
+}
+
+template <int MAXV, int PIX>
+static cudaError_t bwd_launch(const Batch<MAXV>& b, const Ws& ws, const float* dL,
+                              const float* fwd_T, const uint32_t* fwd_nc, int resident,
+                              bool persistent, cudaStream_t st) {
+  const int thr = b.cfg.tile_w * b.cfg.tile_h / PIX;
+  if (persistent) {
+    cudaError_t e = cudaMemsetAsync(ws.plan + kPlanQueue + 1, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    static int cached = 0;
+    if (!cached) cached = resident_ctas((const void*)k_render_bwd<MAXV, PIX, true>, thr, resident);
+    const uint32_t grid = min((uint32_t)cached, b.tiles);
+    k_render_bwd<MAXV, PIX, true><<<grid, thr, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
+  } else {
+    k_render_bwd<MAXV, PIX, false><<<b.tiles, thr, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
+  }
+  return cudaGetLastError();
+}
+
+// resident: the device's SM count (the persistent grid is SMs x resident CTAs per SM); one
+// thread per 2 (forward) or 4 (backward; 2 for 8x8 tiles) pixels
 template <int MAXV>
 cudaError_t launch_render_fwd(const Batch<MAXV>& b, const Ws& ws, float* out_rgb, float* out_T,
                               uint32_t* out_nc, int resident, bool persistent, cudaStream_t st) {
-  (void)resident;
-  (void)persistent;
   if (b.tiles == 0) return cudaSuccess;
-  const int px = b.cfg.tile_w * b.cfg.tile_h;
-  if (px >= 128)
-    k_render_fwd<MAXV, 2><<<b.tiles, px / 2, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
-  else
-    k_render_fwd<MAXV, 2><<<b.tiles, px / 2, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
-  return cudaGetLastError();
+  return fwd_launch<MAXV, 2>(b, ws, out_rgb, out_T, out_nc, resident, persistent, st);
 }
 
 template <int MAXV>
 cudaError_t launch_render_bwd(const Batch<MAXV>& b, const Ws& ws, const float* dL,
                               const float* fwd_T, const uint32_t* fwd_nc, int resident,
                               bool persistent, cudaStream_t st) {
-  (void)resident;
-  (void)persistent;
   if (b.tiles == 0) return cudaSuccess;
-  const int px = b.cfg.tile_w * b.cfg.tile_h;
-  if (px >= 128)
-    k_render_bwd<MAXV, 4><<<b.tiles, px / 4, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
-  else
-    k_render_bwd<MAXV, 2><<<b.tiles, px / 2, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
-  return cudaGetLastError();
+  if (b.cfg.tile_w * b.cfg.tile_h >= 128)
+    return bwd_launch<MAXV, 4>(b, ws, dL, fwd_T, fwd_nc, resident, persistent, st);
+  return bwd_launch<MAXV, 2>(b, ws, dL, fwd_T, fwd_nc, resident, persistent, st);
 }
 
 template cudaError_t launch_render_fwd<kMaxViewsSmall>(const BatchS&, const Ws&, float*, float*,

@@ -20,19 +20,20 @@
 
 namespace flod {
 
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagInc = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1u;
+// look-back words: 2 flag bits over a 62-bit count
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kWindow = 8;         // predecessors read per look-back step
 
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __global__ void __launch_bounds__(256) k_hist(Ws ws, int n_passes) {
@@ -121,8 +122,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
   const unsigned long long P0 = *ws.pair_count;
   const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
   const uint32_t nparts = ws.plan[kPlanNParts];
-  uint32_t* lb = ws.lookback + (size_t)lbt * ws.max_parts * 256u;
-  uint32_t* lb_next = ws.lookback + (size_t)(lbt ^ 1) * ws.max_parts * 256u;
+  unsigned long long* lb = ws.lookback + (size_t)lbt * ws.max_parts * 256u;
+  unsigned long long* lb_next = ws.lookback + (size_t)(lbt ^ 1) * ws.max_parts * 256u;
   const uint32_t* goff = ws.hist + pass * 256;
   const int shift = 8 * pass;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -206,13 +207,13 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
     // aggregates up to the nearest inclusive prefix; re-poll from the first one not ready
     if (tid < 256) {
       const int d = tid;
-      uint32_t excl = 0;
+      unsigned long long excl = 0;
       if (part > 0) {
         int q = (int)part - 1;
         uint32_t spins = 0;
         bool done = false;
         while (!done && q >= 0) {
-          uint32_t wv[kWindow];
+          unsigned long long wv[kWindow];
 #pragma unroll
           for (int i = 0; i < kWindow; ++i)
             wv[i] = (q - i >= 0) ? ld_relaxed(lb + (size_t)(q - i) * 256u + d) : kFlagInc;
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
 #pragma unroll
           for (int i = 0; i < kWindow; ++i) {
             if (done || stalled) continue;
-            const uint32_t flag = wv[i] & ~kValMask;
+            const unsigned long long flag = wv[i] & ~kValMask;
             if (flag == 0) {
               stalled = true;
               continue;
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
         }
         st_relaxed(lb + (size_t)part * 256u + d, kFlagInc | ((excl + total) & kValMask));
       }
-      sm.gbase[d] = goff[d] + excl;
+      sm.gbase[d] = goff[d] + (uint32_t)excl;
     }
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortPart, P - base);

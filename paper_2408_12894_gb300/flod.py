@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libflod.so")
 MAX_VIEWS = 128
 MAX_SETS = 16
 SEL_SHIFT = 28
-MAX_PAIRS = (1 << 30) - 1
+MAX_PAIRS = (1 << 32) - 8192
 DEV_CAPACITY = 0x1
 DEV_TIMEOUT = 0x2
 

@@ -1,0 +1,179 @@
+"""Batched multi-view, multi-level rendering: one launch per stage for every view of a batch,
+persistent render CTAs over a largest-first tile queue, the whole step captured in a CUDA
+graph, and an autotuner for the tile shape and the shared-memory batch size.
+
+A batch is a list of jobs. A job is one camera rendering either a whole Gaussian set (a FLoD
+level) or a per-view selective mix of levels (Eq. 6 with the given distance thresholds,
+selected from the camera's own position every step, Sec. 5.2 "per-view Gaussian set").
+Everything below only orders calls into the C ABI; every stage runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import itertools
+
+import torch
+
+from . import flod
+
+TILE_SHAPES = ((16, 16), (8, 8), (32, 8))
+BATCH_SIZES = (256, 128, 64, 32)
+
+
+class Job:
+    """One camera and what it renders: ``set_index`` (a whole set) or, when ``levels`` is
+    given, the selective mix of those set indices (coarse to fine) with ``thresholds``."""
+
+    def __init__(self, cam: dict, set_index: int = 0, levels=None, thresholds=None):
+        self.cam = cam
+        self.set_index = set_index
+        self.levels = None if levels is None else list(levels)
+        self.thresholds = None if thresholds is None else [float(t) for t in thresholds]
+
+
+class BatchedStep:
+    """All jobs of a batch rendered (and optionally differentiated) as one step.
+
+    ``run()`` enqueues the step on the current stream; ``capture()`` records it into a CUDA
+    graph and ``replay()`` launches the graph. Selection lists live in buffers owned here and
+    are refilled by flod_select_levels inside the step."""
+
+    def __init__(self, sets, jobs, cfg=None, pair_capacity=None, backward=False, dL=None):
+        self.sets = list(sets)
+        self.jobs = list(jobs)
+        self.backward = backward
+        self.cfg = cfg if cfg is not None else flod.default_config(persistent=1)
+        dev = self.sets[0].means.device
+        self.sel = []
+        views = []
+        for j in self.jobs:
+            if j.levels is None:
+                views.append(flod.view_struct(j.cam, j.set_index))
+                self.sel.append(None)
+            else:
+                lv = [self.sets[i] for i in j.levels]
+                cap = sum(s.n for s in lv)
+                buf = torch.zeros(cap, dtype=torch.int32, device=dev)
+                cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+                scr = torch.zeros(max(flod.flod_select_scratch_size(lv), 4), dtype=torch.uint8,
+                                  device=dev)
+                # selection entries are (level index << 28) | i and index the sets array
+                # directly, so a selective job's levels must be sets 0 .. n-1
+                if j.levels != list(range(len(j.levels))):
+                    raise flod.FlodError("selective levels must be the first sets, in order")
+                self.sel.append((lv, buf, cnt, scr))
+                views.append(flod.view_struct(j.cam, 0, sel=buf, sel_count=cnt, sel_capacity=cap))
+        self.rast = flod.Rasterizer(self.sets, views, self.cfg, pair_capacity)
+        self.out = self.rast.new_outputs()
+        self.dL = dL
+        self.graph = None
+        if backward:
+            self.grads = [[torch.zeros_like(getattr(s, f)) for f in flod.GaussianSet.FIELDS]
+                          for s in self.sets]
+            self.grads_c = flod.grads_struct(self.grads)
+
+    def set_camera(self, i: int, cam: dict):
+        """Move job i's camera (and, for a selective job, its selection origin). A captured
+        graph keeps the cameras it was captured with."""
+        self.jobs[i].cam = cam
+        self.rast.views[i].cam = flod.camera_struct(cam)
+        self.rast.refresh_structs()
+
+    def selected_count(self, i: int) -> int:
+        """Entries selected for job i by the last step (synchronises)."""
+        return int(self.sel[i][2].item()) if self.sel[i] is not None else self.sets[self.jobs[i].set_index].n
+
+    def _select(self, stream=None):
+        for j, s in zip(self.jobs, self.sel):
+            if s is None:
+                continue
+            lv, buf, cnt, scr = s
+            flod.flod_select_levels(lv, j.cam["cam_pos"], buf, cnt, scr, d_thresh=j.thresholds,
+                                    stream=stream)
+
+    def run(self, stream=None):
+        """Enqueue one step (no host synchronisation)."""
+        self._select(stream)
+        r = self.rast
+        r.preprocess(stream)
+        r.bin_sort(stream)
+        r.render_fwd(*self.out, stream)
+        if self.backward:
+            for per_set in self.grads:
+                for t in per_set:
+                    t.zero_()
+            r.blend_bwd(self.dL, self.out[1], self.out[2], stream)
+            r.preprocess_bwd(self.grads_c, stream)
+
+    def size_capacity(self, headroom: float = 1.15):
+        """Run once eagerly and grow the pair capacity to fit (synchronises)."""
+        for _ in range(4):
+            self.run()
+            torch.cuda.synchronize()
+            need = int(self.rast.pair_count.item())
+            if need <= self.rast.pair_capacity:
+                return need
+            self.rast.pair_capacity = min(flod.MAX_PAIRS, int(need * headroom) + 4096)
+            self.rast._alloc()
+        raise flod.FlodError("pair capacity did not converge")
+
+    def capture(self):
+        """Record one step into a CUDA graph (the pair capacity must already fit)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run()                      # warm up on the side stream
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
+
+
+def signature(sets, jobs, backward: bool):
+    return (tuple(s.n for s in sets), backward,
+            tuple((j.cam["width"], j.cam["height"], j.set_index,
+                   None if j.levels is None else tuple(j.levels)) for j in jobs))
+
+
+_cache: dict = {}
+
+
+def autotune(sets, jobs, backward=False, dL=None, steps=3, shapes=TILE_SHAPES,
+             batches=BATCH_SIZES):
+    """Time every (tile shape, batch size) candidate on the batch itself (persistent
+    launch, eager) and return (best config, {candidate: ms}). Results are cached per
+    workload signature for the life of the process."""
+    key = signature(sets, jobs, backward)
+    if key in _cache:
+        return _cache[key]
+    times = {}
+    best = None
+    for (tw, th), bs in itertools.product(shapes, batches):
+        cfg = flod.default_config(tile_w=tw, tile_h=th, batch=bs, persistent=1)
+        try:
+            step = BatchedStep(sets, jobs, cfg, backward=backward, dL=dL)
+            step.size_capacity()
+        except (flod.FlodError, torch.cuda.OutOfMemoryError):
+            times[(tw, th, bs)] = float("inf")      # does not fit: never chosen
+            torch.cuda.empty_cache()
+            continue
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step.run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        times[(tw, th, bs)] = ms
+        if best is None or ms < times[best]:
+            best = (tw, th, bs)
+        del step
+        torch.cuda.empty_cache()
+    cfg = flod.default_config(tile_w=best[0], tile_h=best[1], batch=best[2], persistent=1)
+    _cache[key] = (cfg, times)
+    return cfg, times

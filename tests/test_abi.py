@@ -66,7 +66,7 @@ def test_host_side_checks_without_a_device(libpath):
     # invalid arguments are refused before anything is enqueued
     bad = flod.default_config(tile_w=12)
     assert flod.lib().flod_workspace_size(sets, 1, views, 1, 1 << 20, C.byref(bad)) == 0
-    assert flod.lib().flod_workspace_size(sets, 1, views, 1, 1 << 31, C.byref(cfg)) == 0
+    assert flod.lib().flod_workspace_size(sets, 1, views, 1, 1 << 32, C.byref(cfg)) == 0
     v2 = flod.View()
     v2.cam.width = 0
     assert flod.lib().flod_workspace_size(sets, 1, (flod.View * 1)(v2), 1, 1024, C.byref(cfg)) == 0

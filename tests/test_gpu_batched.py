@@ -1,0 +1,144 @@
+"""Batched multi-view, multi-level path: one launch per stage for mixed-resolution views over
+several levels and a per-view selective mix; persistent render CTAs over the largest-first
+tile queue; CUDA-graph replay; autotuner."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import assert_image_close
+from oracle import raster as R
+from oracle import select as S
+from paper_2408_12894_gb300 import flod, multiview, synth
+
+pytestmark = pytest.mark.gpu
+
+COUNTS = (2_000, 6_000, 15_000, 30_000, 60_000)
+TH = [100.0, 50.0, 25.0, 10.0]
+
+
+def _scene():
+    base = synth.level_scene(counts=COUNTS, radius=20.0, sh_degree=3)
+    stretched = synth.stretch_levels(base, 5.0)
+    sel_sets = [flod.GaussianSet.from_numpy(g, 5.0 * s) for (g, _), s in zip(stretched, synth.LEVEL_SMIN)]
+    lvl_sets = [flod.GaussianSet.from_numpy(g, s) for (g, _), s in zip(base, synth.LEVEL_SMIN)]
+    sets = sel_sets + lvl_sets          # selective levels first (sets 0..4), then levels 5..9
+    rng = np.random.default_rng(7)
+    res = [(160, 90), (96, 96), (200, 120), (128, 72), (64, 48), (120, 80)]
+    jobs, np_sets = [], [g for g, _ in stretched] + [g for g, _ in base]
+    for i, (w, h) in enumerate(res):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        if i % 3 == 2:
+            cam = synth.camera(d * 60.0, w, h)
+            jobs.append(multiview.Job(cam, levels=[0, 1, 2, 3, 4], thresholds=TH))
+        else:
+            cam = synth.camera(d * 40.0, w, h)
+            jobs.append(multiview.Job(cam, set_index=5 + (i % 5)))
+    return sets, jobs, np_sets
+
+
+def _per_view(sets, jobs, backward=False, dLs=None):
+    """The same jobs, one plain (one-shot, 16x16) rasterizer per view."""
+    imgs, grads = [], [[torch.zeros_like(getattr(s, f)) for f in flod.GaussianSet.FIELDS] for s in sets]
+    for k, j in enumerate(jobs):
+        st = multiview.BatchedStep(sets, [j], flod.default_config(), backward=backward,
+                                   dL=None if dLs is None else dLs[k])
+        st.size_capacity()
+        torch.cuda.synchronize()
+        imgs.append(st.out[0].clone())
+        if backward:
+            for a, b in zip(grads, st.grads):
+                for x, y in zip(a, b):
+                    x += y
+    return imgs, grads
+
+
+def _split(flat, jobs, ch):
+    out, off = [], 0
+    for j in jobs:
+        n = ch * j.cam["width"] * j.cam["height"]
+        out.append(flat[off:off + n])
+        off += n
+    return out
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (8, 8), (32, 8)])
+def test_batched_persistent_images_equal_per_view(shape):
+    sets, jobs, _ = _scene()
+    cfg = flod.default_config(tile_w=shape[0], tile_h=shape[1], persistent=1)
+    st = multiview.BatchedStep(sets, jobs, cfg)
+    st.size_capacity()
+    torch.cuda.synchronize()
+    assert flod.flod_read_status(st.rast.ws) == 0
+    batched = _split(st.out[0], jobs, 3)
+    single, _ = _per_view(sets, jobs)
+    for k, (a, b) in enumerate(zip(batched, single)):
+        if shape == (16, 16):
+            assert torch.equal(a, b), f"view {k}"
+        else:
+            assert_image_close(a.view(3, -1).cpu().numpy(), b.view(3, -1).cpu().numpy().astype(np.float64))
+
+
+def test_batched_gradients_equal_sum_of_per_view():
+    sets, jobs, _ = _scene()
+    dL_np = synth.upstream_gradient(3, [j.cam for j in jobs])
+    dL = torch.as_tensor(dL_np, device="cuda")
+    st = multiview.BatchedStep(sets, jobs, flod.default_config(persistent=1), backward=True, dL=dL)
+    st.size_capacity()
+    torch.cuda.synchronize()
+    dLs = _split(dL, jobs, 3)
+    _, ref = _per_view(sets, jobs, backward=True, dLs=dLs)
+    for a_set, b_set in zip(st.grads, ref):
+        for a, b in zip(a_set, b_set):
+            nb = torch.linalg.norm(b).item()
+            if nb == 0:
+                assert torch.linalg.norm(a).item() == 0
+                continue
+            assert torch.linalg.norm(a - b).item() <= 1e-4 * nb
+
+
+def test_graph_replay_matches_eager():
+    sets, jobs, _ = _scene()
+    dL = torch.as_tensor(synth.upstream_gradient(4, [j.cam for j in jobs]), device="cuda")
+    st = multiview.BatchedStep(sets, jobs, flod.default_config(persistent=1), backward=True, dL=dL)
+    st.size_capacity()
+    torch.cuda.synchronize()
+    img_eager = st.out[0].clone()
+    g_eager = [t.clone() for t in st.grads[5]]
+    st.out[0].zero_()
+    st.capture()
+    for _ in range(2):
+        st.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(st.out[0], img_eager)
+    for a, b in zip(st.grads[5], g_eager):
+        assert torch.allclose(a, b, rtol=1e-5, atol=1e-9)
+    assert flod.flod_read_status(st.rast.ws) == 0
+
+
+def test_selective_view_matches_oracle():
+    sets, jobs, np_sets = _scene()
+    j = jobs[2]
+    st = multiview.BatchedStep(sets, [j], flod.default_config(persistent=1))
+    st.size_capacity()
+    torch.cuda.synchronize()
+    # oracle: Eq. 6 selection, then one rasterization of G_sel with each Gaussian's own s_min
+    ent = S.select([np_sets[i]["means"] for i in range(5)], j.cam["cam_pos"], TH)
+    lv, idx = ent >> S.LEVEL_SHIFT, ent & ((1 << S.LEVEL_SHIFT) - 1)
+    g = {k: np.concatenate([np_sets[l][k][i:i + 1] for l, i in zip(lv, idx)]) for k in
+         ("means", "quats", "s_opt", "opacity_logit", "sh")}
+    smin = torch.as_tensor(np.array([5.0 * synth.LEVEL_SMIN[l] for l in lv])[:, None])
+    img, _, _ = R.render(g, 3, smin, j.cam, R.Config())
+    assert_image_close(st.out[0].view(3, -1).cpu().numpy(), img.reshape(3, -1))
+
+
+def test_autotuner_picks_a_candidate():
+    sets, jobs, _ = _scene()
+    cfg, times = multiview.autotune(sets, jobs[:3], steps=1, shapes=((16, 16), (8, 8)),
+                                    batches=(256, 64))
+    assert len(times) == 4 and all(np.isfinite(v) and v > 0 for v in times.values())
+    assert (cfg.tile_w, cfg.tile_h, cfg.batch) == min(times, key=times.get)
+    assert cfg.persistent == 1
+    again, _ = multiview.autotune(sets, jobs[:3], steps=1, shapes=((16, 16), (8, 8)),
+                                  batches=(256, 64))
+    assert (again.tile_w, again.batch) == (cfg.tile_w, cfg.batch)
