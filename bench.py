@@ -237,9 +237,8 @@ def adjust_chain_numpy(s_opt, counts):
 def run_flod(a):
     import numpy as np
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2408_12894_gb300 import replicas
+    rank, world, local = replicas.world()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -301,9 +300,7 @@ def run_flod(a):
     assert flod.flod_read_status(rast.ws) == 0, "device status error"
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+        replicas.barrier()
 
     # ---- forward frames
     barrier()
@@ -333,10 +330,7 @@ def run_flod(a):
     stage_ms = {n: sum(evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(a.steps)) / a.steps
                 for j, n in enumerate(names)}
     ms = total_ms / a.steps
-    if dist is not None:
-        t = torch.tensor([ms, fwd_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, fwd_ms = t.tolist()
+    ms, fwd_ms = replicas.max_over_ranks([ms, fwd_ms], device="cuda")
 
     # ---- end to end: upstream gradient in from pinned host memory, image back, every step
     img_host = torch.empty(3 * H * W, dtype=torch.float32).pin_memory()
@@ -350,10 +344,7 @@ def run_flod(a):
     e2e1.record(st)
     barrier()
     e2e_ms = e2e0.elapsed_time(e2e1) / a.steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms, = replicas.max_over_ranks([e2e_ms], device="cuda")
 
     fwd_evals = (ev_after[0] - ev_before[0]) / a.steps
     bwd_evals = (ev_after[1] - ev_before[1]) / a.steps

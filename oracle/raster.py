@@ -293,3 +293,61 @@ def discrete_state(pre: dict, cam: dict, cfg: Config, lists=None) -> bytes:
                 live = torch.cumprod(1.0 - a, dim=1) >= T_MIN
             parts += [clamped.numpy().tobytes(), kept.numpy().tobytes(), live.numpy().tobytes()]
     return b"".join(parts)
+
+
+def sampled_gradients(g: dict, sh_degree: int, s_min, cam: dict, cfg: Config,
+                      grad_out: np.ndarray, sample: np.ndarray, lists=None, pre=None):
+    """dL/d(parameters) of the Gaussians ``sample`` only, for L = sum(grad_out * image).
+
+    A Gaussian enters only the tiles its rectangle covers, so its gradient is the sum over
+    those tiles' pixels: each such tile is blended with the sampled Gaussian's 2D values as
+    autograd leaves and every other Gaussian held constant, and the resulting 2D gradient is
+    chained through that Gaussian's own preprocess. Exact (same definition as
+    ``forward_backward``) at any scene size. Returns {name: array [len(sample), ...]}."""
+    W, H = cam["width"], cam["height"]
+    if pre is None:
+        with torch.no_grad():
+            pre = preprocess(params(g), sh_degree, s_min, cam, cfg)
+    keys, vals, ranges, tiles_x, tiles_y = lists if lists is not None else tile_lists(pre, cam, cfg)
+    bg = torch.as_tensor(np.asarray(cfg.bg, dtype=np.float64))
+    go = torch.as_tensor(np.asarray(grad_out, dtype=np.float64))
+    out = {k: [] for k in ("means", "quats", "s_opt", "opacity_logit", "sh")}
+    tx0, tx1, ty0, ty1 = pre["tile_rect"]
+    names = ("mean2d", "conic", "opacity", "rgb")
+    base = {k: pre[k].detach() for k in names}
+    for j in np.asarray(sample, dtype=np.int64):
+        one = {k: np.asarray(g[k])[j:j + 1] for k in ("means", "quats", "s_opt", "opacity_logit", "sh")}
+        pj = params(one, requires_grad=True)
+        smj = s_min if np.isscalar(s_min) else s_min[j:j + 1]
+        prej = preprocess(pj, sh_degree, smj, cam, cfg)
+        leaves = {k: prej[k] for k in names}
+        total = None
+        if pre["tiles_touched"][j] > 0:
+            for ty in range(ty0[j], ty1[j] + 1):
+                for tx in range(tx0[j], tx1[j] + 1):
+                    tile = ty * tiles_x + tx
+                    s, e = ranges[tile]
+                    gi = vals[s:e].astype(np.int64)
+                    pos = np.nonzero(gi == j)[0]
+                    x0, y0 = tx * cfg.tile_w, ty * cfg.tile_h
+                    x1, y1 = min(x0 + cfg.tile_w, W), min(y0 + cfg.tile_h, H)
+                    pix = _pixel_centres(np.arange(x0, x1), np.arange(y0, y1))
+                    sel = torch.as_tensor(gi)
+                    cols = {}
+                    for k in names:
+                        t = base[k][sel].clone()
+                        mask = torch.zeros(len(gi), dtype=torch.bool)
+                        mask[torch.as_tensor(pos)] = True
+                        shape = (-1,) + (1,) * (t.dim() - 1)
+                        cols[k] = torch.where(mask.view(shape), leaves[k].expand_as(t), t)
+                    a = alpha_raw(pix, cols["mean2d"], cols["conic"], cols["opacity"])
+                    col, _, _ = blend(a, cols["rgb"], bg)
+                    gt = go[:, y0:y1, x0:x1].reshape(3, -1).T
+                    term = (col * gt).sum()
+                    total = term if total is None else total + term
+        if total is not None:
+            total.backward()
+        for k in out:
+            gk = pj[k].grad
+            out[k].append(np.zeros(pj[k].shape[1:]) if gk is None else gk.numpy()[0])
+    return {k: np.stack(v) for k, v in out.items()}

@@ -193,3 +193,15 @@ def test_gradient_matches_central_finite_differences(seed):
             checked += 1
     print("fd checked", checked, "skipped", skipped)
     assert checked >= 80 and skipped <= checked // 4, (checked, skipped)
+
+
+def test_sampled_gradients_equal_full_gradient():
+    g = synth.gaussian_set(3, 400, k=4, radius=0.8, sh_degree=3, s_mean=-2.6)
+    cam = synth.camera((0.2, 0.1, -2.5), 48, 40)
+    w = np.random.default_rng(0).normal(size=(3, 40, 48))
+    cfg = R.Config()
+    _, _, _, full = R.forward_backward(g, 3, 0.01, cam, cfg, w)
+    sample = np.array([0, 5, 17, 123, 399])
+    sg = R.sampled_gradients(g, 3, 0.01, cam, cfg, w, sample)
+    for k in full:
+        np.testing.assert_allclose(sg[k], full[k][sample], rtol=1e-12, atol=1e-15)
