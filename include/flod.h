@@ -103,9 +103,14 @@ typedef struct {
                          count) and the renderers run persistent CTAs over that order */
 } flod_raster_config;
 
-/* Gradient outputs of one set, same shapes as the parameters; accumulated with +=. */
+/* Gradient outputs of one set, same shapes as the parameters (quats and, at SH degree 3,
+ * sh 16-byte aligned). Accumulated with += unless `overwrite` is 1: then every gradient of
+ * the set is written once (zeros for Gaussians that touch no tile), which needs no zeroed
+ * buffers; overwrite requires that exactly one view renders the set, as a whole set (no
+ * selection list), else the call returns FLOD_ERR_INVALID_ARG. */
 typedef struct {
   float *means, *quats, *s_opt, *opacity_logit, *sh;
+  int overwrite;
 } flod_grads;
 
 /* Byte offsets of the workspace's regions (see flod_workspace_layout). */

@@ -128,7 +128,7 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   if (u >= (1ull << 32) || t >= (1ull << 31)) return FLOD_ERR_INVALID_ARG;
   int tile_bits = 1;
   while (tile_bits < 31 && (1ull << tile_bits) < t) ++tile_bits;
-  P.n_passes = (32 + tile_bits + 7) / 8;
+  P.n_passes = (32 + tile_bits + kRadixBits - 1) / kRadixBits;
   P.max_parts = (uint32_t)((pair_capacity + kSortPart - 1) / kSortPart);
   if (P.max_parts == 0) P.max_parts = 1;
 
@@ -155,8 +155,8 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   L.keys[1] = take(8 * pair_capacity);
   L.vals[0] = take(4 * pair_capacity);
   L.vals[1] = take(4 * pair_capacity);
-  L.hist = take(4 * kPlanPasses * 256);
-  L.lookback = take(8ull * 2 * P.max_parts * 256);
+  L.hist = take(4 * kPlanPasses * kRadixBins);
+  L.lookback = take(8ull * 2 * P.max_parts * kRadixBins);
   L.ranges = take(8 * t);
   L.grad2d = take(48 * u);
   L.queue = take(4 * (t + 128));
@@ -361,8 +361,10 @@ flod_status flod_render_fwd(const flod_gaussians* sets, int n_sets, const flod_v
 }
 
 namespace {
-GradTable grad_table(const flod_view* views, int n_views, int n_sets, const flod_grads* grads) {
-  GradTable gt;
+// Per set: atomics when several units may hold one Gaussian (several views, or a selection
+// list beside other views), plain read-modify-write otherwise, plain stores on request.
+bool grad_table(const flod_view* views, int n_views, int n_sets, const flod_grads* grads,
+                GradTable& gt) {
   memset(&gt, 0, sizeof(gt));
   int direct[FLOD_MAX_SETS] = {0};
   int n_sel = 0;
@@ -372,9 +374,18 @@ GradTable grad_table(const flod_view* views, int n_views, int n_sets, const flod
   }
   for (int k = 0; k < n_sets; ++k) {
     gt.g[k] = grads[k];
-    gt.shared[k] = (direct[k] + n_sel) > 1 ? 1 : 0;
+    // float4 gradient writes: quaternion rows, and SH rows at degree 3, 16-byte aligned
+    if (reinterpret_cast<uintptr_t>(grads[k].quats) & 15u) return false;
+    if (reinterpret_cast<uintptr_t>(grads[k].sh) & 15u) return false;
+    const bool shared = (direct[k] + n_sel) > 1;
+    if (grads[k].overwrite) {
+      if (direct[k] != 1 || n_sel != 0) return false;
+      gt.mode[k] = kGradOverwrite;
+    } else {
+      gt.mode[k] = shared ? kGradAtomic : kGradAccumulate;
+    }
   }
-  return gt;
+  return true;
 }
 }  // namespace
 
@@ -406,7 +417,8 @@ flod_status flod_preprocess_bwd(const flod_gaussians* sets, int n_sets, const fl
   if (!grads) return FLOD_ERR_INVALID_ARG;
   flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
   if (s != FLOD_OK) return s;
-  const GradTable gt = grad_table(views, n_views, n_sets, grads);
+  GradTable gt;
+  if (!grad_table(views, n_views, n_sets, grads, gt)) return FLOD_ERR_INVALID_ARG;
   const Ws w = ws_ptrs(ws, P);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   return with_batch(sets, n_sets, views, n_views, cfg, P,

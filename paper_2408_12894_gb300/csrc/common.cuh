@@ -93,7 +93,7 @@ struct Ws {
 };
 
 // radix-sort plan words (uint32 plan[64])
-constexpr int kPlanPasses = 8;       // at most 8 digit passes of 8 bits over 64-bit keys
+constexpr int kPlanPasses = 8;       // at most 8 digit passes over 64-bit keys
 constexpr int kPlanActive = 0;       // plan[kPlanActive + p] = 1 if pass p moves keys
 constexpr int kPlanSrc = 8;          // plan[kPlanSrc + p] = source buffer of pass p
 constexpr int kPlanLb = 16;          // plan[kPlanLb + p] = look-back table of pass p
@@ -107,7 +107,9 @@ constexpr int kPlanEvalFwd = 48;     // uint64 running count of forward evaluati
 constexpr int kPlanEvalBwd = 50;     // uint64 running count of backward evaluations
 constexpr int kPlanFinal = 63;       // buffer holding the sorted result
 
-constexpr int kSortThreads = 512;
+constexpr int kRadixBits = 9;                        // digit width of one sort pass
+constexpr int kRadixBins = 1 << kRadixBits;          // 512 digit values
+constexpr int kSortThreads = 512;                    // one thread per digit value
 constexpr int kSortKeysPerThread = 8;
 constexpr int kSortPart = kSortThreads * kSortKeysPerThread;   // 4096 keys per partition
 
@@ -163,6 +165,12 @@ constexpr float kNegHalfLog2e = -0.5f * 1.4426950408889634f;
 // (a, b, c, o) -> (a k, 2 b k, c k, o) with k = -log2(e)/2
 __device__ __forceinline__ float4 scale_conic(float4 co) {
   return make_float4(co.x * kNegHalfLog2e, 2.f * co.y * kNegHalfLog2e, co.z * kNegHalfLog2e, co.w);
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {

@@ -5,9 +5,12 @@
 
 namespace flod {
 
+// How the preprocess backward writes a set's gradients.
+enum GradMode : int { kGradAccumulate = 0, kGradAtomic = 1, kGradOverwrite = 2 };
+
 struct GradTable {
   flod_grads g[FLOD_MAX_SETS];
-  int shared[FLOD_MAX_SETS];   // 1: several units may update one Gaussian -> atomics
+  int mode[FLOD_MAX_SETS];   // GradMode: RMW (one unit per Gaussian), atomics, or store
 };
 
 // preprocess.cu

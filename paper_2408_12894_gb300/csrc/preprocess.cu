@@ -196,9 +196,42 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batc
 // ---------------------------------------------------------------------------------------
 // backward
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void add_grad(float* p, float v, bool atomic) {
-  if (v == 0.f) return;
-  if (atomic) atomicAdd(p, v); else *p += v;
+// Writes v into one gradient slot: read-modify-write, atomic add or plain store.
+__device__ __forceinline__ void put1(float* p, float v, int mode) {
+  if (mode == kGradOverwrite) *p = v;
+  else if (v != 0.f) {
+    if (mode == kGradAtomic) atomicAdd(p, v);
+    else *p += v;
+  }
+}
+__device__ __forceinline__ void put4(float* p, float4 v, int mode) {   // p 16-byte aligned
+  float4* q = reinterpret_cast<float4*>(p);
+  if (mode == kGradOverwrite) {
+    *q = v;
+  } else if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
+    if (mode == kGradAtomic) {
+      atomicAdd(q, v);
+    } else {
+      float4 o = *q;
+      *q = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+    }
+  }
+}
+
+// Zero gradients of one Gaussian (overwrite mode, Gaussian not rendered).
+__device__ __forceinline__ void zero_grads(const flod_grads& GR, uint32_t gi, int K, int deg) {
+  if (GR.means) for (int k = 0; k < 3; ++k) GR.means[3ull * gi + k] = 0.f;
+  if (GR.quats) *reinterpret_cast<float4*>(GR.quats + 4ull * gi) = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (GR.s_opt) for (int k = 0; k < 3; ++k) GR.s_opt[3ull * gi + k] = 0.f;
+  if (GR.opacity_logit) GR.opacity_logit[gi] = 0.f;
+  if (GR.sh) {
+    float* gs = GR.sh + 3ull * K * gi;
+    if (deg == 3) {
+      for (int i = 0; i < 12; ++i) reinterpret_cast<float4*>(gs)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int i = 0; i < 3 * K; ++i) gs[i] = 0.f;
+    }
+  }
 }
 
 template <int MAXV>
@@ -206,52 +239,70 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
                                                         Ws ws, GradTable gt) {
   const uint32_t u = blockIdx.x * 128u + threadIdx.x;
   if (u >= b.units) return;
-  if (ws.tiles_touched[u] == 0) return;
   const int vi = view_of_unit(b, u);
   const ViewP& V = b.views[vi];
   int si = 0;
   uint32_t gi = 0;
   if (!unit_source(b, V, u - V.unit_off, si, gi)) return;
+  const SetP& S = b.sets[si];
+  const flod_grads& GR = gt.g[si];
+  const int mode = gt.mode[si];
+  const int K = (S.deg + 1) * (S.deg + 1);
+  if (ws.tiles_touched[u] == 0) {
+    if (mode == kGradOverwrite) zero_grads(GR, gi, K, S.deg);
+    return;
+  }
   const float4 g0 = ws.grad2d[3ull * u];      // du, dv, dopacity
   const float4 g1 = ws.grad2d[3ull * u + 1];  // da, db, dc
   const float4 g2 = ws.grad2d[3ull * u + 2];  // dr, dg, db
-  const SetP& S = b.sets[si];
-  const flod_grads& GR = gt.g[si];
-  const bool atomic = gt.shared[si] != 0;
   Geom G;
   geometry(S, gi, V, b.cfg, G);
 
   // ---- colour -> SH coefficients and view direction
   float Y[16], dir[3], dlen, raw[3];
   sh_colour(S, gi, V, Y, dir, dlen, raw);
-  float drgb[3] = {raw[0] > 0.f ? g2.x : 0.f, raw[1] > 0.f ? g2.y : 0.f, raw[2] > 0.f ? g2.z : 0.f};
-  const int K = (S.deg + 1) * (S.deg + 1);
+  const float drgb[3] = {raw[0] > 0.f ? g2.x : 0.f, raw[1] > 0.f ? g2.y : 0.f,
+                         raw[2] > 0.f ? g2.z : 0.f};
   float dmu[3] = {0.f, 0.f, 0.f};
   if (drgb[0] != 0.f || drgb[1] != 0.f || drgb[2] != 0.f) {
     const float* c = S.sh + 3ull * K * gi;
     float wk[16];
-    for (int k = 0; k < K; ++k)
-      wk[k] = __ldg(c + 3 * k) * drgb[0] + __ldg(c + 3 * k + 1) * drgb[1] + __ldg(c + 3 * k + 2) * drgb[2];
-    if (GR.sh) {
-      float* gs = GR.sh + 3ull * K * gi;
-      for (int k = 0; k < K; ++k) {
-        add_grad(gs + 3 * k, Y[k] * drgb[0], atomic);
-        add_grad(gs + 3 * k + 1, Y[k] * drgb[1], atomic);
-        add_grad(gs + 3 * k + 2, Y[k] * drgb[2], atomic);
-      }
-    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      wk[k] = k < K ? __ldg(c + 3 * k) * drgb[0] + __ldg(c + 3 * k + 1) * drgb[1] +
+                          __ldg(c + 3 * k + 2) * drgb[2]
+                    : 0.f;
     float gx, gy, gz;
     sh_grad_dir(S.deg, dir[0], dir[1], dir[2], wk, gx, gy, gz);
-    float proj = gx * dir[0] + gy * dir[1] + gz * dir[2];
-    float il = 1.f / dlen;
+    const float proj = gx * dir[0] + gy * dir[1] + gz * dir[2];
+    const float il = 1.f / dlen;
     dmu[0] += (gx - proj * dir[0]) * il;
     dmu[1] += (gy - proj * dir[1]) * il;
     dmu[2] += (gz - proj * dir[2]) * il;
   }
+  if (GR.sh) {
+    float* gs = GR.sh + 3ull * K * gi;
+    if (S.deg == 3) {
+      // 48 values Y[k] * drgb[c] at index 3k + c, as 12 float4
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        float e[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int idx = 4 * q + t;
+          e[t] = Y[idx / 3] * drgb[idx % 3];
+        }
+        put4(gs + 4 * q, make_float4(e[0], e[1], e[2], e[3]), mode);
+      }
+    } else {
+      for (int k = 0; k < K; ++k)
+        for (int c = 0; c < 3; ++c) put1(gs + 3 * k + c, Y[k] * drgb[c], mode);
+    }
+  }
 
   // ---- opacity
   const float o = 1.f / (1.f + expf(-__ldg(S.logit + gi)));
-  if (GR.opacity_logit) add_grad(GR.opacity_logit + gi, g0.z * o * (1.f - o), atomic);
+  if (GR.opacity_logit) put1(GR.opacity_logit + gi, g0.z * o * (1.f - o), mode);
 
   // ---- conic (a, b, c) -> Sigma' (A, B, C)
   const float A = G.A, B = G.B, C = G.C;
@@ -289,21 +340,23 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
     }
   if (GR.s_opt) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) add_grad(GR.s_opt + 3ull * gi + k, ds[k] * G.es[k], atomic);
+    for (int k = 0; k < 3; ++k) put1(GR.s_opt + 3ull * gi + k, ds[k] * G.es[k], mode);
   }
   // ---- R(q_n) -> dq_n -> dq
   if (GR.quats) {
     const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
-    float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    float dx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] - 2.f * x * dR[8]);
-    float dy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] - 2.f * y * dR[8]);
-    float dz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] + x * dR[6] + y * dR[7]);
-    float dot = w * dw + x * dx + y * dy + z * dz;
-    float* gq = GR.quats + 4ull * gi;
-    add_grad(gq, (dw - w * dot) * G.qinv, atomic);
-    add_grad(gq + 1, (dx - x * dot) * G.qinv, atomic);
-    add_grad(gq + 2, (dy - y * dot) * G.qinv, atomic);
-    add_grad(gq + 3, (dz - z * dot) * G.qinv, atomic);
+    const float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    const float dx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] +
+                            z * dR[6] + w * dR[7] - 2.f * x * dR[8]);
+    const float dy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] -
+                            w * dR[6] + z * dR[7] - 2.f * y * dR[8]);
+    const float dz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] +
+                            y * dR[5] + x * dR[6] + y * dR[7]);
+    const float dot = w * dw + x * dx + y * dy + z * dz;
+    put4(GR.quats + 4ull * gi,
+         make_float4((dw - w * dot) * G.qinv, (dx - x * dot) * G.qinv, (dy - y * dot) * G.qinv,
+                     (dz - z * dot) * G.qinv),
+         mode);
   }
   // ---- T = J W -> dJ -> dt ; mean2d -> dt
   const float* W = V.vm;
@@ -336,7 +389,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
   dmu[2] += W[2] * dt0 + W[6] * dt1 + W[10] * dt2;
   if (GR.means) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) add_grad(GR.means + 3ull * gi + k, dmu[k], atomic);
+    for (int k = 0; k < 3; ++k) put1(GR.means + 3ull * gi + k, dmu[k], mode);
   }
 }
 

@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
             have_c = true;
           }
           any = true;
-          const float ioma = __frcp_rn(1.f - a);
+          const float ioma = rcp_approx(1.f - a);
           T[j] *= ioma;
           const float w = a * T[j];
           acc[6] += w * g0[j];

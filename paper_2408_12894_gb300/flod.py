@@ -61,7 +61,7 @@ class RasterConfig(C.Structure):
 
 class Grads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("quats", C.c_void_p), ("s_opt", C.c_void_p),
-                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p)]
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("overwrite", C.c_int)]
 
 
 class WsLayout(C.Structure):
@@ -257,9 +257,10 @@ def flod_preprocess_bwd(sets, views, cfg, ws, pair_capacity, grads, stream=None)
                                      _stream(stream)), "flod_preprocess_bwd")
 
 
-def grads_struct(grads):
-    """grads: per set, a sequence of 5 tensors (or None) in GaussianSet.FIELDS order."""
-    return _array(Grads, [Grads(*[_ptr(t) for t in gr]) for gr in grads])
+def grads_struct(grads, overwrite: bool = False):
+    """grads: per set, a sequence of 5 tensors (or None) in GaussianSet.FIELDS order.
+    overwrite: write the gradients instead of adding to them (see flod_grads)."""
+    return _array(Grads, [Grads(*[_ptr(t) for t in gr], int(overwrite)) for gr in grads])
 
 
 def flod_select_scratch_size(levels) -> int:

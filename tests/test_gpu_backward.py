@@ -72,3 +72,26 @@ def test_backward_zero_upstream_gives_zero():
     got, _ = _gpu_grads(g, cams, 0.0, np.zeros(3 * 64 * 64, np.float32))
     for v in got.values():
         assert np.all(v == 0)
+
+
+def test_overwrite_mode_equals_accumulate_into_zeros():
+    g = synth.gaussian_set(12, 3000, k=8, radius=1.0, sh_degree=3, s_mean=-3.0)
+    cam = synth.camera((0.3, -0.2, -3.0), 96, 64)
+    dL = torch.as_tensor(synth.upstream_gradient(13, [cam]), device="cuda")
+    rast = rasterizer([g], [cam], [0.02])
+    rgb, T, nc = rast.forward()
+    acc = [[torch.zeros_like(getattr(rast.sets[0], f)) for f in flod.GaussianSet.FIELDS]]
+    rast.render_bwd(dL, T, nc, acc)
+    over = [[torch.full_like(getattr(rast.sets[0], f), 7.5) for f in flod.GaussianSet.FIELDS]]
+    rast.blend_bwd(dL, T, nc)
+    rast.preprocess_bwd(flod.grads_struct(over, overwrite=True))
+    torch.cuda.synchronize()
+    for a, b in zip(acc[0], over[0]):
+        assert torch.equal(a, b)
+    # a set that two views render cannot be overwritten
+    rast2 = rasterizer([g], [cam, cam], [0.02])
+    rgb2, T2, nc2 = rast2.forward()
+    dL2 = torch.zeros(2 * dL.numel(), device="cuda")
+    rast2.blend_bwd(dL2, T2, nc2)
+    with pytest.raises(flod.FlodError):
+        rast2.preprocess_bwd(flod.grads_struct(over, overwrite=True))
