@@ -7,7 +7,7 @@
 //   k_plan   per digit: exclusive digit offsets; a digit on which all keys agree is marked
 //            inactive and costs nothing; ping-pong buffer and look-back table per pass.
 //   k_pass   persistent CTAs take 4096-key partitions in ticket order. Per partition:
-//            warp-level ranking by 9 ballots per key (stable: lane, round, warp order =
+//            warp-level ranking with one match.any per key (stable: lane, round, warp order =
 //            input order), publish the per-digit counts (aggregate), look back over
 //            predecessors until an inclusive prefix is found, publish the inclusive prefix,
 //            reorder the partition in shared memory and write each digit's run contiguously.
@@ -155,12 +155,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
     for (int r = 0; r < kSortKeysPerThread; ++r) {
       const bool valid = wbase + r * 32 < P;
       const uint32_t dg = (uint32_t)(k[r] >> shift) & (kRadixBins - 1);
-      uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-      for (int bit = 0; bit < kRadixBits; ++bit) {
-        const uint32_t bb = __ballot_sync(0xffffffffu, (dg >> bit) & 1u);
-        peers &= ((dg >> bit) & 1u) ? bb : ~bb;
-      }
+      // lanes holding the same digit (a lane past the end matches only itself)
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? dg : 0x10000u | (uint32_t)lane);
       uint32_t before = 0;
       if (valid) before = sm.whist[wid][dg];
       __syncwarp();
