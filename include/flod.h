@@ -129,8 +129,10 @@ typedef struct {
   size_t tiles_touched; /* uint32 [units], 0 when culled */
   size_t block_sums;    /* uint64 [units/1024 + 1] exclusive pair offsets per 1024 units */
   size_t slices;        /* uint32 [units/1024 + 1] exclusive count of 4096-pair emission slices */
-  size_t keys[2];       /* uint64 [pair_capacity] x 2 (emission buffer is keys[0]) */
-  size_t vals[2];       /* uint32 [pair_capacity] x 2 */
+  size_t ukeys[2];      /* uint32 [units] x 2: depth keys of the unit-stage sort */
+  size_t uvals[2];      /* uint32 [units] x 2: units in depth order (plan[45] = result buffer) */
+  size_t keys[2];       /* uint32 [pair_capacity] x 2: tile ids of the pairs (keys[0] = emitted) */
+  size_t vals[2];       /* uint32 [pair_capacity] x 2: units of the pairs */
   size_t hist;          /* radix-sort digit histograms */
   size_t lookback;      /* radix-sort decoupled look-back tables */
   size_t ranges;        /* uint32x2 [tiles] [start, end) in the sorted pair list */
@@ -171,11 +173,15 @@ flod_status flod_preprocess(const flod_gaussians *sets, int n_sets, const flod_v
                             int n_views, const flod_raster_config *cfg, void *ws,
                             size_t ws_bytes, uint64_t pair_capacity, flod_stream stream);
 
-/* (tile, depth) binning and sort: key = (global tile << 32) | float bits of t_z for every
- * (unit, covered tile), emitted in unit order; a stable LSD radix sort (onesweep, decoupled
- * look-back) orders them, so ties in depth keep unit order; then the [start, end) range of
- * every tile. Writes the pair total to *d_pair_count (device, may be NULL) and to the
- * workspace. Pairs beyond pair_capacity are dropped and FLOD_DEV_CAPACITY is set. */
+/* (tile, depth) binning and sort: the pairs (unit, covered tile) end up ordered by the key
+ * (global tile << 32) | float bits of t_z, ties by unit index -- the stable sort of the pairs
+ * emitted in unit order. It is a stable LSD radix sort (9-bit digits, onesweep passes with
+ * decoupled look-back) whose depth digits are sorted over units before the pairs are
+ * emitted, since all pairs of a unit share them, and whose tile digits are sorted over the
+ * pairs. Then the [start, end) range of every tile. The result is vals[plan[63]] (units)
+ * with keys[plan[63]] (tile ids). Writes the pair total to *d_pair_count (device, may be
+ * NULL) and to the workspace. Pairs beyond pair_capacity are dropped and FLOD_DEV_CAPACITY
+ * is set. */
 flod_status flod_bin_sort(const flod_gaussians *sets, int n_sets, const flod_view *views,
                           int n_views, const flod_raster_config *cfg, void *ws, size_t ws_bytes,
                           uint64_t pair_capacity, uint64_t *d_pair_count, flod_stream stream);

@@ -128,8 +128,10 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   if (u >= (1ull << 32) || t >= (1ull << 31)) return FLOD_ERR_INVALID_ARG;
   int tile_bits = 1;
   while (tile_bits < 31 && (1ull << tile_bits) < t) ++tile_bits;
-  P.n_passes = (32 + tile_bits + kRadixBits - 1) / kRadixBits;
-  P.max_parts = (uint32_t)((pair_capacity + kSortPart - 1) / kSortPart);
+  P.n_passes = (tile_bits + kRadixBits - 1) / kRadixBits;   // tile digits over the pairs
+  const uint64_t parts_pairs = (pair_capacity + kSortPart - 1) / kSortPart;
+  const uint64_t parts_units = (u + kSortPart - 1) / kSortPart;
+  P.max_parts = (uint32_t)(parts_pairs > parts_units ? parts_pairs : parts_units);
   if (P.max_parts == 0) P.max_parts = 1;
 
   flod_ws_layout& L = P.L;
@@ -151,8 +153,12 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   L.tiles_touched = take(4 * u);
   L.block_sums = take(8 * (u / kScanBlock + 1));
   L.slices = take(4 * (u / kScanBlock + 1));
-  L.keys[0] = take(8 * pair_capacity);
-  L.keys[1] = take(8 * pair_capacity);
+  L.ukeys[0] = take(4 * u);
+  L.ukeys[1] = take(4 * u);
+  L.uvals[0] = take(4 * u);
+  L.uvals[1] = take(4 * u);
+  L.keys[0] = take(4 * pair_capacity);
+  L.keys[1] = take(4 * pair_capacity);
   L.vals[0] = take(4 * pair_capacity);
   L.vals[1] = take(4 * pair_capacity);
   L.hist = take(4 * kPlanPasses * kRadixBins);
@@ -184,7 +190,9 @@ Ws ws_ptrs(void* base, const Plan& P) {
   w.block_sums = reinterpret_cast<unsigned long long*>(b + L.block_sums);
   w.slices = reinterpret_cast<uint32_t*>(b + L.slices);
   for (int i = 0; i < 2; ++i) {
-    w.keys[i] = reinterpret_cast<unsigned long long*>(b + L.keys[i]);
+    w.ukeys[i] = reinterpret_cast<uint32_t*>(b + L.ukeys[i]);
+    w.uvals[i] = reinterpret_cast<uint32_t*>(b + L.uvals[i]);
+    w.keys[i] = reinterpret_cast<uint32_t*>(b + L.keys[i]);
     w.vals[i] = reinterpret_cast<uint32_t*>(b + L.vals[i]);
   }
   w.hist = reinterpret_cast<uint32_t*>(b + L.hist);
@@ -194,6 +202,7 @@ Ws ws_ptrs(void* base, const Plan& P) {
   w.queue = reinterpret_cast<uint32_t*>(b + L.queue);
   w.pair_capacity = L.pair_capacity;
   w.max_parts = P.max_parts;
+  w.units = (uint32_t)L.units;
   return w;
 }
 

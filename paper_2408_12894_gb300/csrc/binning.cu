@@ -1,30 +1,32 @@
-// Tile binning: per-1024-unit pair counts, their exclusive scan, key emission, and the
-// per-tile [start, end) ranges of the sorted list.
-//
-// Keys are (global tile id << 32) | float bits of the view-space depth t_z (t_z > z_near > 0,
-// so the bits order like the values); every unit emits its tiles in row-major order and
-// units are emitted in index order, so the stable radix sort that follows breaks depth
-// ties by unit index. Pair counts never leave the device: the scan writes the total and
-// the partition count that the sort kernels read.
+// Tile binning. The sort key of a pair is (global tile id << 32) | float bits of its unit's
+// view-space depth t_z (t_z > z_near > 0, so the bits order like the values). The depth half
+// is sorted over units first (sort.cu, stage "units"); this file then walks the units in that
+// order ("slots"): per-1024-slot pair counts, their exclusive scan, emission of each unit's
+// tiles in row-major order with the 32-bit tile id as key, the stable sort of the tile half
+// (stage "pairs"), and the per-tile [start, end) ranges of the result. Within a tile the
+// pairs end up by depth with ties by unit index. Pair counts never leave the device: the
+// scan writes the total and the partition count that the sort kernels read.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace flod {
 
-__global__ void __launch_bounds__(256) k_block_sums(const uint32_t* __restrict__ touched,
-                                                    unsigned long long* __restrict__ bsum) {
+// Pair count of every 1024 slots of the depth-sorted unit order.
+__global__ void __launch_bounds__(256) k_block_sums(Ws ws) {
   __shared__ uint32_t red[8];
-  const uint4 v = reinterpret_cast<const uint4*>(touched)[blockIdx.x * 256u + threadIdx.x];
-  uint32_t s = v.x + v.y + v.z + v.w;
+  const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
+  const uint4 o = reinterpret_cast<const uint4*>(order)[blockIdx.x * 256u + threadIdx.x];
+  uint32_t s = ws.tiles_touched[o.x] + ws.tiles_touched[o.y] + ws.tiles_touched[o.z] +
+               ws.tiles_touched[o.w];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t t = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += red[w];
-    bsum[blockIdx.x] = t;
+    ws.block_sums[blockIdx.x] = t;
   }
 }
 
@@ -103,34 +105,35 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
     uint32_t nparts = (uint32_t)((pe + kSortPart - 1) / kSortPart);
     ws.plan[kPlanNParts] = nparts;
 #pragma unroll
-    for (int p = 0; p < kPlanPasses; ++p) ws.plan[kPlanCounter + p] = 0;
+    for (int p = 4; p < kPlanPasses; ++p) ws.plan[kPlanCounter + p] = 0;   // pair-stage tickets
     ws.plan[kPlanQueue] = 0;
     ws.plan[kPlanQueue + 1] = 0;
     ws.plan[kPlanSlices] = carry_sl;
   }
 }
 
-// Key emission, load-balanced over output positions. Each 1024-unit block's contiguous
-// range of pairs is cut into slices of kEmitSlice positions; persistent CTAs take slices in
-// turn. For its slice a CTA rescans the block's 1024 pair counts in shared memory, fetches
-// the tile rectangle and depth of the units that overlap the slice, and its threads walk
-// the slice's positions: position p belongs to the unit whose prefix range holds it
-// (binary search in shared memory) and its tile is the (p - start)-th tile of that unit's
-// rectangle in row-major order. Writes are coalesced, and a block of huge splats is spread
-// over many CTAs.
+// Key emission in depth-sorted unit order, load-balanced over output positions. Each
+// 1024-slot block's contiguous range of pairs is cut into slices of kEmitSlice positions;
+// persistent CTAs take slices in turn. For its slice a CTA rescans the block's 1024 pair
+// counts in shared memory, fetches the tile rectangle of the units that overlap the slice,
+// and its threads walk the slice's positions: position p belongs to the slot whose prefix
+// range holds it (binary search in shared memory) and its tile is the (p - start)-th tile of
+// that unit's rectangle in row-major order. Writes are coalesced, and a block of huge
+// splats is spread over many CTAs.
 template <int MAXV>
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV> b, Ws ws,
                                               uint32_t nblocks) {
   __shared__ uint32_t s_pre[kScanBlock + 1];
   __shared__ uint32_t s_rect[kScanBlock];     // tx0 | (rect width << 16)
-  __shared__ uint32_t s_row[kScanBlock];      // ty0
-  __shared__ uint32_t s_depth[kScanBlock];
+  __shared__ uint32_t s_tile0[kScanBlock];    // global id of the rectangle's first row, column 0
+  __shared__ uint32_t s_tx[kScanBlock];       // tiles per row of the unit's view
   __shared__ uint32_t warp_tot[8];
   __shared__ uint32_t s_blk;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t n_slices = ws.plan[kPlanSlices];
   const unsigned long long cap = ws.pair_capacity;
-  unsigned long long* keys = ws.keys[0];
+  const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
+  uint32_t* keys = ws.keys[0];
   uint32_t* vals = ws.vals[0];
   for (uint32_t w = blockIdx.x; w < n_slices; w += gridDim.x) {
     if (tid == 0) {                       // the block holding slice w
@@ -144,11 +147,12 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
     __syncthreads();
     const uint32_t blk = s_blk;
     const uint32_t r0 = (w - ws.slices[blk]) * (uint32_t)kEmitSlice;
-    const uint32_t unit0 = blk * (uint32_t)kScanBlock;
-    const ViewP& V = b.views[view_of_unit(b, unit0)];
-    const uint4 tt = reinterpret_cast<const uint4*>(ws.tiles_touched)[blk * 256u + tid];
-    const uint32_t cnt[4] = {tt.x, tt.y, tt.z, tt.w};
-    const uint32_t s = tt.x + tt.y + tt.z + tt.w;
+    const uint4 un = reinterpret_cast<const uint4*>(order)[blk * 256u + tid];
+    const uint32_t unit[4] = {un.x, un.y, un.z, un.w};
+    uint32_t cnt[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cnt[j] = ws.tiles_touched[unit[j]];
+    const uint32_t s = cnt[0] + cnt[1] + cnt[2] + cnt[3];
     uint32_t x = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -163,17 +167,18 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
     const uint32_t r1_full = r0 + (uint32_t)kEmitSlice;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int ul = 4 * tid + j;
-      s_pre[ul] = run;
+      const int sl = 4 * tid + j;
+      s_pre[sl] = run;
       if (cnt[j] && run < r1_full && run + cnt[j] > r0) {
-        const uint32_t u = unit0 + ul;
+        const uint32_t u = unit[j];
+        const ViewP& V = b.views[view_of_unit(b, u)];
         const float2 xy = ws.xy[u];
         int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
         tile_rect(xy.x, xy.y, ws.radius[u], V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0,
                   tx1, ty0, ty1);
-        s_rect[ul] = (uint32_t)tx0 | ((uint32_t)(tx1 - tx0 + 1) << 16);
-        s_row[ul] = (uint32_t)ty0;
-        s_depth[ul] = __float_as_uint(ws.depth[u]);
+        s_rect[sl] = (uint32_t)tx0 | ((uint32_t)(tx1 - tx0 + 1) << 16);
+        s_tile0[sl] = V.tile_off + (uint32_t)ty0 * V.tiles_x;
+        s_tx[sl] = V.tiles_x;
       }
       run += cnt[j];
     }
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
     const unsigned long long base = ws.block_sums[blk];
     for (uint32_t p = r0 + tid; p < r1; p += 256) {
       if (base + p >= cap) break;
-      int lo = 0, hi = kScanBlock - 1;        // last unit with s_pre[u] <= p
+      int lo = 0, hi = kScanBlock - 1;        // last slot with s_pre[slot] <= p
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (s_pre[mid] <= p) lo = mid; else hi = mid - 1;
@@ -192,11 +197,8 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
       const uint32_t k = p - s_pre[lo];
       const uint32_t r = s_rect[lo];
       const uint32_t wdt = r >> 16;
-      const uint32_t tx = (r & 0xffffu) + k % wdt;
-      const uint32_t ty = s_row[lo] + k / wdt;
-      const unsigned long long tile = (unsigned long long)(V.tile_off + ty * V.tiles_x + tx);
-      keys[base + p] = (tile << 32) | s_depth[lo];
-      vals[base + p] = unit0 + (uint32_t)lo;
+      keys[base + p] = s_tile0[lo] + (k / wdt) * s_tx[lo] + (r & 0xffffu) + k % wdt;
+      vals[base + p] = order[blk * (uint32_t)kScanBlock + lo];
     }
     __syncthreads();
   }
@@ -205,11 +207,11 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
 __global__ void __launch_bounds__(256) k_ranges(Ws ws) {
   const unsigned long long P0 = *ws.pair_count;
   const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
-  const unsigned long long* keys = ws.keys[ws.plan[kPlanFinal]];
+  const uint32_t* keys = ws.keys[ws.plan[kPlanFinal]];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ws.ranges[t].x = i;
-    if (i == P - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ws.ranges[t].y = i + 1;
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ws.ranges[t].x = i;
+    if (i == P - 1 || keys[i + 1] != t) ws.ranges[t].y = i + 1;
   }
 }
 
@@ -259,12 +261,13 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
     if (e != cudaSuccess) return e;
   }
   if (nblocks) {
-    k_block_sums<<<nblocks, 256, 0, st>>>(ws.tiles_touched, ws.block_sums);
+    if ((e = launch_unit_sort(ws, resident_small, resident_sort, st)) != cudaSuccess) return e;
+    k_block_sums<<<nblocks, 256, 0, st>>>(ws);
   }
   k_scan_blocks<<<1, 1024, 0, st>>>(ws, nblocks, d_pair_count);
   if (nblocks) k_emit<MAXV><<<resident_small, 256, 0, st>>>(b, ws, nblocks);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_radix_sort(ws, n_passes, resident_small, resident_sort, st)) != cudaSuccess) return e;
+  if ((e = launch_pair_sort(ws, n_passes, resident_small, resident_sort, st)) != cudaSuccess) return e;
   k_ranges<<<resident_small, 256, 0, st>>>(ws);
   if (build_queue && b.tiles) {
     if ((e = cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t) * kQueueHeader, st)) != cudaSuccess)

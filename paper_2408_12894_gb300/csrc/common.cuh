@@ -81,8 +81,10 @@ struct Ws {
   uint32_t* tiles_touched;
   unsigned long long* block_sums;
   uint32_t* slices;
-  unsigned long long* keys[2];
-  uint32_t* vals[2];
+  uint32_t* ukeys[2];      // unit-stage sort: depth keys
+  uint32_t* uvals[2];      // unit-stage sort: unit indices (the result is the emission order)
+  uint32_t* keys[2];       // pair-stage sort: tile keys
+  uint32_t* vals[2];       // pair-stage sort: unit indices (the result is what renders read)
   uint32_t* hist;
   unsigned long long* lookback;
   uint2* ranges;
@@ -90,10 +92,11 @@ struct Ws {
   uint32_t* queue;
   uint64_t pair_capacity;
   uint32_t max_parts;
+  uint32_t units;
 };
 
 // radix-sort plan words (uint32 plan[64])
-constexpr int kPlanPasses = 8;       // at most 8 digit passes over 64-bit keys
+constexpr int kPlanPasses = 8;       // slots 0-3: depth digits over units; 4-7: tile digits over pairs
 constexpr int kPlanActive = 0;       // plan[kPlanActive + p] = 1 if pass p moves keys
 constexpr int kPlanSrc = 8;          // plan[kPlanSrc + p] = source buffer of pass p
 constexpr int kPlanLb = 16;          // plan[kPlanLb + p] = look-back table of pass p
@@ -101,6 +104,8 @@ constexpr int kPlanCounter = 24;     // plan[kPlanCounter + p] = partition ticke
 constexpr int kPlanNParts = 40;      // number of partitions
 constexpr int kPlanQueue = 41;       // render work-queue ticket counter (x2: fwd, bwd)
 constexpr int kPlanSlices = 43;      // number of key-emission slices
+constexpr int kPlanNPartsUnits = 44; // partitions of the unit-stage sort
+constexpr int kPlanFinalUnits = 45;  // buffer holding the depth-sorted unit order
 constexpr int kEmitSlice = 4096;     // output positions per emission slice
 constexpr int kQueueHeader = 66;     // queue[0..32] bucket counts, [33..65] offsets, then tiles
 constexpr int kPlanEvalFwd = 48;     // uint64 running count of forward evaluations

@@ -27,8 +27,9 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
                            cudaStream_t st);
 
 // sort.cu
-cudaError_t launch_radix_sort(const Ws& ws, int n_passes, int resident_hist, int resident_sort,
-                              cudaStream_t st);
+cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st);
+cudaError_t launch_pair_sort(const Ws& ws, int n_digits, int resident_small, int resident_sort,
+                             cudaStream_t st);
 int sort_kernel_smem_bytes();
 cudaError_t sort_kernel_prepare();           // opt-in shared memory size
 const void* sort_kernel_ptr();

@@ -1,16 +1,25 @@
-// Stable LSD radix sort of the (tile, depth) pairs: 9-bit digits (512 values; 45-bit keys of
-// a 1080p frame take 5 passes), one "onesweep" pass per digit with decoupled look-back (Merrill & Garland's single-pass prefix scan, as used by
+// Stable LSD radix sort of the (tile, depth) pairs, 9-bit digits, one "onesweep" pass per
+// digit with decoupled look-back (Merrill & Garland's single-pass prefix scan, as used by
 // onesweep sorting), all sizes read on the device.
 //
-//   k_hist   one read of all keys: the histograms of every digit at once; clears the first
-//            look-back table.
-//   k_plan   per digit: exclusive digit offsets; a digit on which all keys agree is marked
-//            inactive and costs nothing; ping-pong buffer and look-back table per pass.
-//   k_pass   persistent CTAs take 4096-key partitions in ticket order. Per partition:
-//            warp-level ranking with one match.any per key (stable: lane, round, warp order =
-//            input order), publish the per-digit counts (aggregate), look back over
-//            predecessors until an inclusive prefix is found, publish the inclusive prefix,
-//            reorder the partition in shared memory and write each digit's run contiguously.
+// Every pair of a unit carries the same 32 depth bits, so the depth digits (the low half of
+// the key) are sorted over units before any pair exists (stage "units": key = depth bits,
+// value = unit); the pairs are then emitted in that order and only the tile digits (the
+// high half) are sorted over the pairs (stage "pairs": key = tile id, value = unit). Both
+// stages are stable and the units start in index order, so the result is the stable sort of
+// (tile << 32 | depth bits) over pairs emitted in unit order: within a tile by depth, ties
+// by unit index.
+//
+//   k_unit_keys  unit keys (depth bits, or all ones for a unit with no tile) and the digit
+//                histograms of stage "units"; clears the first look-back table.
+//   k_hist       the digit histograms of the pair keys; clears the first look-back table.
+//   k_plan       per digit: exclusive digit offsets; a digit on which all keys agree is
+//                marked inactive and costs nothing; ping-pong buffer and table per pass.
+//   k_pass       persistent CTAs take 4096-key partitions in ticket order. Per partition:
+//                warp-level ranking with one match.any per key (stable: lane, round, warp
+//                order = input order), publish the per-digit counts (aggregate), reorder the
+//                partition in shared memory, look back over predecessors until an inclusive
+//                prefix is found, publish the inclusive prefix, write each digit's run.
 //
 // Every wait on a predecessor is bounded; when the bound is hit the kernel sets
 // FLOD_DEV_TIMEOUT in the status word and continues (the output is then invalid, the
@@ -36,37 +45,83 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(256) k_hist(Ws ws, int n_passes) {
-  __shared__ uint32_t h[kPlanPasses * kRadixBins];
-  for (int i = threadIdx.x; i < kPlanPasses * kRadixBins; i += 256) h[i] = 0;
+// One sort stage: ping-pong key/value buffers, its element count and its plan slots.
+struct Stage {
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  const unsigned long long* count;   // device element count (pair stage), or NULL
+  uint32_t fixed_count;              // element count when `count` is NULL (unit stage)
+  uint64_t cap;                      // elements beyond cap are ignored
+  int slot0;                         // first plan slot (digit d uses slot slot0 + d)
+  int nparts_word;                   // plan word holding the partition count
+  int final_word;                    // plan word receiving the result's buffer index
+};
+
+__device__ __forceinline__ uint32_t stage_count(const Stage& s) {
+  if (!s.count) return s.fixed_count;
+  const unsigned long long c = *s.count;
+  return (uint32_t)(c < s.cap ? c : s.cap);
+}
+
+__device__ __forceinline__ void block_hist_flush(const uint32_t* h, uint32_t* hist, int n_digits) {
+  for (int i = threadIdx.x; i < n_digits * kRadixBins; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// Stage "units": key = float bits of the view-space depth of a unit with tiles (positive, so
+// the bits order like the values), all ones otherwise; value = unit index.
+__global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st, int n_digits) {
+  __shared__ uint32_t h[4 * kRadixBins];
+  for (int i = threadIdx.x; i < 4 * kRadixBins; i += 256) h[i] = 0;
   __syncthreads();
-  const unsigned long long P0 = *ws.pair_count;
-  const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
-  const unsigned long long* keys = ws.keys[0];
+  const uint32_t U = st.fixed_count;
   const uint32_t stride = gridDim.x * 256u;
-  for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < P; i += stride) {
-    const unsigned long long k = keys[i];
-    for (int p = 0; p < n_passes; ++p)
-      atomicAdd(&h[p * kRadixBins + (uint32_t)((k >> (kRadixBits * p)) & (kRadixBins - 1))], 1u);
+  for (uint32_t u = blockIdx.x * 256u + threadIdx.x; u < U; u += stride) {
+    const uint32_t key = ws.tiles_touched[u] ? __float_as_uint(ws.depth[u]) : 0xffffffffu;
+    st.keys[0][u] = key;
+    st.vals[0][u] = u;
+    for (int d = 0; d < n_digits; ++d)
+      atomicAdd(&h[d * kRadixBins + ((key >> (kRadixBits * d)) & (kRadixBins - 1))], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n_passes * kRadixBins; i += 256)
-    if (h[i]) atomicAdd(&ws.hist[i], h[i]);
-  const uint32_t nparts = ws.plan[kPlanNParts];
+  block_hist_flush(h, ws.hist + st.slot0 * kRadixBins, n_digits);
+  const uint32_t nparts = (U + kSortPart - 1) / kSortPart;
+  for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < nparts * (uint32_t)kRadixBins; i += stride)
+    ws.lookback[i] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < 4) ws.plan[kPlanCounter + st.slot0 + threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ws.plan[st.nparts_word] = nparts;
+}
+
+// Stage "pairs": histograms of the tile keys the emission wrote.
+__global__ void __launch_bounds__(256) k_hist(Ws ws, Stage st, int n_digits) {
+  __shared__ uint32_t h[4 * kRadixBins];
+  for (int i = threadIdx.x; i < 4 * kRadixBins; i += 256) h[i] = 0;
+  __syncthreads();
+  const uint32_t P = stage_count(st);
+  const uint32_t* keys = st.keys[0];
+  const uint32_t stride = gridDim.x * 256u;
+  for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < P; i += stride) {
+    const uint32_t k = keys[i];
+    for (int d = 0; d < n_digits; ++d)
+      atomicAdd(&h[d * kRadixBins + ((k >> (kRadixBits * d)) & (kRadixBins - 1))], 1u);
+  }
+  __syncthreads();
+  block_hist_flush(h, ws.hist + st.slot0 * kRadixBins, n_digits);
+  const uint32_t nparts = ws.plan[st.nparts_word];
   for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < nparts * (uint32_t)kRadixBins; i += stride)
     ws.lookback[i] = 0;
 }
 
-__global__ void __launch_bounds__(kRadixBins) k_plan(Ws ws, int n_passes) {
+__global__ void __launch_bounds__(kRadixBins) k_plan(Ws ws, Stage st, int n_digits) {
   __shared__ uint32_t wsum[kRadixBins / 32];
-  const unsigned long long P0 = *ws.pair_count;
-  const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
+  const uint32_t P = stage_count(st);
   const int d = threadIdx.x, lane = d & 31, wid = d >> 5;
   int src = 0, nact = 0;
-  for (int p = 0; p < n_passes; ++p) {
-    const uint32_t c = ws.hist[p * kRadixBins + d];
+  for (int p = 0; p < 4; ++p) {
+    const int slot = st.slot0 + p;
+    const uint32_t c = p < n_digits ? ws.hist[slot * kRadixBins + d] : 0u;
     const int one_bin = __syncthreads_or(c == P);
-    const bool active = P > 0 && !one_bin;
+    const bool active = p < n_digits && P > 0 && !one_bin;
     uint32_t x = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -77,29 +132,26 @@ __global__ void __launch_bounds__(kRadixBins) k_plan(Ws ws, int n_passes) {
     __syncthreads();
     uint32_t pre = 0;
     for (int w = 0; w < wid; ++w) pre += wsum[w];
-    ws.hist[p * kRadixBins + d] = pre + x - c;
+    ws.hist[slot * kRadixBins + d] = pre + x - c;
     __syncthreads();
     if (d == 0) {
-      ws.plan[kPlanActive + p] = active ? 1u : 0u;
-      ws.plan[kPlanSrc + p] = (uint32_t)src;
-      ws.plan[kPlanLb + p] = (uint32_t)(nact & 1);
+      ws.plan[kPlanActive + slot] = active ? 1u : 0u;
+      ws.plan[kPlanSrc + slot] = (uint32_t)src;
+      ws.plan[kPlanLb + slot] = (uint32_t)(nact & 1);
     }
     if (active) {
       src ^= 1;
       ++nact;
     }
   }
-  for (int p = n_passes + d; p < kPlanPasses; p += kRadixBins) {
-    if (p >= n_passes) ws.plan[kPlanActive + p] = 0;
-  }
-  if (d == 0) ws.plan[kPlanFinal] = (uint32_t)src;
+  if (d == 0) ws.plan[st.final_word] = (uint32_t)src;
 }
 
 constexpr int kSortWarps = kSortThreads / 32;
 static_assert(kSortThreads == kRadixBins, "one thread per digit value in the partition steps");
 
 struct SortSmem {
-  unsigned long long keys[kSortPart];
+  uint32_t keys[kSortPart];
   uint32_t vals[kSortPart];
   uint32_t whist[kSortWarps][kRadixBins];   // per-warp digit counts, then per-warp prefixes
   uint32_t local_start[kRadixBins];
@@ -112,29 +164,29 @@ struct SortSmem {
 // 32 * kSortKeysPerThread consecutive keys starting at w * 32 * kSortKeysPerThread, round by
 // round, so (warp, round, lane) order is input order and the ranking is stable. Thread d
 // then owns digit value d for the partition-level steps.
-__global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
+__global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int digit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
-  if (!ws.plan[kPlanActive + pass]) return;
-  const int src = (int)ws.plan[kPlanSrc + pass];
-  const int lbt = (int)ws.plan[kPlanLb + pass];
-  const unsigned long long* __restrict__ kin = ws.keys[src];
-  const uint32_t* __restrict__ vin = ws.vals[src];
-  unsigned long long* __restrict__ kout = ws.keys[src ^ 1];
-  uint32_t* __restrict__ vout = ws.vals[src ^ 1];
-  const unsigned long long P0 = *ws.pair_count;
-  const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
-  const uint32_t nparts = ws.plan[kPlanNParts];
+  const int slot = st.slot0 + digit;
+  if (!ws.plan[kPlanActive + slot]) return;
+  const int src = (int)ws.plan[kPlanSrc + slot];
+  const int lbt = (int)ws.plan[kPlanLb + slot];
+  const uint32_t* __restrict__ kin = src ? st.keys[1] : st.keys[0];
+  const uint32_t* __restrict__ vin = src ? st.vals[1] : st.vals[0];
+  uint32_t* __restrict__ kout = src ? st.keys[0] : st.keys[1];
+  uint32_t* __restrict__ vout = src ? st.vals[0] : st.vals[1];
+  const uint32_t P = stage_count(st);
+  const uint32_t nparts = ws.plan[st.nparts_word];
   unsigned long long* lb = ws.lookback + (size_t)lbt * ws.max_parts * kRadixBins;
   unsigned long long* lb_next = ws.lookback + (size_t)(lbt ^ 1) * ws.max_parts * kRadixBins;
-  const uint32_t* goff = ws.hist + pass * kRadixBins;
-  const int shift = kRadixBits * pass;
+  const uint32_t* goff = ws.hist + slot * kRadixBins;
+  const int shift = kRadixBits * digit;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int d = tid;   // digit value owned in the partition steps
 
   for (;;) {
-    if (tid == 0) sm.part = atomicAdd(&ws.plan[kPlanCounter + pass], 1u);
+    if (tid == 0) sm.part = atomicAdd(&ws.plan[kPlanCounter + slot], 1u);
     for (int i = tid; i < kSortWarps * kRadixBins; i += kSortThreads) (&sm.whist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t part = sm.part;
@@ -142,19 +194,19 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
     const uint32_t base = part * (uint32_t)kSortPart;
     const uint32_t wbase = base + wid * (32 * kSortKeysPerThread) + lane;
 
-    unsigned long long k[kSortKeysPerThread];
+    uint32_t k[kSortKeysPerThread];
     uint32_t v[kSortKeysPerThread];
     uint32_t rank[kSortKeysPerThread];
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
       const uint32_t idx = wbase + r * 32;
-      k[r] = idx < P ? kin[idx] : ~0ull;
+      k[r] = idx < P ? kin[idx] : ~0u;
       v[r] = idx < P ? vin[idx] : 0u;
     }
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
       const bool valid = wbase + r * 32 < P;
-      const uint32_t dg = (uint32_t)(k[r] >> shift) & (kRadixBins - 1);
+      const uint32_t dg = (k[r] >> shift) & (kRadixBins - 1);
       // lanes holding the same digit (a lane past the end matches only itself)
       const uint32_t peers = __match_any_sync(0xffffffffu, valid ? dg : 0x10000u | (uint32_t)lane);
       uint32_t before = 0;
@@ -195,7 +247,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
       if (wbase + r * 32 < P) {
-        const uint32_t dd = (uint32_t)(k[r] >> shift) & (kRadixBins - 1);
+        const uint32_t dd = (k[r] >> shift) & (kRadixBins - 1);
         const uint32_t pos = sm.local_start[dd] + sm.whist[wid][dd] + rank[r];
         sm.keys[pos] = k[r];
         sm.vals[pos] = v[r];
@@ -242,8 +294,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, int pass) {
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortPart, P - base);
     for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
-      const unsigned long long key = sm.keys[i];
-      const uint32_t dd = (uint32_t)(key >> shift) & (kRadixBins - 1);
+      const uint32_t key = sm.keys[i];
+      const uint32_t dd = (key >> shift) & (kRadixBins - 1);
       const uint32_t dst = sm.gbase[dd] + (i - sm.local_start[dd]);
       kout[dst] = key;
       vout[dst] = sm.vals[i];
@@ -261,14 +313,59 @@ cudaError_t sort_kernel_prepare() {
 
 const void* sort_kernel_ptr() { return reinterpret_cast<const void*>(&k_pass); }
 
-cudaError_t launch_radix_sort(const Ws& ws, int n_passes, int resident_hist, int resident_sort,
-                              cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * kPlanPasses * kRadixBins, st);
+static Stage unit_stage(const Ws& ws) {
+  Stage s;
+  s.keys[0] = ws.ukeys[0];
+  s.keys[1] = ws.ukeys[1];
+  s.vals[0] = ws.uvals[0];
+  s.vals[1] = ws.uvals[1];
+  s.count = nullptr;
+  s.fixed_count = ws.units;
+  s.cap = ws.units;
+  s.slot0 = 0;
+  s.nparts_word = kPlanNPartsUnits;
+  s.final_word = kPlanFinalUnits;
+  return s;
+}
+
+static Stage pair_stage(const Ws& ws) {
+  Stage s;
+  s.keys[0] = ws.keys[0];
+  s.keys[1] = ws.keys[1];
+  s.vals[0] = ws.vals[0];
+  s.vals[1] = ws.vals[1];
+  s.count = ws.pair_count;
+  s.fixed_count = 0;
+  s.cap = ws.pair_capacity;
+  s.slot0 = 4;
+  s.nparts_word = kPlanNParts;
+  s.final_word = kPlanFinal;
+  return s;
+}
+
+// Stage "units": depth digits (32 bits -> 4 passes).
+cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st) {
+  const Stage s = unit_stage(ws);
+  const int n_digits = 4;
+  cudaError_t e = cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * 4 * kRadixBins, st);
   if (e != cudaSuccess) return e;
-  k_hist<<<resident_hist, 256, 0, st>>>(ws, n_passes);
-  k_plan<<<1, kRadixBins, 0, st>>>(ws, n_passes);
-  for (int p = 0; p < n_passes; ++p)
-    k_pass<<<resident_sort, kSortThreads, sizeof(SortSmem), st>>>(ws, p);
+  k_unit_keys<<<resident_small, 256, 0, st>>>(ws, s, n_digits);
+  k_plan<<<1, kRadixBins, 0, st>>>(ws, s, n_digits);
+  for (int p = 0; p < n_digits; ++p)
+    k_pass<<<resident_sort, kSortThreads, sizeof(SortSmem), st>>>(ws, s, p);
+  return cudaGetLastError();
+}
+
+// Stage "pairs": tile digits (n_digits passes over the emitted pairs).
+cudaError_t launch_pair_sort(const Ws& ws, int n_digits, int resident_small, int resident_sort,
+                             cudaStream_t st) {
+  const Stage s = pair_stage(ws);
+  cudaError_t e = cudaMemsetAsync(ws.hist + 4 * kRadixBins, 0, sizeof(uint32_t) * 4 * kRadixBins, st);
+  if (e != cudaSuccess) return e;
+  k_hist<<<resident_small, 256, 0, st>>>(ws, s, n_digits);
+  k_plan<<<1, kRadixBins, 0, st>>>(ws, s, n_digits);
+  for (int p = 0; p < n_digits; ++p)
+    k_pass<<<resident_sort, kSortThreads, sizeof(SortSmem), st>>>(ws, s, p);
   return cudaGetLastError();
 }
 

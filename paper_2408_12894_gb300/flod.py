@@ -68,7 +68,8 @@ class WsLayout(C.Structure):
     _fields_ = [(n, C.c_size_t) for n in ("total", "status", "pair_count", "plan", "xy", "depth",
                                           "conic_o", "rgb", "radius", "tiles_touched",
                                           "block_sums", "slices")] + \
-               [("keys", C.c_size_t * 2), ("vals", C.c_size_t * 2)] + \
+               [("ukeys", C.c_size_t * 2), ("uvals", C.c_size_t * 2),
+                ("keys", C.c_size_t * 2), ("vals", C.c_size_t * 2)] + \
                [(n, C.c_size_t) for n in ("hist", "lookback", "ranges", "grad2d", "queue")] + \
                [(n, C.c_uint64) for n in ("units", "tiles", "pixels", "pair_capacity")]
 

@@ -53,15 +53,20 @@ def units(rast, view: int, n: int) -> dict:
 
 
 def sorted_pairs(rast):
-    """(keys uint64, vals uint32, ranges [tiles,2], pair_count, status) after bin_sort."""
+    """(keys uint64, vals uint32, ranges [tiles,2], pair_count, status) after bin_sort.
+
+    The workspace keeps the 32-bit tile id of every sorted pair; the 64-bit sort key
+    (tile << 32 | depth bits) is rebuilt from it and the depth of the pair's unit."""
     torch.cuda.synchronize()
     P = int(rast.pair_count.item())
     plan = rast.region("plan", torch.int32, 64).cpu().numpy()
     fin = int(plan[63])
     cap = rast.pair_capacity
     Pe = min(P, cap)
-    keys = rast.region("keys", torch.int64, cap, fin)[:Pe].cpu().numpy().view(np.uint64)
+    tiles = rast.region("keys", torch.int32, cap, fin)[:Pe].cpu().numpy().view(np.uint32)
     vals = rast.region("vals", torch.int32, cap, fin)[:Pe].cpu().numpy().view(np.uint32)
+    dbits = rast.region("depth", torch.float32, rast.layout.units).cpu().numpy().view(np.uint32)
+    keys = (tiles.astype(np.uint64) << np.uint64(32)) | dbits[vals].astype(np.uint64)
     ranges = rast.region("ranges", torch.int32, 2 * rast.layout.tiles).view(-1, 2).cpu().numpy()
     status = flod.flod_read_status(rast.ws)
     return keys, vals, ranges.astype(np.int64), P, status

@@ -80,10 +80,12 @@ def test_overwrite_mode_equals_accumulate_into_zeros():
     dL = torch.as_tensor(synth.upstream_gradient(13, [cam]), device="cuda")
     rast = rasterizer([g], [cam], [0.02])
     rgb, T, nc = rast.forward()
-    acc = [[torch.zeros_like(getattr(rast.sets[0], f)) for f in flod.GaussianSet.FIELDS]]
-    rast.render_bwd(dL, T, nc, acc)
-    over = [[torch.full_like(getattr(rast.sets[0], f), 7.5) for f in flod.GaussianSet.FIELDS]]
+    # one blend backward (its float atomics make the per-unit sums order-dependent), then
+    # both write modes of the preprocess backward over the same per-unit gradients
     rast.blend_bwd(dL, T, nc)
+    acc = [[torch.zeros_like(getattr(rast.sets[0], f)) for f in flod.GaussianSet.FIELDS]]
+    rast.preprocess_bwd(flod.grads_struct(acc))
+    over = [[torch.full_like(getattr(rast.sets[0], f), 7.5) for f in flod.GaussianSet.FIELDS]]
     rast.preprocess_bwd(flod.grads_struct(over, overwrite=True))
     torch.cuda.synchronize()
     for a, b in zip(acc[0], over[0]):

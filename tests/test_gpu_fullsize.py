@@ -35,11 +35,12 @@ def _invariants(rast, rgb, T, nc):
     tt = rast.region("tiles_touched", torch.int32, U).to(torch.int64)
     assert int(tt.sum().item()) == P
     plan = rast.region("plan", torch.int32, 64)
-    keys = rast.region("keys", torch.int64, rast.pair_capacity, int(plan[63].item()))[:P]
-    tiles = keys >> 32
+    fin = int(plan[63].item())
+    tiles = rast.region("keys", torch.int32, rast.pair_capacity, fin)[:P].to(torch.int64)
+    vals = rast.region("vals", torch.int32, rast.pair_capacity, fin)[:P].to(torch.int64)
     assert bool((tiles[1:] >= tiles[:-1]).all())
     same = tiles[1:] == tiles[:-1]
-    depth = keys & 0xFFFFFFFF
+    depth = rast.region("depth", torch.float32, U)[vals]
     assert bool((depth[1:][same] >= depth[:-1][same]).all())
     rg = rast.region("ranges", torch.int32, 2 * rast.layout.tiles).view(-1, 2).to(torch.int64)
     nz = rg[rg[:, 1] > rg[:, 0]]
