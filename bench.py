@@ -159,8 +159,8 @@ class OracleStep:
         t0 = time.perf_counter()
         p = R.params(sub, requires_grad=True)
         pre = R.preprocess(p, 3, self.s_min, self.cam, self.cfg)
-        k, v = R.bin_pairs(pre["tile_rect"], pre["tiles_touched"], pre["depth"].detach().numpy(),
-                           self.lists[3], self.n_tiles)
+        k, v = R.bin_segments(pre["segments"], pre["depth"].detach().numpy(), self.lists[3],
+                              self.n_tiles)
         R.sort_pairs(k, v)
         outs = [pre[n] for n in ("mean2d", "conic", "opacity", "rgb")]
         torch.autograd.backward(outs, [torch.ones_like(o) for o in outs])

@@ -60,6 +60,8 @@ typedef enum {
 /* Device status bits (flod_read_status). */
 #define FLOD_DEV_CAPACITY 0x1u /* pairs exceeded pair_capacity: pairs beyond it dropped */
 #define FLOD_DEV_TIMEOUT 0x2u  /* radix-sort look-back wait gave up */
+#define FLOD_DEV_TILESET 0x4u  /* emission listed another tile count than tiles_touched
+                                  (only with inconsistent per-unit inputs in the workspace) */
 
 #define FLOD_MAX_VIEWS 128
 #define FLOD_MAX_SETS 16
@@ -98,7 +100,9 @@ typedef struct {
   float dilation;     /* px^2 added to the 2D covariance diagonal (default 0.3) */
   float z_near;       /* cull t_z <= z_near (default 0.2) */
   float bg[3];        /* background colour (default black) */
-  int extent_rule;    /* 0: opacity-aware exact support (default); 1: 3 sigma */
+  int extent_rule;    /* 2 (default): opacity-aware support ellipse, listed row by row
+                         (tile columns whose pixel centres meet it); 0: its bounding circle's
+                         square; 1: 3 sigma square */
   int persistent;     /* 1: flod_bin_sort also orders the tiles largest-first (by pair
                          count) and the renderers run persistent CTAs over that order */
 } flod_raster_config;
@@ -125,7 +129,11 @@ typedef struct {
   size_t depth;         /* float [units] view-space z */
   size_t conic_o;       /* float4 [units] (a, b, c, opacity), q = a dx^2 + 2b dx dy + c dy^2 */
   size_t rgb;           /* float4 [units] (r, g, b, 0) */
-  size_t radius;        /* float [units] extent radius in pixels */
+  size_t radius;        /* float [units] extent radius in pixels (rules 0, 1; rule 2: the
+                           rule-0 circle radius, informational) */
+  size_t ext;           /* float4 [units] tile-set parameters (m, h, rx, ry): rule 2 the
+                           support ellipse's row shear and scale and bounding half-widths,
+                           rules 0 and 1 (0, 0, r, r) */
   size_t tiles_touched; /* uint32 [units], 0 when culled */
   size_t block_sums;    /* uint64 [units/1024 + 1] exclusive pair offsets per 1024 units */
   size_t slices;        /* uint32 [units/1024 + 1] exclusive count of 4096-pair emission slices */

@@ -43,7 +43,7 @@ class Config:
     dilation: float = 0.3
     z_near: float = 0.2
     bg: tuple = (0.0, 0.0, 0.0)
-    extent_rule: int = 0
+    extent_rule: int = 2
     extra: dict = field(default_factory=dict)
 
 
@@ -64,39 +64,56 @@ def preprocess(p: dict, sh_degree: int, s_min: float, cam: dict, cfg: Config) ->
     t, mean2d, cov2d, in_front = P.project(p["means"], cov3d, cam, cfg.dilation, cfg.z_near)
     con, det = P.conic(cov2d)
     o = G.sigmoid(p["opacity_logit"])
-    r, ok = P.radius(cov2d.detach(), o.detach(), cfg.extent_rule)
+    r, ok = P.radius(cov2d.detach(), o.detach(), 1 if cfg.extent_rule == 1 else 0)
     _, _, cam_pos = P.camera_tensors(cam)
     rgb, rgb_raw = SH.colour(p["sh"], p["means"], cam_pos, sh_degree)
     valid = in_front & (det.detach() > 0) & ok
-    px = P.pixel_rect(mean2d[:, 0].detach().numpy(), mean2d[:, 1].detach().numpy(),
-                      r.numpy(), cam["width"], cam["height"])
-    tr = P.tile_rect(px, cfg.tile_w, cfg.tile_h, valid.numpy())
+    u, v = mean2d[:, 0].detach().numpy(), mean2d[:, 1].detach().numpy()
+    if cfg.extent_rule == 2:
+        ext, ok2 = P.ellipse_extent(cov2d.detach(), o.detach())
+        valid = valid & ok2
+        e = ext.numpy()
+        px = P.pixel_rect_xy(u, v, e[:, 2], e[:, 3], cam["width"], cam["height"])
+        segs, touched = P.ellipse_segments(u, v, e, px, cfg.tile_w, cfg.tile_h, valid.numpy())
+        tr = P.tile_rect(px, cfg.tile_w, cfg.tile_h, valid.numpy() & (touched > 0))
+    else:
+        ext = torch.stack([torch.zeros_like(r), torch.zeros_like(r), r, r], dim=1)
+        px = P.pixel_rect(u, v, r.numpy(), cam["width"], cam["height"])
+        tr = P.tile_rect(px, cfg.tile_w, cfg.tile_h, valid.numpy())
+        touched = tr[4]
+        segs = P.rect_segments(tr[:4], touched)
     return {"mean2d": mean2d, "depth": t[:, 2], "conic": con, "opacity": o, "rgb": rgb,
-            "rgb_raw": rgb_raw, "radius": r, "valid": valid, "cov2d": cov2d, "t": t,
-            "pixel_rect": px, "tile_rect": tr[:4], "tiles_touched": tr[4]}
+            "rgb_raw": rgb_raw, "radius": r, "ext": ext, "valid": valid, "cov2d": cov2d,
+            "t": t, "pixel_rect": px, "tile_rect": tr[:4], "segments": segs,
+            "tiles_touched": touched}
 
 
 def f32_bits(x) -> np.ndarray:
     return np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
 
 
-def bin_pairs(tile_rect, tiles_touched, depth_f32, tiles_x: int, n_tiles: int,
-              tile_offset: int = 0, unit_offset: int = 0):
+def bin_segments(segments, depth_f32, tiles_x: int, n_tiles: int, tile_offset: int = 0,
+                 unit_offset: int = 0):
     """(tile, depth) keys for every (Gaussian, covered tile), emitted in Gaussian order and
-    within a Gaussian row-major over its tile rectangle; key = tile << 32 | bits(depth).
-    Returns (keys, values) unsorted, in emission order."""
-    tx0, tx1, ty0, ty1 = (np.asarray(a, dtype=np.int64) for a in tile_rect)
-    cnt = np.asarray(tiles_touched, dtype=np.int64)
-    g = np.repeat(np.arange(cnt.size, dtype=np.int64), cnt)
-    start = np.cumsum(cnt) - cnt
-    k = np.arange(g.size, dtype=np.int64) - start[g]
-    w = (tx1 - tx0 + 1)[g]
-    tx = tx0[g] + k % w
-    ty = ty0[g] + k // w
-    tile = tile_offset + ty * tiles_x + tx
-    assert g.size == 0 or (tile.max() < tile_offset + n_tiles and tile.min() >= tile_offset)
+    within a Gaussian row by row, left to right, over its segments (unit, ty, cx0, cx1);
+    key = tile << 32 | bits(depth). Returns (keys, values) unsorted, in emission order."""
+    unit, ty, cx0, cx1 = (np.asarray(a, dtype=np.int64) for a in segments)
+    w = cx1 - cx0 + 1
+    s = np.repeat(np.arange(unit.size, dtype=np.int64), w)
+    start = np.cumsum(w) - w
+    tx = cx0[s] + (np.arange(s.size, dtype=np.int64) - start[s])
+    tile = tile_offset + ty[s] * tiles_x + tx
+    assert s.size == 0 or (tile.max() < tile_offset + n_tiles and tile.min() >= tile_offset)
+    g = unit[s]
     keys = (tile.astype(np.uint64) << np.uint64(32)) | f32_bits(depth_f32)[g]
     return keys, (g + unit_offset).astype(np.uint32)
+
+
+def bin_pairs(tile_rect, tiles_touched, depth_f32, tiles_x: int, n_tiles: int,
+              tile_offset: int = 0, unit_offset: int = 0):
+    """bin_segments over full tile rectangles (rules 0 and 1): row-major in each rectangle."""
+    return bin_segments(P.rect_segments(tile_rect, tiles_touched), depth_f32, tiles_x, n_tiles,
+                        tile_offset, unit_offset)
 
 
 def sort_pairs(keys: np.ndarray, vals: np.ndarray):
@@ -186,8 +203,8 @@ def tile_lists(pre: dict, cam: dict, cfg: Config):
     W, H = cam["width"], cam["height"]
     tiles_x = -(-W // cfg.tile_w)
     tiles_y = -(-H // cfg.tile_h)
-    keys, vals = bin_pairs(pre["tile_rect"], pre["tiles_touched"], pre["depth"].detach().numpy(),
-                           tiles_x, tiles_x * tiles_y)
+    keys, vals = bin_segments(pre["segments"], pre["depth"].detach().numpy(), tiles_x,
+                              tiles_x * tiles_y)
     keys, vals = sort_pairs(keys, vals)
     return keys, vals, tile_ranges(keys, tiles_x * tiles_y), tiles_x, tiles_y
 
@@ -270,6 +287,7 @@ def discrete_state(pre: dict, cam: dict, cfg: Config, lists=None) -> bytes:
     lim_x = 1.3 * 0.5 * cam["width"] / cam["fx"]
     lim_y = 1.3 * 0.5 * cam["height"] / cam["fy"]
     parts = [pre["valid"].numpy().tobytes(), np.stack(pre["tile_rect"]).tobytes(),
+             np.stack(pre["segments"]).tobytes(),
              (pre["rgb_raw"].detach().numpy() > 0).tobytes(),
              (np.abs(t[:, 0] / tz) > lim_x).tobytes(), (np.abs(t[:, 1] / tz) > lim_y).tobytes()]
     W, H = cam["width"], cam["height"]
@@ -299,7 +317,7 @@ def sampled_gradients(g: dict, sh_degree: int, s_min, cam: dict, cfg: Config,
                       grad_out: np.ndarray, sample: np.ndarray, lists=None, pre=None):
     """dL/d(parameters) of the Gaussians ``sample`` only, for L = sum(grad_out * image).
 
-    A Gaussian enters only the tiles its rectangle covers, so its gradient is the sum over
+    A Gaussian enters only the tiles it is binned to, so its gradient is the sum over
     those tiles' pixels: each such tile is blended with the sampled Gaussian's 2D values as
     autograd leaves and every other Gaussian held constant, and the resulting 2D gradient is
     chained through that Gaussian's own preprocess. Exact (same definition as
@@ -312,7 +330,7 @@ def sampled_gradients(g: dict, sh_degree: int, s_min, cam: dict, cfg: Config,
     bg = torch.as_tensor(np.asarray(cfg.bg, dtype=np.float64))
     go = torch.as_tensor(np.asarray(grad_out, dtype=np.float64))
     out = {k: [] for k in ("means", "quats", "s_opt", "opacity_logit", "sh")}
-    tx0, tx1, ty0, ty1 = pre["tile_rect"]
+    seg_unit, seg_ty, seg_x0, seg_x1 = (np.asarray(a) for a in pre["segments"])
     names = ("mean2d", "conic", "opacity", "rgb")
     base = {k: pre[k].detach() for k in names}
     for j in np.asarray(sample, dtype=np.int64):
@@ -322,29 +340,29 @@ def sampled_gradients(g: dict, sh_degree: int, s_min, cam: dict, cfg: Config,
         prej = preprocess(pj, sh_degree, smj, cam, cfg)
         leaves = {k: prej[k] for k in names}
         total = None
-        if pre["tiles_touched"][j] > 0:
-            for ty in range(ty0[j], ty1[j] + 1):
-                for tx in range(tx0[j], tx1[j] + 1):
-                    tile = ty * tiles_x + tx
-                    s, e = ranges[tile]
-                    gi = vals[s:e].astype(np.int64)
-                    pos = np.nonzero(gi == j)[0]
-                    x0, y0 = tx * cfg.tile_w, ty * cfg.tile_h
-                    x1, y1 = min(x0 + cfg.tile_w, W), min(y0 + cfg.tile_h, H)
-                    pix = _pixel_centres(np.arange(x0, x1), np.arange(y0, y1))
-                    sel = torch.as_tensor(gi)
-                    cols = {}
-                    for k in names:
-                        t = base[k][sel].clone()
-                        mask = torch.zeros(len(gi), dtype=torch.bool)
-                        mask[torch.as_tensor(pos)] = True
-                        shape = (-1,) + (1,) * (t.dim() - 1)
-                        cols[k] = torch.where(mask.view(shape), leaves[k].expand_as(t), t)
-                    a = alpha_raw(pix, cols["mean2d"], cols["conic"], cols["opacity"])
-                    col, _, _ = blend(a, cols["rgb"], bg)
-                    gt = go[:, y0:y1, x0:x1].reshape(3, -1).T
-                    term = (col * gt).sum()
-                    total = term if total is None else total + term
+        for q in np.nonzero(seg_unit == j)[0]:
+            ty = int(seg_ty[q])
+            for tx in range(int(seg_x0[q]), int(seg_x1[q]) + 1):
+                tile = ty * tiles_x + tx
+                s, e = ranges[tile]
+                gi = vals[s:e].astype(np.int64)
+                pos = np.nonzero(gi == j)[0]
+                x0, y0 = tx * cfg.tile_w, ty * cfg.tile_h
+                x1, y1 = min(x0 + cfg.tile_w, W), min(y0 + cfg.tile_h, H)
+                pix = _pixel_centres(np.arange(x0, x1), np.arange(y0, y1))
+                sel = torch.as_tensor(gi)
+                cols = {}
+                for k in names:
+                    t = base[k][sel].clone()
+                    mask = torch.zeros(len(gi), dtype=torch.bool)
+                    mask[torch.as_tensor(pos)] = True
+                    shape = (-1,) + (1,) * (t.dim() - 1)
+                    cols[k] = torch.where(mask.view(shape), leaves[k].expand_as(t), t)
+                a = alpha_raw(pix, cols["mean2d"], cols["conic"], cols["opacity"])
+                col, _, _ = blend(a, cols["rgb"], bg)
+                gt = go[:, y0:y1, x0:x1].reshape(3, -1).T
+                term = (col * gt).sum()
+                total = term if total is None else total + term
         if total is not None:
             total.backward()
         for k in out:

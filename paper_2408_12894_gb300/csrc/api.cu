@@ -65,7 +65,7 @@ bool cfg_ok(const flod_raster_config* c) {
                      (c->tile_w == 32 && c->tile_h == 8);
   const bool batch = c->batch == 32 || c->batch == 64 || c->batch == 128 || c->batch == 256;
   return shape && batch && c->dilation >= 0.f && c->z_near > 0.f &&
-         (c->extent_rule == 0 || c->extent_rule == 1) && isfinite(c->dilation) &&
+         (c->extent_rule >= 0 && c->extent_rule <= 2) && isfinite(c->dilation) &&
          isfinite(c->z_near);
 }
 
@@ -150,6 +150,7 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   L.conic_o = take(16 * u);
   L.rgb = take(16 * u);
   L.radius = take(4 * u);
+  L.ext = take(16 * u);
   L.tiles_touched = take(4 * u);
   L.block_sums = take(8 * (u / kScanBlock + 1));
   L.slices = take(4 * (u / kScanBlock + 1));
@@ -186,6 +187,7 @@ Ws ws_ptrs(void* base, const Plan& P) {
   w.conic_o = reinterpret_cast<float4*>(b + L.conic_o);
   w.rgb = reinterpret_cast<float4*>(b + L.rgb);
   w.radius = reinterpret_cast<float*>(b + L.radius);
+  w.ext = reinterpret_cast<float4*>(b + L.ext);
   w.tiles_touched = reinterpret_cast<uint32_t*>(b + L.tiles_touched);
   w.block_sums = reinterpret_cast<unsigned long long*>(b + L.block_sums);
   w.slices = reinterpret_cast<uint32_t*>(b + L.slices);
@@ -292,7 +294,7 @@ void flod_default_config(flod_raster_config* c) {
   c->dilation = 0.3f;
   c->z_near = 0.2f;
   c->bg[0] = c->bg[1] = c->bg[2] = 0.f;
-  c->extent_rule = 0;
+  c->extent_rule = 2;
   c->persistent = 0;
 }
 

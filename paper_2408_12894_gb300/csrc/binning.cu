@@ -114,102 +114,272 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
 
 // Key emission in depth-sorted unit order, load-balanced over output positions. Each
 // 1024-slot block's contiguous range of pairs is cut into slices of kEmitSlice positions;
-// persistent CTAs take slices in turn. For its slice a CTA rescans the block's 1024 pair
-// counts in shared memory, fetches the tile rectangle of the units that overlap the slice,
-// and its threads walk the slice's positions: position p belongs to the slot whose prefix
-// range holds it (binary search in shared memory) and its tile is the (p - start)-th tile of
-// that unit's rectangle in row-major order. Writes are coalesced, and a block of huge
-// splats is spread over many CTAs.
+// persistent CTAs take slices in turn. For its slice [r0, r1) a CTA
+//   1. rescans the block's 1024 pair counts (slot start positions);
+//   2. counts the tile rows of the slots that overlap the slice and scans them: each
+//      (slot, tile row) is one work item;
+//   3. evaluates the items, kEmitItems at a time, one per thread and step: the row's tile
+//      columns (UnitTiles/unit_row, the rule preprocess counted with), a block scan of their
+//      counts for the row's first position, and, for a row that overlaps the slice, a
+//      "segment": its first tile id (minus its first slice position) and its unit, with the
+//      segment's id marked at that position;
+//   4. fills every position with the id of the last mark at or before it (a block scan);
+//   5. writes keys (tile ids) and values (units), one position per thread and step.
+// Threads stay converged whatever the mix of splat sizes, writes are coalesced, and a block
+// of huge splats is spread over many CTAs. A slot whose rows hold another tile count than
+// preprocess stored sets FLOD_DEV_TILESET.
+constexpr int kEmitItems = 2048;
+constexpr uint16_t kNoSeg = 0xffffu;
+
+template <int MAXV>
+__device__ __forceinline__ bool slot_tiles(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
+                                           UnitTiles& t, uint32_t& row_base, uint32_t& tiles_x) {
+  const ViewP& V = b.views[view_of_unit(b, u)];
+  const float2 xy = ws.xy[u];
+  row_base = V.tile_off;
+  tiles_x = V.tiles_x;
+  return unit_tiles(xy.x, xy.y, ws.ext[u], V.width, V.height, b.cfg.tile_w, b.cfg.tile_h,
+                    b.cfg.extent_rule == 2, t);
+}
+
+// Block-wide exclusive sum over 256 threads (8 warps); also returns the total.
+__device__ __forceinline__ uint32_t block_excl_sum(uint32_t x, uint32_t* warp_tot, uint32_t& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  __syncthreads();
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  uint32_t pre = 0;
+  total = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t t = warp_tot[q];
+    if (q < wid) pre += t;
+    total += t;
+  }
+  return pre + inc - x;
+}
+
 template <int MAXV>
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV> b, Ws ws,
                                               uint32_t nblocks) {
-  __shared__ uint32_t s_pre[kScanBlock + 1];
-  __shared__ uint32_t s_rect[kScanBlock];     // tx0 | (rect width << 16)
-  __shared__ uint32_t s_tile0[kScanBlock];    // global id of the rectangle's first row, column 0
-  __shared__ uint32_t s_tx[kScanBlock];       // tiles per row of the unit's view
+  __shared__ uint32_t s_pre[kScanBlock + 1];     // slot start positions (block-relative)
+  __shared__ uint32_t s_row[kScanBlock + 1];     // first item of each slot
+  __shared__ uint32_t s_unit[kScanBlock];
+  __shared__ uint16_t s_owner[kEmitSlice];       // segment id per slice position
+  __shared__ uint32_t s_seg_tile[kEmitSlice];    // tile id at slice position 0 (mod 2^32)
+  __shared__ uint16_t s_seg_slot[kEmitSlice];
   __shared__ uint32_t warp_tot[8];
-  __shared__ uint32_t s_blk;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  __shared__ uint32_t s_blkmap[256];             // block of each of my next 256 slices
+  __shared__ uint32_t s_nseg;
+  const int tid = threadIdx.x;
   const uint32_t n_slices = ws.plan[kPlanSlices];
   const unsigned long long cap = ws.pair_capacity;
   const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
   uint32_t* keys = ws.keys[0];
   uint32_t* vals = ws.vals[0];
-  for (uint32_t w = blockIdx.x; w < n_slices; w += gridDim.x) {
-    if (tid == 0) {                       // the block holding slice w
-      uint32_t lo = 0, hi = nblocks - 1;
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (ws.slices[mid] <= w) lo = mid; else hi = mid - 1;
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t w = blockIdx.x + it * gridDim.x;
+    if (w >= n_slices) break;
+    if ((it & 255u) == 0) {               // the blocks of my next 256 slices, searched at once
+      __syncthreads();
+      const uint32_t wt = blockIdx.x + (it + (uint32_t)tid) * gridDim.x;
+      if (wt < n_slices) {
+        uint32_t lo = 0, hi = nblocks - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (ws.slices[mid] <= wt) lo = mid; else hi = mid - 1;
+        }
+        s_blkmap[tid] = lo;
       }
-      s_blk = lo;
     }
+    if (tid == 0) s_nseg = 0;
+    for (int i = tid; i < kEmitSlice; i += 256) s_owner[i] = kNoSeg;
     __syncthreads();
-    const uint32_t blk = s_blk;
+    const uint32_t blk = s_blkmap[it & 255u];
     const uint32_t r0 = (w - ws.slices[blk]) * (uint32_t)kEmitSlice;
+    // 1. slot start positions
     const uint4 un = reinterpret_cast<const uint4*>(order)[blk * 256u + tid];
     const uint32_t unit[4] = {un.x, un.y, un.z, un.w};
     uint32_t cnt[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) cnt[j] = ws.tiles_touched[unit[j]];
-    const uint32_t s = cnt[0] + cnt[1] + cnt[2] + cnt[3];
-    uint32_t x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    for (int j = 0; j < 4; ++j) {
+      cnt[j] = ws.tiles_touched[unit[j]];
+      s_unit[4 * tid + j] = unit[j];
     }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    uint32_t run = 0;
-    for (int q = 0; q < wid; ++q) run += warp_tot[q];
-    run += x - s;
-    const uint32_t r1_full = r0 + (uint32_t)kEmitSlice;
+    uint32_t total;
+    uint32_t run = block_excl_sum(cnt[0] + cnt[1] + cnt[2] + cnt[3], warp_tot, total);
+    uint32_t pre[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int sl = 4 * tid + j;
-      s_pre[sl] = run;
-      if (cnt[j] && run < r1_full && run + cnt[j] > r0) {
-        const uint32_t u = unit[j];
-        const ViewP& V = b.views[view_of_unit(b, u)];
-        const float2 xy = ws.xy[u];
-        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-        tile_rect(xy.x, xy.y, ws.radius[u], V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0,
-                  tx1, ty0, ty1);
-        s_rect[sl] = (uint32_t)tx0 | ((uint32_t)(tx1 - tx0 + 1) << 16);
-        s_tile0[sl] = V.tile_off + (uint32_t)ty0 * V.tiles_x;
-        s_tx[sl] = V.tiles_x;
-      }
+      pre[j] = run;
+      s_pre[4 * tid + j] = run;
       run += cnt[j];
     }
     if (tid == 255) s_pre[kScanBlock] = run;
+    const uint32_t r1 = min(r0 + (uint32_t)kEmitSlice, total);
+    // 2. tile rows of the slots that overlap the slice
+    uint32_t nrow[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      nrow[j] = 0;
+      if (cnt[j] && pre[j] < r1 && pre[j] + cnt[j] > r0) {
+        UnitTiles t;
+        uint32_t row_base, tiles_x;
+        if (slot_tiles(b, ws, unit[j], t, row_base, tiles_x)) nrow[j] = (uint32_t)(t.ty1 - t.ty0 + 1);
+        else set_status(ws.status, FLOD_DEV_TILESET);
+      }
+    }
+    uint32_t n_items;
+    run = block_excl_sum(nrow[0] + nrow[1] + nrow[2] + nrow[3], warp_tot, n_items);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s_row[4 * tid + j] = run;
+      run += nrow[j];
+    }
+    if (tid == 255) s_row[kScanBlock] = run;
     __syncthreads();
-    const uint32_t total = s_pre[kScanBlock];
-    const uint32_t r1 = min(r1_full, total);
+    // the first overlapping slot: its start is the position of item 0
+    uint32_t p_first = 0;
+    {
+      int lo = 0, hi = kScanBlock - 1;         // first slot whose end exceeds r0
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_pre[mid + 1] > r0) hi = mid; else lo = mid + 1;
+      }
+      p_first = s_pre[lo];
+    }
+    // 3. items, kEmitItems per round, 8 consecutive items per thread
+    uint32_t carry = p_first;
+    for (uint32_t ib = 0; ib < n_items; ib += kEmitItems) {
+      const uint32_t i0 = ib + 8u * tid;
+      int slot = -1;
+      UnitTiles t;
+      uint32_t row_base = 0, tiles_x = 0;
+      uint32_t nn[8], tile0[8];
+      int sl[8];
+      uint32_t mine = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        nn[k] = 0;
+        sl[k] = -1;
+        const uint32_t i = i0 + k;
+        if (i >= n_items) continue;
+        if (slot < 0) {                        // last slot whose first item is <= i
+          int lo = 0, hi = kScanBlock - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_row[mid] <= i) lo = mid; else hi = mid - 1;
+          }
+          slot = lo;
+          slot_tiles(b, ws, s_unit[slot], t, row_base, tiles_x);
+        }
+        while (s_row[slot + 1] <= i) {         // next slot with rows
+          ++slot;
+          if (s_row[slot + 1] > i) slot_tiles(b, ws, s_unit[slot], t, row_base, tiles_x);
+        }
+        const int ty = t.ty0 + (int)(i - s_row[slot]);
+        int cx0, cx1;
+        if (unit_row(t, ty, cx0, cx1)) {
+          nn[k] = (uint32_t)(cx1 - cx0 + 1);
+          tile0[k] = row_base + (uint32_t)ty * tiles_x + (uint32_t)cx0;   // row's first tile
+        }
+        sl[k] = slot;
+        mine += nn[k];
+      }
+      uint32_t round_total;
+      uint32_t pos = carry + block_excl_sum(mine, warp_tot, round_total);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (nn[k] && pos < r1 && pos + nn[k] > r0) {
+          const uint32_t first = max(pos, r0);
+          const uint32_t id = atomicAdd(&s_nseg, 1u);
+          if (id < (uint32_t)kEmitSlice) {
+            s_owner[first - r0] = (uint16_t)id;
+            s_seg_tile[id] = tile0[k] + (first - pos) - (first - r0);
+            s_seg_slot[id] = (uint16_t)sl[k];
+          }
+        }
+        pos += nn[k];
+      }
+      carry += round_total;
+    }
+    // the rows of the overlapping slots must add up to their stored counts
+    if (tid == 0) {
+      int lo = 0, hi = kScanBlock - 1;         // last slot starting before r1
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pre[mid] < r1) lo = mid; else hi = mid - 1;
+      }
+      if (carry != s_pre[lo + 1] || s_nseg > (uint32_t)kEmitSlice)
+        set_status(ws.status, FLOD_DEV_TILESET);
+    }
+    __syncthreads();
+    // 4. fill: each position takes the last segment marked at or before it
+    constexpr int kPer = kEmitSlice / 256;
+    uint16_t last = kNoSeg;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint16_t o = s_owner[tid * kPer + k];
+      if (o != kNoSeg) last = o;
+    }
+    {
+      // carry-in: the last mark of the nearest preceding thread that has one
+      const int lane = tid & 31, wid = tid >> 5;
+      uint32_t v = last;                       // kNoSeg = none
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o && v == kNoSeg) v = y;
+      }
+      // v: inclusive "last mark" up to this lane; the exclusive one comes from lane - 1
+      uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
+      if (lane == 0) ex = kNoSeg;
+      __syncthreads();
+      if (lane == 31) warp_tot[wid] = v;
+      __syncthreads();
+      if (ex == kNoSeg) {
+        for (int q = wid - 1; q >= 0; --q) {
+          if (warp_tot[q] != kNoSeg) {
+            ex = warp_tot[q];
+            break;
+          }
+        }
+      }
+      uint16_t cur = (uint16_t)ex;
+      for (int k = 0; k < kPer; ++k) {
+        const uint16_t o = s_owner[tid * kPer + k];
+        if (o != kNoSeg) cur = o;
+        else s_owner[tid * kPer + k] = cur;
+      }
+    }
+    __syncthreads();
+    // 5. write
     const unsigned long long base = ws.block_sums[blk];
     for (uint32_t p = r0 + tid; p < r1; p += 256) {
       if (base + p >= cap) break;
-      int lo = 0, hi = kScanBlock - 1;        // last slot with s_pre[slot] <= p
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_pre[mid] <= p) lo = mid; else hi = mid - 1;
-      }
-      const uint32_t k = p - s_pre[lo];
-      const uint32_t r = s_rect[lo];
-      const uint32_t wdt = r >> 16;
-      keys[base + p] = s_tile0[lo] + (k / wdt) * s_tx[lo] + (r & 0xffffu) + k % wdt;
-      vals[base + p] = order[blk * (uint32_t)kScanBlock + lo];
+      const uint32_t rel = p - r0;
+      const uint16_t sgi = s_owner[rel];
+      if (sgi == kNoSeg) continue;             // only with an inconsistent tile set
+      keys[base + p] = s_seg_tile[sgi] + rel;
+      vals[base + p] = s_unit[s_seg_slot[sgi]];
     }
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(256) k_ranges(Ws ws) {
+__global__ void __launch_bounds__(256) k_ranges(Ws ws, uint32_t n_tiles) {
   const unsigned long long P0 = *ws.pair_count;
   const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
   const uint32_t* keys = ws.keys[ws.plan[kPlanFinal]];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
     const uint32_t t = keys[i];
+    if (t >= n_tiles) continue;   // only after an inconsistent tile set (FLOD_DEV_TILESET)
     if (i == 0 || keys[i - 1] != t) ws.ranges[t].x = i;
     if (i == P - 1 || keys[i + 1] != t) ws.ranges[t].y = i + 1;
   }
@@ -268,7 +438,7 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
   if (nblocks) k_emit<MAXV><<<resident_small, 256, 0, st>>>(b, ws, nblocks);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_pair_sort(ws, n_passes, resident_small, resident_sort, st)) != cudaSuccess) return e;
-  k_ranges<<<resident_small, 256, 0, st>>>(ws);
+  k_ranges<<<resident_small, 256, 0, st>>>(ws, b.tiles);
   if (build_queue && b.tiles) {
     if ((e = cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t) * kQueueHeader, st)) != cudaSuccess)
       return e;

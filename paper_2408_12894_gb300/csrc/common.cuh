@@ -15,6 +15,7 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;
 constexpr float kClampFov = 1.3f;        // Jacobian off-screen guard, x tan(half fov)
+constexpr float kExtentMargin = 1.0f + 1.0f / 1024.0f;   // rule 2: tau widened by 2^-10
 
 constexpr int kScanBlock = 1024;         // units per block-sum entry; view capacities are
                                          // rounded up to a multiple of it
@@ -78,6 +79,7 @@ struct Ws {
   float4* conic_o;
   float4* rgb;
   float* radius;
+  float4* ext;             // (m, h, rx, ry) of the unit's tile set (see UnitTiles)
   uint32_t* tiles_touched;
   unsigned long long* block_sums;
   uint32_t* slices;
@@ -141,12 +143,12 @@ __device__ __forceinline__ int view_of_tile(const Batch<MAXV>& b, uint32_t t) {
 // The pixel rectangle rule, every step rounded to nearest in float32 so that a float32
 // reference takes the same decisions: columns ceil((u - r) - 0.5) .. floor((u + r) - 0.5),
 // clamped to the image; then tiles. Returns false if empty.
-__device__ __forceinline__ bool tile_rect(float u, float v, float r, int W, int H, int tw,
-                                          int th, int& tx0, int& tx1, int& ty0, int& ty1) {
-  float x0 = ceilf(__fsub_rn(__fsub_rn(u, r), 0.5f));
-  float x1 = floorf(__fsub_rn(__fadd_rn(u, r), 0.5f));
-  float y0 = ceilf(__fsub_rn(__fsub_rn(v, r), 0.5f));
-  float y1 = floorf(__fsub_rn(__fadd_rn(v, r), 0.5f));
+__device__ __forceinline__ bool pixel_rect(float u, float v, float rx, float ry, int W, int H,
+                                           int& px0, int& px1, int& py0, int& py1) {
+  float x0 = ceilf(__fsub_rn(__fsub_rn(u, rx), 0.5f));
+  float x1 = floorf(__fsub_rn(__fadd_rn(u, rx), 0.5f));
+  float y0 = ceilf(__fsub_rn(__fsub_rn(v, ry), 0.5f));
+  float y1 = floorf(__fsub_rn(__fadd_rn(v, ry), 0.5f));
   // NaN compares false: treat as empty
   if (!(x0 <= x1) || !(y0 <= y1)) return false;
   x0 = fmaxf(x0, 0.f);
@@ -154,10 +156,83 @@ __device__ __forceinline__ bool tile_rect(float u, float v, float r, int W, int 
   x1 = fminf(x1, (float)(W - 1));
   y1 = fminf(y1, (float)(H - 1));
   if (x0 > x1 || y0 > y1) return false;
-  tx0 = (int)x0 / tw;
-  tx1 = (int)x1 / tw;
-  ty0 = (int)y0 / th;
-  ty1 = (int)y1 / th;
+  px0 = (int)x0;
+  px1 = (int)x1;
+  py0 = (int)y0;
+  py1 = (int)y1;
+  return true;
+}
+
+__device__ __forceinline__ bool tile_rect(float u, float v, float r, int W, int H, int tw,
+                                          int th, int& tx0, int& tx1, int& ty0, int& ty1) {
+  int px0, px1, py0, py1;
+  if (!pixel_rect(u, v, r, r, W, H, px0, px1, py0, py1)) return false;
+  tx0 = px0 / tw;
+  tx1 = px1 / tw;
+  ty0 = py0 / th;
+  ty1 = py1 / th;
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Tile sets of a unit ("segments": one run of tile columns per tile row)
+// ---------------------------------------------------------------------------------------
+// ext = (m, h, rx, ry) of the unit's support ellipse {d : d^T Sigma'^-1 d <= tau} (extent
+// rule 2; rules 0 and 1 store (0, 0, r, r) and list full rectangle rows). Row dy of the
+// ellipse is x in u + m dy +- h sqrt(ry^2 - dy^2); its rightmost point lies at
+// dy = m ry^2 / rx (the leftmost at minus that) and the right boundary is concave in dy, so
+// over a band of rows the extremes are at those points clamped to the band. Every
+// operation is rounded explicitly, so that preprocess (which counts the tiles) and emission
+// (which lists them) take identical decisions and a float32 reference can repeat them.
+struct UnitTiles {
+  float u, v;
+  float4 e;
+  float dyx, ry2;
+  int px0, px1, py0, py1;   // pixel rectangle (clamped to the image)
+  int ty0, ty1;             // its tile rows
+  int tw, th;
+  bool rows;                // rule 2: per-row column ranges
+};
+
+__device__ __forceinline__ bool unit_tiles(float u, float v, float4 e, int W, int H, int tw,
+                                           int th, bool rows, UnitTiles& t) {
+  if (!pixel_rect(u, v, e.z, e.w, W, H, t.px0, t.px1, t.py0, t.py1)) return false;
+  t.u = u;
+  t.v = v;
+  t.e = e;
+  t.ry2 = __fmul_rn(e.w, e.w);
+  t.dyx = e.z > 0.f ? __fdiv_rn(__fmul_rn(e.x, t.ry2), e.z) : 0.f;
+  t.ty0 = t.py0 / th;
+  t.ty1 = t.py1 / th;
+  t.tw = tw;
+  t.th = th;
+  t.rows = rows;
+  return true;
+}
+
+// Tile columns [cx0, cx1] of tile row ty (ty0 <= ty <= ty1); false if the row has none.
+__device__ __forceinline__ bool unit_row(const UnitTiles& t, int ty, int& cx0, int& cx1) {
+  if (!t.rows) {
+    cx0 = t.px0 / t.tw;
+    cx1 = t.px1 / t.tw;
+    return true;
+  }
+  const int jy0 = max(ty * t.th, t.py0);
+  const int jy1 = min(ty * t.th + t.th - 1, t.py1);
+  const float dy0 = __fsub_rn((float)jy0 + 0.5f, t.v);
+  const float dy1 = __fsub_rn((float)jy1 + 0.5f, t.v);
+  const float dr = fminf(fmaxf(t.dyx, dy0), dy1);
+  const float dl = fminf(fmaxf(-t.dyx, dy0), dy1);
+  const float wr = __fmul_rn(t.e.y, __fsqrt_rn(fmaxf(__fsub_rn(t.ry2, __fmul_rn(dr, dr)), 0.f)));
+  const float wl = dl == dr ? wr  // same point: the same value, one square root fewer
+                            : __fmul_rn(t.e.y, __fsqrt_rn(fmaxf(__fsub_rn(t.ry2, __fmul_rn(dl, dl)), 0.f)));
+  const float xr = __fadd_rn(__fadd_rn(t.u, __fmul_rn(t.e.x, dr)), wr);
+  const float xl = __fsub_rn(__fadd_rn(t.u, __fmul_rn(t.e.x, dl)), wl);
+  const float c0 = fmaxf(ceilf(__fsub_rn(xl, 0.5f)), (float)t.px0);
+  const float c1 = fminf(floorf(__fsub_rn(xr, 0.5f)), (float)t.px1);
+  if (!(c0 <= c1)) return false;
+  cx0 = (int)c0 / t.tw;
+  cx1 = (int)c1 / t.tw;
   return true;
 }
 

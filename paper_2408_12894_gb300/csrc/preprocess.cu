@@ -3,7 +3,7 @@
 // Forward (one thread per unit): Eq. 4 constrained scale s = exp(s_opt) + s_min (Sec. 4.1),
 // Eq. 1 covariance through M = R diag(s) (Sigma = M M^T, Sec. 3), the local-affine
 // projection of Eq. 2 (Sigma' = (J W M)(J W M)^T + dilation I), conic, opacity, the
-// opacity-aware extent, the tile rectangle and the SH colour.
+// opacity-aware extent, the tile set (rectangle, or ellipse rows) and the SH colour.
 //
 // Backward (one thread per unit): the chain rule of the same steps, from the per-unit
 // gradient of (u, v, conic, opacity, rgb) that the blending backward accumulated, to the
@@ -141,56 +141,81 @@ __device__ __forceinline__ void sh_colour(const SetP& S, uint32_t gi, const View
 template <int MAXV>
 __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batch<MAXV> b, Ws ws) {
   const uint32_t u = blockIdx.x * 256u + threadIdx.x;
-  if (u >= b.units) return;
-  const ViewP& V = b.views[view_of_unit(b, u)];
+  const bool in_range = u < b.units;   // always true (units are padded to 1024); kept for safety
+  const ViewP& V = b.views[view_of_unit(b, in_range ? u : 0u)];
   int si = 0;
   uint32_t gi = 0;
-  bool ok = unit_source(b, V, u - V.unit_off, si, gi);
+  bool ok = in_range && unit_source(b, V, u - V.unit_off, si, gi);
   float2 xy = make_float2(0.f, 0.f);
   float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 rgb = make_float4(0.f, 0.f, 0.f, 0.f);
-  float depth = 0.f, rad = 0.f;
+  float4 ext = make_float4(0.f, 0.f, 0.f, 0.f);
+  float depth = 0.f, rad = 0.f, o = 0.f;
   uint32_t touched = 0;
+  Geom G;
+  UnitTiles t;
   if (ok) {
     const SetP& S = b.sets[si];
-    Geom G;
     geometry(S, gi, V, b.cfg, G);
     ok = G.t[2] > b.cfg.z_near && G.det > 0.f;
-    float o = 1.f / (1.f + expf(-__ldg(S.logit + gi)));
+    o = 1.f / (1.f + expf(-__ldg(S.logit + gi)));
     if (ok) {
       float lmax = 0.5f * (G.A + G.C) + sqrtf(fmaxf(0.25f * (G.A - G.C) * (G.A - G.C) + G.B * G.B, 0.f));
-      if (b.cfg.extent_rule == 0) {
+      if (b.cfg.extent_rule != 1) {
         ok = o >= kAlphaMin;
-        rad = sqrtf(fmaxf(2.f * logf(255.f * o) * lmax, 0.f));
+        const float tau = 2.f * logf(255.f * o);
+        rad = sqrtf(fmaxf(tau * lmax, 0.f));
+        if (b.cfg.extent_rule == 2) {
+          // support ellipse q <= tau (widened by 2^-10): row shear m, row scale h, box rx, ry
+          const float tw = tau * kExtentMargin;
+          ext = make_float4(G.B / G.C, sqrtf(G.det) / G.C, sqrtf(fmaxf(tw * G.A, 0.f)),
+                            sqrtf(fmaxf(tw * G.C, 0.f)));
+        } else {
+          ext = make_float4(0.f, 0.f, rad, rad);
+        }
       } else {
         rad = 3.f * sqrtf(lmax);
+        ext = make_float4(0.f, 0.f, rad, rad);
       }
     }
     if (ok) {
       xy.x = V.fx * G.t[0] * G.itz + V.cx;
       xy.y = V.fy * G.t[1] * G.itz + V.cy;
-      int tx0, tx1, ty0, ty1;
-      ok = tile_rect(xy.x, xy.y, rad, V.width, V.height, b.cfg.tile_w, b.cfg.tile_h, tx0, tx1, ty0, ty1);
-      if (ok) touched = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-    }
-    if (ok) {
-      float id = 1.f / G.det;
-      co = make_float4(G.C * id, -G.B * id, G.A * id, o);
-      depth = G.t[2];
-      float Y[16], dir[3], dlen, raw[3];
-      sh_colour(S, gi, V, Y, dir, dlen, raw);
-      rgb = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), 0.f);
-    } else {
-      xy = make_float2(0.f, 0.f);
-      rad = 0.f;
+      ok = unit_tiles(xy.x, xy.y, ext, V.width, V.height, b.cfg.tile_w, b.cfg.tile_h,
+                      b.cfg.extent_rule == 2, t);
     }
   }
-  ws.xy[u] = xy;
-  ws.depth[u] = depth;
-  ws.conic_o[u] = co;
-  ws.rgb[u] = rgb;
-  ws.radius[u] = rad;
-  ws.tiles_touched[u] = touched;
+  // tile count: the rows of the tile rectangle
+  if (ok) {
+    for (int ty = t.ty0; ty <= t.ty1; ++ty) {
+      int cx0, cx1;
+      if (unit_row(t, ty, cx0, cx1)) touched += (uint32_t)(cx1 - cx0 + 1);
+    }
+  }
+  ok = ok && touched > 0;
+  if (ok) {
+    const SetP& S = b.sets[si];
+    float id = 1.f / G.det;
+    co = make_float4(G.C * id, -G.B * id, G.A * id, o);
+    depth = G.t[2];
+    float Y[16], dir[3], dlen, raw[3];
+    sh_colour(S, gi, V, Y, dir, dlen, raw);
+    rgb = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), 0.f);
+  } else {
+    xy = make_float2(0.f, 0.f);
+    rad = 0.f;
+    ext = make_float4(0.f, 0.f, 0.f, 0.f);
+    touched = 0;
+  }
+  if (in_range) {
+    ws.xy[u] = xy;
+    ws.depth[u] = depth;
+    ws.conic_o[u] = co;
+    ws.rgb[u] = rgb;
+    ws.radius[u] = rad;
+    ws.ext[u] = ext;
+    ws.tiles_touched[u] = touched;
+  }
 }
 
 // ---------------------------------------------------------------------------------------

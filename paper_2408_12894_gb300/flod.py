@@ -27,6 +27,7 @@ SEL_SHIFT = 28
 MAX_PAIRS = (1 << 32) - 8192
 DEV_CAPACITY = 0x1
 DEV_TIMEOUT = 0x2
+DEV_TILESET = 0x4
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "pair capacity exceeded", 3: "device wait timed out",
           4: "CUDA error", 5: "unsupported device (needs sm_103)", 6: "workspace too small"}
@@ -66,7 +67,7 @@ class Grads(C.Structure):
 
 class WsLayout(C.Structure):
     _fields_ = [(n, C.c_size_t) for n in ("total", "status", "pair_count", "plan", "xy", "depth",
-                                          "conic_o", "rgb", "radius", "tiles_touched",
+                                          "conic_o", "rgb", "radius", "ext", "tiles_touched",
                                           "block_sums", "slices")] + \
                [("ukeys", C.c_size_t * 2), ("uvals", C.c_size_t * 2),
                 ("keys", C.c_size_t * 2), ("vals", C.c_size_t * 2)] + \

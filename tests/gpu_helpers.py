@@ -47,6 +47,7 @@ def units(rast, view: int, n: int) -> dict:
         "conic_o": rast.region("conic_o", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n],
         "rgb": rast.region("rgb", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n],
         "radius": rast.region("radius", torch.float32, U)[u0:u0 + n],
+        "ext": rast.region("ext", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n],
         "tiles_touched": rast.region("tiles_touched", torch.int32, U)[u0:u0 + n],
     }
     return {k: v.cpu().numpy() for k, v in out.items()}
@@ -97,21 +98,69 @@ def rect_boundary_distance(u, v, r):
     return np.minimum.reduce(ds)
 
 
+def unit_tile_sets_f32(u, v, ext, valid, cam, ocfg):
+    """tiles_touched, the tile rectangle and the row segments of float32 units, decided in
+    float32 with the kernels' operations (rules 0 and 1: ext = (0, 0, r, r) rectangles;
+    rule 2: ellipse rows)."""
+    W, H = cam["width"], cam["height"]
+    ext = np.asarray(ext, dtype=np.float32)
+    px = OP.pixel_rect_xy(u, v, ext[:, 2], ext[:, 3], W, H, np.float32)
+    if ocfg.extent_rule == 2:
+        segs, touched = OP.ellipse_segments(u, v, ext, px, ocfg.tile_w, ocfg.tile_h, valid,
+                                            np.float32)
+        tr = OP.tile_rect(px, ocfg.tile_w, ocfg.tile_h, valid & (touched > 0))
+    else:
+        tr = OP.tile_rect(px, ocfg.tile_w, ocfg.tile_h, valid)
+        touched = tr[4]
+        segs = OP.rect_segments(tr[:4], touched)
+    return touched, tr[:4], segs
+
+
 def oracle_units_f32(pre, cam, ocfg):
-    """The oracle's FP64 preprocess rounded to float32, with tiles_touched decided in float32
-    by the same rectangle rule (so an integer stage fed with it has one exact answer)."""
+    """The oracle's FP64 preprocess rounded to float32, with the tile sets decided in float32
+    by the same rule (so an integer stage fed with it has one exact answer)."""
     valid = pre["valid"].numpy()
     u = pre["mean2d"][:, 0].detach().numpy().astype(np.float32)
     v = pre["mean2d"][:, 1].detach().numpy().astype(np.float32)
     r = pre["radius"].numpy().astype(np.float32)
+    ext = pre["ext"].numpy().astype(np.float32)
     u, v, r = (np.where(valid, a, np.float32(0)) for a in (u, v, r))
-    px = OP.pixel_rect_f32(u, v, r, cam["width"], cam["height"])
-    tr = OP.tile_rect(px, ocfg.tile_w, ocfg.tile_h, valid)
-    return {"u": u, "v": v, "r": r, "depth": pre["depth"].detach().numpy().astype(np.float32),
+    ext = np.where(valid[:, None], ext, np.float32(0))
+    touched, tr, segs = unit_tile_sets_f32(u, v, ext, valid, cam, ocfg)
+    return {"u": u, "v": v, "r": r, "ext": ext,
+            "depth": pre["depth"].detach().numpy().astype(np.float32),
             "conic": pre["conic"].detach().numpy().astype(np.float32),
             "opacity": pre["opacity"].detach().numpy().astype(np.float32),
             "rgb": pre["rgb"].detach().numpy().astype(np.float32),
-            "valid": valid & (tr[4] > 0), "tile_rect": tr[:4], "tiles_touched": tr[4]}
+            "valid": valid & (touched > 0), "tile_rect": tr, "segments": segs,
+            "tiles_touched": touched}
+
+
+def random_units_f32(rng, n, cam, ocfg, r_scale=4.0, aniso=20.0, depth=None):
+    """Synthetic float32 units with random support ellipses (any orientation, anisotropy up to
+    ``aniso``), partly off-screen, and their float32 tile sets."""
+    W, H = cam["width"], cam["height"]
+    u = rng.uniform(-50, W + 50, n).astype(np.float32)
+    v = rng.uniform(-50, H + 50, n).astype(np.float32)
+    th = rng.uniform(0, np.pi, n)
+    s1 = rng.gamma(2.0, r_scale, n) + 0.3
+    s2 = s1 / np.exp(rng.uniform(0, np.log(aniso), n)) + 0.3
+    c, sn = np.cos(th), np.sin(th)
+    A = c * c * s1 * s1 + sn * sn * s2 * s2
+    B = c * sn * (s1 * s1 - s2 * s2)
+    C = sn * sn * s1 * s1 + c * c * s2 * s2
+    if ocfg.extent_rule == 2:
+        ext = np.stack([B / C, np.sqrt(A * C - B * B) / C, np.sqrt(A), np.sqrt(C)], 1)
+    else:
+        r = np.sqrt(0.5 * (A + C) + np.sqrt(0.25 * (A - C) ** 2 + B * B))
+        ext = np.stack([0 * r, 0 * r, r, r], 1)
+    ext = ext.astype(np.float32)
+    valid = rng.random(n) > 0.05
+    touched, tr, segs = unit_tile_sets_f32(u, v, ext, valid, cam, ocfg)
+    d = rng.uniform(20, 60, n).astype(np.float32) if depth is None else depth
+    return {"u": u, "v": v, "r": ext[:, 3].copy(), "ext": ext, "depth": d,
+            "valid": valid & (touched > 0), "tile_rect": tr, "segments": segs,
+            "tiles_touched": touched}
 
 
 def inject_units(rast, view: int, f: dict):
@@ -124,6 +173,9 @@ def inject_units(rast, view: int, f: dict):
     rast.region("xy", torch.float32, 2 * U).view(-1, 2)[u0:u0 + n] = torch.as_tensor(xy, device=dev)
     rast.region("depth", torch.float32, U)[u0:u0 + n] = torch.as_tensor(f["depth"], device=dev)
     rast.region("radius", torch.float32, U)[u0:u0 + n] = torch.as_tensor(f["r"], device=dev)
+    ext = f["ext"] if "ext" in f else np.stack([0 * f["r"], 0 * f["r"], f["r"], f["r"]], 1)
+    rast.region("ext", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n] = \
+        torch.as_tensor(np.ascontiguousarray(ext, dtype=np.float32), device=dev)
     tt = np.where(f["valid"], f["tiles_touched"], 0).astype(np.int32)
     rast.region("tiles_touched", torch.int32, U)[u0:u0 + n] = torch.as_tensor(tt, device=dev)
     if "conic" in f:

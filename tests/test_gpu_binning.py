@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from gpu_helpers import (clear_units, inject_units, oracle_cfg, oracle_pre, oracle_units_f32,
-                         rasterizer, sorted_pairs)
+                         random_units_f32, rasterizer, sorted_pairs)
 from oracle import projection as OP
 from oracle import raster as R
 from paper_2408_12894_gb300 import flod, synth
@@ -21,9 +21,9 @@ def _oracle_lists(rast, fs, cams, ocfg):
     for i, (f, cam) in enumerate(zip(fs, cams)):
         tx = -(-cam["width"] // ocfg.tile_w)
         ty = -(-cam["height"] // ocfg.tile_h)
-        tt = np.where(f["valid"], f["tiles_touched"], 0)
-        k, v = R.bin_pairs(f["tile_rect"], tt, f["depth"], tx, tx * ty,
-                           tile_offset=rast.tile_off[i], unit_offset=rast.unit_off[i])
+        segs = tuple(np.asarray(a)[f["valid"][np.asarray(f["segments"][0])]] for a in f["segments"])
+        k, v = R.bin_segments(segs, f["depth"], tx, tx * ty, tile_offset=rast.tile_off[i],
+                              unit_offset=rast.unit_off[i])
         keys.append(k)
         vals.append(v)
     k, v = R.sort_pairs(np.concatenate(keys), np.concatenate(vals))
@@ -38,7 +38,7 @@ def _run(rast, fs, cams):
     rast.bin_sort()
     keys, vals, ranges, P, status = sorted_pairs(rast)
     k, v, rg = _oracle_lists(rast, fs, cams, ocfg)
-    assert status == 0
+    assert status == 0, status
     assert P == k.size
     assert np.array_equal(keys, k)
     assert np.array_equal(vals, v)
@@ -51,10 +51,10 @@ def _scene_units(g, s_min, cams, cfg):
     return [oracle_units_f32(oracle_pre(g, s_min, c, ocfg), c, ocfg) for c in cams]
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
-def test_binning_single_view(tile):
+@pytest.mark.parametrize("tile,rule", [((16, 16), 2), ((8, 8), 2), ((32, 8), 2), ((16, 16), 0)])
+def test_binning_single_view(tile, rule):
     g, cams = synth.scene_single_forward()
-    cfg = flod.default_config(tile_w=tile[0], tile_h=tile[1])
+    cfg = flod.default_config(tile_w=tile[0], tile_h=tile[1], extent_rule=rule)
     rast = rasterizer([g], cams, [0.0], cfg=cfg)
     P = _run(rast, _scene_units(g, 0.0, cams, cfg), cams)
     assert P > 0
@@ -69,46 +69,44 @@ def test_binning_batched_views_ragged_sizes():
     _run(rast, _scene_units(g, 0.0, cams, cfg), cams)
 
 
-def test_binning_ties_in_depth_keep_unit_order():
+@pytest.mark.parametrize("rule", [2, 0])
+def test_binning_ties_in_depth_keep_unit_order(rule):
     # 3000 Gaussians on 7 distinct depths: the stable sort must keep unit order inside a tie
     rng = np.random.default_rng(0)
     n = 3000
     cam = synth.camera((0.0, 0.0, -3.0), 256, 256)
-    f = {"u": rng.uniform(-20, 280, n).astype(np.float32),
-         "v": rng.uniform(-20, 280, n).astype(np.float32),
-         "r": rng.uniform(0.5, 40, n).astype(np.float32),
-         "depth": rng.choice(np.float32([1.0, 2.0, 2.5, 3.0, 7.25, 11.0, 100.0]), n),
-         "valid": rng.random(n) > 0.1}
-    px = OP.pixel_rect_f32(f["u"], f["v"], f["r"], 256, 256)
-    tr = OP.tile_rect(px, 16, 16, f["valid"])
-    f["tile_rect"], f["tiles_touched"] = tr[:4], tr[4]
-    f["valid"] = f["valid"] & (tr[4] > 0)
+    cfg = flod.default_config(extent_rule=rule)
+    depth = rng.choice(np.float32([1.0, 2.0, 2.5, 3.0, 7.25, 11.0, 100.0]), n)
+    f = random_units_f32(rng, n, cam, oracle_cfg(cfg), r_scale=6.0, depth=depth)
     g = synth.gaussian_set(0, n, sh_degree=0)
-    rast = rasterizer([g], [cam], [0.0])
+    rast = rasterizer([g], [cam], [0.0], cfg=cfg)
     _run(rast, [f], [cam])
 
 
 def test_binning_many_partitions_and_passes():
-    # about 6M pairs over 4 views of 1080p: > 1400 sort partitions, 6 digit passes
+    # millions of pairs over 4 views of 1080p: > 1000 sort partitions in both stages
     rng = np.random.default_rng(1)
     n = 400_000
     cams = [synth.camera((0.0, 0.0, -40.0 - i), 1920, 1080) for i in range(4)]
-    fs = []
-    for c in cams:
-        f = {"u": rng.uniform(-50, 1970, n).astype(np.float32),
-             "v": rng.uniform(-50, 1130, n).astype(np.float32),
-             "r": rng.gamma(2.0, 4.0, n).astype(np.float32),
-             "depth": rng.uniform(20, 60, n).astype(np.float32),
-             "valid": np.ones(n, bool)}
-        px = OP.pixel_rect_f32(f["u"], f["v"], f["r"], 1920, 1080)
-        tr = OP.tile_rect(px, 16, 16, f["valid"])
-        f["tile_rect"], f["tiles_touched"] = tr[:4], tr[4]
-        f["valid"] = tr[4] > 0
-        fs.append(f)
+    cfg = flod.default_config()
+    fs = [random_units_f32(rng, n, c, oracle_cfg(cfg), r_scale=5.0) for c in cams]
     g = synth.gaussian_set(0, n, sh_degree=0)
-    rast = rasterizer([g], cams, [0.0], pair_capacity=12_000_000)
+    rast = rasterizer([g], cams, [0.0], cfg=cfg, pair_capacity=12_000_000)
     P = _run(rast, fs, cams)
     assert P > 4_000_000
+
+
+def test_binning_huge_splats_span_many_slices():
+    # a few hundred splats that each cover hundreds of tiles, over 8x8 tiles
+    rng = np.random.default_rng(2)
+    n = 600
+    cam = synth.camera((0.0, 0.0, -3.0), 1280, 720)
+    cfg = flod.default_config(tile_w=8, tile_h=8)
+    f = random_units_f32(rng, n, cam, oracle_cfg(cfg), r_scale=60.0, aniso=8.0)
+    g = synth.gaussian_set(0, n, sh_degree=0)
+    rast = rasterizer([g], [cam], [0.0], cfg=cfg, pair_capacity=4_000_000)
+    P = _run(rast, [f], [cam])
+    assert P > 100_000
 
 
 def test_binning_empty():
@@ -126,6 +124,7 @@ def test_capacity_overflow_is_reported_not_faulted():
     cfg = flod.default_config()
     fs = _scene_units(g, 0.0, cams, cfg)
     need = int(np.where(fs[0]["valid"], fs[0]["tiles_touched"], 0).sum())
+    assert need > 2048
     rast = rasterizer([g], cams, [0.0], cfg=cfg, pair_capacity=need // 2)
     clear_units(rast)
     inject_units(rast, 0, fs[0])

@@ -28,8 +28,8 @@ def _stage_render(g, cam, cfg, s_min=0.0):
     f = oracle_units_f32(pre, cam, ocfg)
     tx = -(-cam["width"] // cfg.tile_w)
     ty = -(-cam["height"] // cfg.tile_h)
-    tt = np.where(f["valid"], f["tiles_touched"], 0)
-    k, v = R.bin_pairs(f["tile_rect"], tt, f["depth"], tx, tx * ty)
+    segs = tuple(np.asarray(a)[f["valid"][np.asarray(f["segments"][0])]] for a in f["segments"])
+    k, v = R.bin_segments(segs, f["depth"], tx, tx * ty)
     k, v = R.sort_pairs(k, v)
     rg = R.tile_ranges(k, tx * ty)
     rast = rasterizer([g], [cam], [s_min], cfg=cfg, pair_capacity=max(k.size, 1024))

@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 import torch
 
 from oracle import gaussians as G
@@ -136,3 +137,144 @@ def test_near_plane_culls():
          "s_opt": np.full((3, 3), -3.0), "opacity_logit": np.zeros(3), "sh": np.zeros((3, 1, 3))}
     pre = R.preprocess(R.params(g), 0, 0.0, cam, R.Config())
     assert list(pre["valid"].numpy()) == [False, False, True]
+
+
+# ---------------------------------------------------------------------------------------
+# rule 2: ellipse rows
+# ---------------------------------------------------------------------------------------
+def _random_splats(seed, n, W, H):
+    """Random 2D Gaussians: anisotropy up to 1:40, any orientation, partly off-screen."""
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(0, np.pi, n)
+    s1 = np.exp(rng.uniform(np.log(0.3), np.log(25.0), n))
+    s2 = s1 / np.exp(rng.uniform(0, np.log(40.0), n))
+    R_ = np.stack([np.cos(th), -np.sin(th), np.sin(th), np.cos(th)], 1).reshape(n, 2, 2)
+    D = np.zeros((n, 2, 2))
+    D[:, 0, 0], D[:, 1, 1] = s1 ** 2, s2 ** 2
+    cov = R_ @ D @ R_.transpose(0, 2, 1) + 0.3 * np.eye(2)[None]
+    u = rng.uniform(-30, W + 30, n)
+    v = rng.uniform(-30, H + 30, n)
+    o = rng.uniform(0.003, 1.0, n)
+    return u, v, cov, o
+
+
+def _alpha(u, v, cov, o, W, H):
+    """o exp(-q/2) at every pixel centre, FP64 [n, H, W] (conic from numpy's inverse)."""
+    inv = np.linalg.inv(cov)
+    xs = np.arange(W) + 0.5
+    ys = np.arange(H) + 0.5
+    dx = xs[None, None, :] - u[:, None, None]
+    dy = ys[None, :, None] - v[:, None, None]
+    q = inv[:, 0, 0, None, None] * dx * dx + 2 * inv[:, 0, 1, None, None] * dx * dy \
+        + inv[:, 1, 1, None, None] * dy * dy
+    return o[:, None, None] * np.exp(-0.5 * q)
+
+
+def _listed(segs, n, tiles_x, tiles_y):
+    out = np.zeros((n, tiles_y, tiles_x), bool)
+    for j, ty, a, b in zip(*segs):
+        out[j, ty, a:b + 1] = True
+    return out
+
+
+def _rule2(u, v, cov, o, W, H, tile, dtype=np.float64):
+    ext, ok = P.ellipse_extent(torch.as_tensor(cov), torch.as_tensor(o))
+    e = ext.numpy()
+    if dtype == np.float32:
+        u, v, e = u.astype(np.float32), v.astype(np.float32), e.astype(np.float32)
+    px = P.pixel_rect_xy(u, v, e[:, 2], e[:, 3], W, H, dtype)
+    return P.ellipse_segments(u, v, e, px, tile, tile, ok.numpy(), dtype), e, ok.numpy()
+
+
+def test_ellipse_extent_closed_forms():
+    # axis-aligned: m = 0, h = sx / sy, rx = sqrt(tau) sx, ry = sqrt(tau) sy
+    cov = torch.tensor([[[9.0, 0.0], [0.0, 4.0]]], dtype=torch.float64)
+    o = torch.tensor([0.5], dtype=torch.float64)
+    e, ok = P.ellipse_extent(cov, o)
+    tau = 2 * math.log(255 * 0.5) * (1 + 2.0 ** -10)
+    np.testing.assert_allclose(e[0].numpy(), [0.0, 1.5, 3 * math.sqrt(tau), 2 * math.sqrt(tau)],
+                               rtol=1e-14)
+    assert bool(ok[0])
+    # rotated: the boundary, sampled from the eigen-decomposition, has x extremes +-rx,
+    # y extremes +-ry, and every boundary point satisfies x = m dy +- h sqrt(ry^2 - dy^2)
+    u, v, covs, oo = _random_splats(11, 50, 100, 100)
+    e, ok = P.ellipse_extent(torch.as_tensor(covs), torch.as_tensor(oo))
+    e = e.numpy()
+    t = np.linspace(0, 2 * np.pi, 20001)
+    for i in np.nonzero(ok.numpy())[0]:
+        lam, V = np.linalg.eigh(covs[i])
+        tau = 2 * math.log(255 * oo[i]) * (1 + 2.0 ** -10)
+        pts = (V @ (np.sqrt(tau * lam)[:, None] * np.stack([np.cos(t), np.sin(t)])))
+        m, h, rx, ry = e[i]
+        assert abs(pts[0].max() - rx) <= 1e-6 * rx and abs(pts[1].max() - ry) <= 1e-6 * ry
+        w = h * np.sqrt(np.maximum(ry * ry - pts[1] ** 2, 0))
+        off = np.minimum(np.abs(pts[0] - (m * pts[1] + w)), np.abs(pts[0] - (m * pts[1] - w)))
+        assert off.max() <= 1e-6 * rx + 1e-3 * h * ry * np.sqrt(2 * np.pi / 20001)
+    # culled below 1/255 and for a singular covariance
+    e, ok = P.ellipse_extent(torch.tensor([[[1.0, 0.0], [0.0, 1.0]], [[1.0, 1.0], [1.0, 1.0]]],
+                                          dtype=torch.float64),
+                             torch.tensor([0.5 / 255, 0.5], dtype=torch.float64))
+    assert not ok.any() and float(e.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("seed,tile", [(0, 16), (1, 8)])
+def test_ellipse_rows_cover_every_supported_pixel(seed, tile):
+    W, H = 120, 90
+    u, v, cov, o = _random_splats(seed, 400, W, H)
+    a = _alpha(u, v, cov, o, W, H)
+    tx, ty = -(-W // tile), -(-H // tile)
+    for dtype, thr in ((np.float64, 1 / 255), (np.float32, (1 / 255) * (1 + 1e-4))):
+        (segs, touched), _, ok = _rule2(u, v, cov, o, W, H, tile, dtype)
+        lst = _listed(segs, u.size, tx, ty)
+        assert np.array_equal(touched, lst.reshape(u.size, -1).sum(1))
+        need = a >= thr
+        cov_tiles = np.zeros((u.size, ty, tx), bool)
+        jj, yy, xx = np.nonzero(need)
+        cov_tiles[jj, yy // tile, xx // tile] = True
+        assert not np.any(cov_tiles & ~lst), dtype
+
+
+@pytest.mark.parametrize("seed,tile", [(2, 16), (3, 8)])
+def test_ellipse_rows_are_tight(seed, tile):
+    # every listed tile's pixel-centre rectangle meets the ellipse q <= tau: the minimum of
+    # the convex q over the rectangle, taken on its edges (1D closed form), is <= tau
+    W, H = 120, 90
+    u, v, cov, o = _random_splats(seed, 300, W, H)
+    (segs, touched), e, ok = _rule2(u, v, cov, o, W, H, tile)
+    inv = np.linalg.inv(cov)
+    tau = np.where(ok, 2 * np.log(255 * o) * (1 + 2.0 ** -10), 0)
+
+    def qmin(j, xa, xb, ya, yb):
+        a, b, c = inv[j, 0, 0], inv[j, 0, 1], inv[j, 1, 1]
+        if xa <= u[j] <= xb and ya <= v[j] <= yb:
+            return 0.0
+        best = np.inf
+        for xe in (xa, xb):
+            dx = xe - u[j]
+            dy = np.clip(-b * dx / c, ya - v[j], yb - v[j])
+            best = min(best, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+        for ye in (ya, yb):
+            dy = ye - v[j]
+            dx = np.clip(-b * dy / a, xa - u[j], xb - u[j])
+            best = min(best, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+        return best
+
+    n_tiles = 0
+    for j, tyi, c0, c1 in zip(*segs):
+        ya = max(tyi * tile, 0) + 0.5
+        yb = min(tyi * tile + tile - 1, H - 1) + 0.5
+        for txi in range(c0, c1 + 1):
+            xa = txi * tile + 0.5
+            xb = min(txi * tile + tile - 1, W - 1) + 0.5
+            assert qmin(j, xa, xb, ya, yb) <= tau[j] * (1 + 1e-9) + 1e-12
+            n_tiles += 1
+    assert n_tiles == touched.sum() > 500
+
+
+def test_ellipse_rows_f32_mirror_matches_f64_rule_almost_everywhere():
+    W, H = 1920, 1080
+    u, v, cov, o = _random_splats(7, 20000, W, H)
+    (s64, t64), _, _ = _rule2(u, v, cov, o, W, H, 16)
+    (s32, t32), _, _ = _rule2(u, v, cov, o, W, H, 16, np.float32)
+    assert np.mean(t64 != t32) < 2e-3
+    assert abs(int(t64.sum()) - int(t32.sum())) <= 1e-4 * t64.sum()

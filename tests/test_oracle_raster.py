@@ -15,20 +15,22 @@ def _scene(seed, n, W=64, H=64, s_mean=-3.0, deg=0, radius=1.0):
     return g, cam
 
 
-@pytest.mark.parametrize("seed,n,W,H,tile", [(0, 200, 64, 64, 16), (1, 150, 70, 45, 16),
-                                             (2, 200, 64, 64, 8), (3, 120, 40, 40, 32)])
-def test_tiled_equals_per_pixel_brute_force(seed, n, W, H, tile):
+@pytest.mark.parametrize("seed,n,W,H,tile,rule", [(0, 200, 64, 64, 16, 2), (1, 150, 70, 45, 16, 2),
+                                                  (2, 200, 64, 64, 8, 2), (3, 120, 40, 40, 32, 2),
+                                                  (0, 200, 64, 64, 16, 0), (2, 200, 64, 64, 8, 0)])
+def test_tiled_equals_per_pixel_brute_force(seed, n, W, H, tile, rule):
     g, cam = _scene(seed, n, W, H)
-    cfg = R.Config(tile_w=tile, tile_h=tile if tile != 32 else 8)
+    cfg = R.Config(tile_w=tile, tile_h=tile if tile != 32 else 8, extent_rule=rule)
     img_t, tf_t, _ = R.render(g, 0, 0.0, cam, cfg, tiled=True)
     img_b, tf_b, _ = R.render(g, 0, 0.0, cam, cfg, tiled=False)
     np.testing.assert_allclose(img_t, img_b, atol=1e-12)
     np.testing.assert_allclose(tf_t, tf_b, atol=1e-12)
 
 
-def test_binning_invariants_and_per_tile_brute_force():
+@pytest.mark.parametrize("rule", [0, 2])
+def test_binning_invariants_and_per_tile_brute_force(rule):
     g, cam = _scene(4, 300, 80, 48, s_mean=-2.5)
-    cfg = R.Config()
+    cfg = R.Config(extent_rule=rule)
     pre = R.preprocess(R.params(g), 0, 0.0, cam, cfg)
     keys, vals, ranges, tx, ty = R.tile_lists(pre, cam, cfg)
     assert keys.size == int(pre["tiles_touched"].sum())
@@ -37,16 +39,27 @@ def test_binning_invariants_and_per_tile_brute_force():
     nz = ranges[ranges[:, 1] > ranges[:, 0]]
     assert nz[0, 0] == 0 and nz[-1, 1] == keys.size
     assert np.all(nz[1:, 0] == nz[:-1, 1])
-    # brute force per tile: Gaussians whose rectangle covers the tile, by (depth, index)
-    t0, t1, u0, u1 = pre["tile_rect"]
+    # brute force per tile: Gaussians whose tile set holds the tile, by (depth, index)
+    su, sy, sx0, sx1 = pre["segments"]
+    if rule == 0:
+        t0, t1, u0, u1 = pre["tile_rect"]
+        assert su.size == int(np.where(pre["tiles_touched"] > 0, u1 - u0 + 1, 0).sum())
     depth = pre["depth"].detach().numpy().astype(np.float32)
     for tile in range(tx * ty):
         x, y = tile % tx, tile // tx
-        cover = np.nonzero((t0 <= x) & (x <= t1) & (u0 <= y) & (y <= u1)
-                           & (pre["tiles_touched"] > 0))[0]
+        cover = np.unique(su[(sy == y) & (sx0 <= x) & (x <= sx1)])
         want = cover[np.lexsort((cover, depth[cover]))]
         s, e = ranges[tile]
         assert np.array_equal(vals[s:e], want)
+
+
+def test_ellipse_rows_list_fewer_pairs_than_the_circle_and_render_the_same():
+    g, cam = _scene(5, 400, 96, 64, s_mean=-2.5)
+    pres = {r: R.preprocess(R.params(g), 0, 0.0, cam, R.Config(extent_rule=r)) for r in (0, 2)}
+    assert pres[2]["tiles_touched"].sum() < 0.95 * pres[0]["tiles_touched"].sum()
+    imgs = {r: R.render_tiled(pres[r], cam, R.Config(extent_rule=r)) for r in (0, 2)}
+    np.testing.assert_allclose(imgs[2][0], imgs[0][0], atol=1e-12)
+    np.testing.assert_allclose(imgs[2][1], imgs[0][1], atol=1e-12)
 
 
 def test_single_gaussian_renders_its_analytic_falloff():
