@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
 //   1. rescans the block's 1024 pair counts (slot start positions);
 //   2. counts the tile rows of the slots that overlap the slice and scans them: each
 //      (slot, tile row) is one work item;
-//   3. evaluates the items, kEmitItems at a time, one per thread and step: the row's tile
-//      columns (UnitTiles/unit_row, the rule preprocess counted with), a block scan of their
+//   3. evaluates the items, split evenly over the threads (consecutive items per thread, at
+//      most kEmitPerThread per round): the row's tile columns (UnitTiles/unit_row, the rule preprocess counted with), a block scan of their
 //      counts for the row's first position, and, for a row that overlaps the slice, a
 //      "segment": its first tile id (minus its first slice position) and its unit, with the
 //      segment's id marked at that position;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
 // Threads stay converged whatever the mix of splat sizes, writes are coalesced, and a block
 // of huge splats is spread over many CTAs. A slot whose rows hold another tile count than
 // preprocess stored sets FLOD_DEV_TILESET.
-constexpr int kEmitItems = 2048;
+constexpr uint32_t kEmitPerThread = 8;
 constexpr uint16_t kNoSeg = 0xffffu;
 
 template <int MAXV>
@@ -229,10 +229,14 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
     for (int j = 0; j < 4; ++j) {
       nrow[j] = 0;
       if (cnt[j] && pre[j] < r1 && pre[j] + cnt[j] > r0) {
-        UnitTiles t;
-        uint32_t row_base, tiles_x;
-        if (slot_tiles(b, ws, unit[j], t, row_base, tiles_x)) nrow[j] = (uint32_t)(t.ty1 - t.ty0 + 1);
-        else set_status(ws.status, FLOD_DEV_TILESET);
+        const ViewP& V = b.views[view_of_unit(b, unit[j])];
+        const float2 xy = ws.xy[unit[j]];
+        const float4 e = ws.ext[unit[j]];
+        int px0, px1, py0, py1;
+        if (pixel_rect(xy.x, xy.y, e.z, e.w, V.width, V.height, px0, px1, py0, py1))
+          nrow[j] = (uint32_t)(py1 / b.cfg.tile_h - py0 / b.cfg.tile_h + 1);
+        else
+          set_status(ws.status, FLOD_DEV_TILESET);
       }
     }
     uint32_t n_items;
@@ -254,22 +258,23 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
       }
       p_first = s_pre[lo];
     }
-    // 3. items, kEmitItems per round, 8 consecutive items per thread
+    // 3. items, `per` consecutive items per thread and round
     uint32_t carry = p_first;
-    for (uint32_t ib = 0; ib < n_items; ib += kEmitItems) {
-      const uint32_t i0 = ib + 8u * tid;
+    const uint32_t per = min(kEmitPerThread, (n_items + 255u) / 256u);
+    for (uint32_t ib = 0; ib < n_items; ib += 256u * per) {
+      const uint32_t i0 = ib + per * tid;
       int slot = -1;
       UnitTiles t;
       uint32_t row_base = 0, tiles_x = 0;
-      uint32_t nn[8], tile0[8];
-      int sl[8];
+      uint32_t nn[kEmitPerThread], tile0[kEmitPerThread];
+      int sl[kEmitPerThread];
       uint32_t mine = 0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < (int)kEmitPerThread; ++k) {
         nn[k] = 0;
         sl[k] = -1;
         const uint32_t i = i0 + k;
-        if (i >= n_items) continue;
+        if (k >= (int)per || i >= n_items) continue;
         if (slot < 0) {                        // last slot whose first item is <= i
           int lo = 0, hi = kScanBlock - 1;
           while (lo < hi) {
@@ -293,17 +298,36 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
         mine += nn[k];
       }
       uint32_t round_total;
-      uint32_t pos = carry + block_excl_sum(mine, warp_tot, round_total);
+      const uint32_t pos0 = carry + block_excl_sum(mine, warp_tot, round_total);
+      // segment ids: one shared-memory atomic per warp
+      uint32_t nmine = 0, pos = pos0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < (int)kEmitPerThread; ++k) {
+        if (nn[k] && pos < r1 && pos + nn[k] > r0) ++nmine;
+        pos += nn[k];
+      }
+      const int lane = tid & 31;
+      uint32_t incl = nmine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      uint32_t wbase = 0;
+      if (lane == 31 && incl) wbase = atomicAdd(&s_nseg, incl);
+      wbase = __shfl_sync(0xffffffffu, wbase, 31);
+      uint32_t id = wbase + incl - nmine;
+      pos = pos0;
+#pragma unroll
+      for (int k = 0; k < (int)kEmitPerThread; ++k) {
         if (nn[k] && pos < r1 && pos + nn[k] > r0) {
           const uint32_t first = max(pos, r0);
-          const uint32_t id = atomicAdd(&s_nseg, 1u);
           if (id < (uint32_t)kEmitSlice) {
             s_owner[first - r0] = (uint16_t)id;
             s_seg_tile[id] = tile0[k] + (first - pos) - (first - r0);
             s_seg_slot[id] = (uint16_t)sl[k];
           }
+          ++id;
         }
         pos += nn[k];
       }
