@@ -131,9 +131,10 @@ typedef struct {
   size_t rgb;           /* float4 [units] (r, g, b, 0) */
   size_t radius;        /* float [units] extent radius in pixels (rules 0, 1; rule 2: the
                            rule-0 circle radius, informational) */
-  size_t ext;           /* float4 [units] tile-set parameters (m, h, rx, ry): rule 2 the
-                           support ellipse's row shear and scale and bounding half-widths,
-                           rules 0 and 1 (0, 0, r, r) */
+  size_t ext;           /* float4 [units] the support ellipse (alpha >= 1/255, widened by a
+                           relative 2^-10) as (m, h, rx, ry): its rows are
+                           x = u + m dy +- h sqrt(ry^2 - dy^2), its bounding half-widths rx,
+                           ry; zero when the support is empty. Rule 2 bins by it */
   size_t tiles_touched; /* uint32 [units], 0 when culled */
   size_t block_sums;    /* uint64 [units/1024 + 1] exclusive pair offsets per 1024 units */
   size_t slices;        /* uint32 [units/1024 + 1] exclusive count of 4096-pair emission slices */

@@ -69,15 +69,14 @@ def preprocess(p: dict, sh_degree: int, s_min: float, cam: dict, cfg: Config) ->
     rgb, rgb_raw = SH.colour(p["sh"], p["means"], cam_pos, sh_degree)
     valid = in_front & (det.detach() > 0) & ok
     u, v = mean2d[:, 0].detach().numpy(), mean2d[:, 1].detach().numpy()
+    ext, ok2 = P.ellipse_extent(cov2d.detach(), o.detach())   # the support ellipse
     if cfg.extent_rule == 2:
-        ext, ok2 = P.ellipse_extent(cov2d.detach(), o.detach())
         valid = valid & ok2
         e = ext.numpy()
         px = P.pixel_rect_xy(u, v, e[:, 2], e[:, 3], cam["width"], cam["height"])
         segs, touched = P.ellipse_segments(u, v, e, px, cfg.tile_w, cfg.tile_h, valid.numpy())
         tr = P.tile_rect(px, cfg.tile_w, cfg.tile_h, valid.numpy() & (touched > 0))
     else:
-        ext = torch.stack([torch.zeros_like(r), torch.zeros_like(r), r, r], dim=1)
         px = P.pixel_rect(u, v, r.numpy(), cam["width"], cam["height"])
         tr = P.tile_rect(px, cfg.tile_w, cfg.tile_h, valid.numpy())
         touched = tr[4]

@@ -138,8 +138,10 @@ __device__ __forceinline__ bool slot_tiles(const Batch<MAXV>& b, const Ws& ws, u
   const float2 xy = ws.xy[u];
   row_base = V.tile_off;
   tiles_x = V.tiles_x;
-  return unit_tiles(xy.x, xy.y, ws.ext[u], V.width, V.height, b.cfg.tile_w, b.cfg.tile_h,
-                    b.cfg.extent_rule == 2, t);
+  const bool rows = b.cfg.extent_rule == 2;
+  const float r = rows ? 0.f : ws.radius[u];
+  return unit_tiles(xy.x, xy.y, rows ? ws.ext[u] : make_float4(0.f, 0.f, r, r), V.width,
+                    V.height, b.cfg.tile_w, b.cfg.tile_h, rows, t);
 }
 
 // Block-wide exclusive sum over 256 threads (8 warps); also returns the total.
@@ -231,9 +233,16 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
       if (cnt[j] && pre[j] < r1 && pre[j] + cnt[j] > r0) {
         const ViewP& V = b.views[view_of_unit(b, unit[j])];
         const float2 xy = ws.xy[unit[j]];
-        const float4 e = ws.ext[unit[j]];
+        float rx, ry;
+        if (b.cfg.extent_rule == 2) {
+          const float4 e = ws.ext[unit[j]];
+          rx = e.z;
+          ry = e.w;
+        } else {
+          rx = ry = ws.radius[unit[j]];
+        }
         int px0, px1, py0, py1;
-        if (pixel_rect(xy.x, xy.y, e.z, e.w, V.width, V.height, px0, px1, py0, py1))
+        if (pixel_rect(xy.x, xy.y, rx, ry, V.width, V.height, px0, px1, py0, py1))
           nrow[j] = (uint32_t)(py1 / b.cfg.tile_h - py0 / b.cfg.tile_h + 1);
         else
           set_status(ws.status, FLOD_DEV_TILESET);

@@ -238,7 +238,7 @@ __device__ __forceinline__ bool unit_row(const UnitTiles& t, int ty, int& cx0, i
 
 // Per-pixel opacity of a splat: alpha = min(0.99, o * exp(-q/2)) with
 // q = a dx^2 + 2 b dx dy + c dy^2, dx = px - u. The conic arrives pre-scaled by -log2(e)/2
-// (see scale_conic), so exp(-q/2) = 2^(q') with one hardware ex2 (splat_alpha_row). Written with explicit
+// (see scale_conic), so exp(-q/2) = 2^(q') with one hardware ex2 (splat_alpha). Written with explicit
 // roundings so that the forward and the backward pass recompute bit-identical values.
 constexpr float kNegHalfLog2e = -0.5f * 1.4426950408889634f;
 
@@ -261,11 +261,23 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 // With t0 = (a' dx) dx and t1 = (2b') dx computed once per Gaussian and column,
 // q' = t0 + dy (t1 + c' dy) for each pixel row of that column.
-__device__ __forceinline__ float splat_alpha_row(float t0, float t1, float dy, float4 cs,
-                                                 float& g) {
-  const float qs = __fmaf_rn(dy, __fmaf_rn(cs.z, dy, t1), t0);
+__device__ __forceinline__ float splat_q(float t0, float t1, float dy, float4 cs) {
+  return __fmaf_rn(dy, __fmaf_rn(cs.z, dy, t1), t0);
+}
+
+// The skip rule alpha < 1/255 taken on q' before any exponential: o 2^q' >= 1/255 <=>
+// q' >= -log2(255 o) (the splat's threshold, computed once per batch load). The forward and
+// the backward take the decision with the same numbers.
+__device__ __forceinline__ float splat_qmin(float o) {
+  float l;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(255.f * o));
+  return -l;
+}
+
+// alpha = min(0.99, o 2^q'), with g = 2^q' (= exp(-q/2)) returned for the backward.
+__device__ __forceinline__ float splat_alpha(float qs, float o, float& g) {
   g = ex2_approx(qs);
-  return fminf(kAlphaMax, __fmul_rn(cs.w, g));
+  return fminf(kAlphaMax, __fmul_rn(o, g));
 }
 
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {

@@ -161,28 +161,26 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batc
     o = 1.f / (1.f + expf(-__ldg(S.logit + gi)));
     if (ok) {
       float lmax = 0.5f * (G.A + G.C) + sqrtf(fmaxf(0.25f * (G.A - G.C) * (G.A - G.C) + G.B * G.B, 0.f));
+      const float tau = 2.f * logf(255.f * o);   // alpha >= 1/255 <=> q <= tau
+      if (o >= kAlphaMin) {
+        // support ellipse q <= tau (widened by 2^-10): row shear m, row scale h, box rx, ry
+        const float tw = tau * kExtentMargin;
+        ext = make_float4(G.B / G.C, sqrtf(G.det) / G.C, sqrtf(fmaxf(tw * G.A, 0.f)),
+                          sqrtf(fmaxf(tw * G.C, 0.f)));
+      }
       if (b.cfg.extent_rule != 1) {
         ok = o >= kAlphaMin;
-        const float tau = 2.f * logf(255.f * o);
         rad = sqrtf(fmaxf(tau * lmax, 0.f));
-        if (b.cfg.extent_rule == 2) {
-          // support ellipse q <= tau (widened by 2^-10): row shear m, row scale h, box rx, ry
-          const float tw = tau * kExtentMargin;
-          ext = make_float4(G.B / G.C, sqrtf(G.det) / G.C, sqrtf(fmaxf(tw * G.A, 0.f)),
-                            sqrtf(fmaxf(tw * G.C, 0.f)));
-        } else {
-          ext = make_float4(0.f, 0.f, rad, rad);
-        }
       } else {
         rad = 3.f * sqrtf(lmax);
-        ext = make_float4(0.f, 0.f, rad, rad);
       }
     }
     if (ok) {
       xy.x = V.fx * G.t[0] * G.itz + V.cx;
       xy.y = V.fy * G.t[1] * G.itz + V.cy;
-      ok = unit_tiles(xy.x, xy.y, ext, V.width, V.height, b.cfg.tile_w, b.cfg.tile_h,
-                      b.cfg.extent_rule == 2, t);
+      const bool rows = b.cfg.extent_rule == 2;
+      ok = unit_tiles(xy.x, xy.y, rows ? ext : make_float4(0.f, 0.f, rad, rad), V.width,
+                      V.height, b.cfg.tile_w, b.cfg.tile_h, rows, t);
     }
   }
   // tile count: the rows of the tile rectangle

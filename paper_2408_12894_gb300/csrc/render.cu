@@ -4,8 +4,8 @@
 // Forward: a CTA renders one tile; each thread owns PIX pixels of one column. The tile's
 // sorted Gaussians are staged into shared memory in batches (mean, conic pre-scaled by
 // -log2(e)/2 with the opacity, colour); every pixel walks them front to back:
-//   alpha = min(0.99, o exp(-q/2)); skip alpha < 1/255; stop before the Gaussian that
-//   would take T below 1e-4; C += rgb alpha T; T *= 1 - alpha.
+//   alpha = min(0.99, o exp(-q/2)); skip alpha < 1/255 (decided on q before the exponential);
+//   stop before the Gaussian that would take T below 1e-4; C += rgb alpha T; T *= 1 - alpha.
 // The CTA leaves the tile as soon as every pixel has stopped (__syncthreads_count).
 //
 // Backward: the same tiles, every pixel walking back to front from its last blended
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
                                                           Ws ws, float* __restrict__ out_rgb,
                                                           float* __restrict__ out_T,
                                                           uint32_t* __restrict__ out_nc) {
-  __shared__ float2 s_xy[256];
+  __shared__ float4 s_xq[256];    // mean x, y and the skip threshold q'_min
   __shared__ float4 s_cs[256];
   __shared__ float4 s_rgb[256];
   const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
@@ -97,36 +97,33 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
       const int cnt = (int)min((uint32_t)batch, rg.y - start);
       for (int k = tid; k < cnt; k += nthr) {
         const uint32_t id = vals[start + k];
-        s_xy[k] = ws.xy[id];
-        s_cs[k] = scale_conic(ws.conic_o[id]);
+        const float2 m = ws.xy[id];
+        const float4 co = ws.conic_o[id];
+        s_xq[k] = make_float4(m.x, m.y, splat_qmin(co.w), 0.f);
+        s_cs[k] = scale_conic(co);
         s_rgb[k] = ws.rgb[id];
       }
       __syncthreads();
       if (!done) {
         for (int k = 0; k < cnt; ++k) {
-          const float2 m = s_xy[k];
+          const float4 mq = s_xq[k];
           const float4 cs = s_cs[k];
-          const float dx = fx - m.x;
+          const float dx = fx - mq.x;
           const float t0 = __fmul_rn(__fmul_rn(cs.x, dx), dx);
           const float t1 = __fmul_rn(cs.y, dx);
           ++pos;
-          bool any_live = false;
 #pragma unroll
           for (int j = 0; j < PIX; ++j) {
-            if (!live[j]) continue;
+            const float qs = splat_q(t0, t1, fy[j] - mq.y, cs);
+            if (!live[j] || qs < mq.z) continue;     // stopped, or alpha < 1/255
             float g;
-            const float a = splat_alpha_row(t0, t1, fy[j] - m.y, cs, g);
-            if (a < kAlphaMin) {
-              any_live = true;
-              continue;
-            }
+            const float a = splat_alpha(qs, cs.w, g);
             const float Tn = T[j] * (1.f - a);
             if (Tn < kTMin) {
               live[j] = false;
               stop[j] = pos;
               continue;
             }
-            any_live = true;
             const float4 c = s_rgb[k];
             const float w = a * T[j];
             c0[j] += w * c.x;
@@ -135,10 +132,21 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
             T[j] = Tn;
             last[j] = pos;
           }
-          if (!any_live) {
-            done = true;
-            break;
+          if ((k & 7) == 7) {              // every eighth splat: leave once all pixels stopped
+            bool any_live = false;
+#pragma unroll
+            for (int j = 0; j < PIX; ++j) any_live = any_live || live[j];
+            if (!any_live) {
+              done = true;
+              break;
+            }
           }
+        }
+        if (!done) {
+          bool any_live = false;
+#pragma unroll
+          for (int j = 0; j < PIX; ++j) any_live = any_live || live[j];
+          done = !any_live;
         }
       }
     }
@@ -271,7 +279,9 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         s_xy[k] = ws.xy[id];
         const float4 co = ws.conic_o[id];
         s_co[k] = co;
-        s_cs[k] = scale_conic(co);
+        float4 cs = scale_conic(co);
+        cs.w = splat_qmin(co.w);     // the opacity stays in s_co
+        s_cs[k] = cs;
         s_rgb[k] = ws.rgb[id];
       }
       __syncthreads();
@@ -279,7 +289,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         const uint32_t pos = bstart - rg.x + (uint32_t)k + 1u;
         const float2 m = s_xy[k];
         const float4 co = s_co[k];
-        const float4 cs = s_cs[k];
+        const float4 cs = s_cs[k];   // (a', 2b', c', q'_min)
         const float dx = fx - m.x;
         const float t0 = __fmul_rn(__fmul_rn(cs.x, dx), dx);
         const float t1 = __fmul_rn(cs.y, dx);
@@ -291,9 +301,10 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         for (int j = 0; j < PIX; ++j) {
           if (pos > last[j]) continue;
           const float dy = fy[j] - m.y;
+          const float qs = splat_q(t0, t1, dy, cs);
+          if (qs < cs.w) continue;                   // alpha < 1/255
           float gg;
-          const float a = splat_alpha_row(t0, t1, dy, cs, gg);
-          if (a < kAlphaMin) continue;
+          const float a = splat_alpha(qs, co.w, gg);
           if (!have_c) {
             c = s_rgb[k];
             have_c = true;

@@ -98,18 +98,19 @@ def rect_boundary_distance(u, v, r):
     return np.minimum.reduce(ds)
 
 
-def unit_tile_sets_f32(u, v, ext, valid, cam, ocfg):
+def unit_tile_sets_f32(u, v, r, ext, valid, cam, ocfg):
     """tiles_touched, the tile rectangle and the row segments of float32 units, decided in
-    float32 with the kernels' operations (rules 0 and 1: ext = (0, 0, r, r) rectangles;
-    rule 2: ellipse rows)."""
+    float32 with the kernels' operations (rules 0 and 1: the square of radius r; rule 2: the
+    rows of the support ellipse ext)."""
     W, H = cam["width"], cam["height"]
-    ext = np.asarray(ext, dtype=np.float32)
-    px = OP.pixel_rect_xy(u, v, ext[:, 2], ext[:, 3], W, H, np.float32)
     if ocfg.extent_rule == 2:
+        ext = np.asarray(ext, dtype=np.float32)
+        px = OP.pixel_rect_xy(u, v, ext[:, 2], ext[:, 3], W, H, np.float32)
         segs, touched = OP.ellipse_segments(u, v, ext, px, ocfg.tile_w, ocfg.tile_h, valid,
                                             np.float32)
         tr = OP.tile_rect(px, ocfg.tile_w, ocfg.tile_h, valid & (touched > 0))
     else:
+        px = OP.pixel_rect_f32(u, v, r, W, H)
         tr = OP.tile_rect(px, ocfg.tile_w, ocfg.tile_h, valid)
         touched = tr[4]
         segs = OP.rect_segments(tr[:4], touched)
@@ -126,7 +127,7 @@ def oracle_units_f32(pre, cam, ocfg):
     ext = pre["ext"].numpy().astype(np.float32)
     u, v, r = (np.where(valid, a, np.float32(0)) for a in (u, v, r))
     ext = np.where(valid[:, None], ext, np.float32(0))
-    touched, tr, segs = unit_tile_sets_f32(u, v, ext, valid, cam, ocfg)
+    touched, tr, segs = unit_tile_sets_f32(u, v, r, ext, valid, cam, ocfg)
     return {"u": u, "v": v, "r": r, "ext": ext,
             "depth": pre["depth"].detach().numpy().astype(np.float32),
             "conic": pre["conic"].detach().numpy().astype(np.float32),
@@ -149,16 +150,13 @@ def random_units_f32(rng, n, cam, ocfg, r_scale=4.0, aniso=20.0, depth=None):
     A = c * c * s1 * s1 + sn * sn * s2 * s2
     B = c * sn * (s1 * s1 - s2 * s2)
     C = sn * sn * s1 * s1 + c * c * s2 * s2
-    if ocfg.extent_rule == 2:
-        ext = np.stack([B / C, np.sqrt(A * C - B * B) / C, np.sqrt(A), np.sqrt(C)], 1)
-    else:
-        r = np.sqrt(0.5 * (A + C) + np.sqrt(0.25 * (A - C) ** 2 + B * B))
-        ext = np.stack([0 * r, 0 * r, r, r], 1)
+    ext = np.stack([B / C, np.sqrt(A * C - B * B) / C, np.sqrt(A), np.sqrt(C)], 1)
     ext = ext.astype(np.float32)
+    r = np.sqrt(0.5 * (A + C) + np.sqrt(0.25 * (A - C) ** 2 + B * B)).astype(np.float32)
     valid = rng.random(n) > 0.05
-    touched, tr, segs = unit_tile_sets_f32(u, v, ext, valid, cam, ocfg)
+    touched, tr, segs = unit_tile_sets_f32(u, v, r, ext, valid, cam, ocfg)
     d = rng.uniform(20, 60, n).astype(np.float32) if depth is None else depth
-    return {"u": u, "v": v, "r": ext[:, 3].copy(), "ext": ext, "depth": d,
+    return {"u": u, "v": v, "r": r, "ext": ext, "depth": d,
             "valid": valid & (touched > 0), "tile_rect": tr, "segments": segs,
             "tiles_touched": touched}
 
@@ -173,9 +171,8 @@ def inject_units(rast, view: int, f: dict):
     rast.region("xy", torch.float32, 2 * U).view(-1, 2)[u0:u0 + n] = torch.as_tensor(xy, device=dev)
     rast.region("depth", torch.float32, U)[u0:u0 + n] = torch.as_tensor(f["depth"], device=dev)
     rast.region("radius", torch.float32, U)[u0:u0 + n] = torch.as_tensor(f["r"], device=dev)
-    ext = f["ext"] if "ext" in f else np.stack([0 * f["r"], 0 * f["r"], f["r"], f["r"]], 1)
     rast.region("ext", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n] = \
-        torch.as_tensor(np.ascontiguousarray(ext, dtype=np.float32), device=dev)
+        torch.as_tensor(np.ascontiguousarray(f["ext"], dtype=np.float32), device=dev)
     tt = np.where(f["valid"], f["tiles_touched"], 0).astype(np.int32)
     rast.region("tiles_touched", torch.int32, U)[u0:u0 + n] = torch.as_tensor(tt, device=dev)
     if "conic" in f:

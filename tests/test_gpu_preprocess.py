@@ -46,10 +46,11 @@ def _check_view(rast, view, g, s_min, cam):
     sh = np.maximum(np.abs(ext_o[both, :2]).max(axis=1, keepdims=True), 1e-3)
     np.testing.assert_allclose(ext_g[both, :2] / sh, ext_o[both, :2] / sh, atol=2e-4)
     # the tile count is exactly the float32 rule applied to the kernel's own (u, v, ext)
-    tt_mirror, _, _ = unit_tile_sets_f32(got["xy"][:, 0], got["xy"][:, 1], ext_g,
-                                         ext_g[:, 2] > 0, cam, ocfg)
+    tt_mirror, _, _ = unit_tile_sets_f32(got["xy"][:, 0], got["xy"][:, 1], got["radius"], ext_g,
+                                         valid_g, cam, ocfg)
     assert np.array_equal(got["tiles_touched"], tt_mirror)
-    assert np.array_equal(valid_g, ext_g[:, 2] > 0)
+    if ocfg.extent_rule != 1:
+        assert np.all(ext_g[valid_g, 3] > 0)
     # and the FP64 rule's count almost everywhere
     assert np.mean(got["tiles_touched"][both] == pre["tiles_touched"][both]) >= 0.995
 
