@@ -10,10 +10,13 @@
 //
 // Backward: the same tiles, every pixel walking back to front from its last blended
 // Gaussian (n_contrib) and recovering T by multiplying with 1 / (1 - alpha), so no per-pair
-// state is stored. d(alpha) = sum_c g_c (rgb_c T - S_c / (1 - alpha)), S = colour behind +
-// T_final bg. Each thread sums its PIX pixels; a warp then reduces the nine per-Gaussian
-// gradients with a transposing butterfly and the owning lanes add them with atomics;
-// warps where no pixel touches the Gaussian skip the reduction.
+// state is stored. d(alpha) = T (g . rgb) - P / (1 - alpha), with P = g . S the upstream
+// gradient against the colour behind (S, background T_final bg included), kept as one
+// scalar per pixel. The conic and mean gradients are linear in dL/dq times dx^2, dx dy,
+// dy^2, dx, dy; dx is fixed per thread (one column), so a thread sums only the moments
+// (1, dy, dy^2) of dL/dq over its PIX pixels and expands them once per Gaussian. A warp then
+// reduces the nine per-Gaussian gradients with a transposing butterfly and the owning lanes
+// add them with atomics; warps where no pixel touches the Gaussian skip the reduction.
 //
 // Launch modes: one CTA per tile in tile order, or persistent CTAs (about the number that
 // fit on the GPU) taking tiles from the largest-first queue that flod_bin_sort builds.
@@ -241,7 +244,9 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
     const uint2 rg = ws.ranges[tile];
     const float fx = (float)px + 0.5f;
     const uint64_t npix = (uint64_t)V.width * V.height;
-    float T[PIX], g0[PIX], g1[PIX], g2[PIX], S0[PIX], S1[PIX], S2[PIX], fy[PIX];
+    // per pixel: T, the upstream gradient g, and P = g . (colour behind the current splat,
+    // background included), the only use of that colour in the chain rule
+    float T[PIX], g0[PIX], g1[PIX], g2[PIX], P[PIX], fy[PIX];
     uint32_t last[PIX];
     uint32_t my_max = 0;
 #pragma unroll
@@ -258,9 +263,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         g1[j] = dL[3 * V.pix_off + npix + p];
         g2[j] = dL[3 * V.pix_off + 2 * npix + p];
       }
-      S0[j] = T[j] * b.cfg.bg[0];
-      S1[j] = T[j] * b.cfg.bg[1];
-      S2[j] = T[j] * b.cfg.bg[2];
+      P[j] = T[j] * (g0[j] * b.cfg.bg[0] + g1[j] * b.cfg.bg[1] + g2[j] * b.cfg.bg[2]);
       my_max = max(my_max, last[j]);
       evals += last[j];
     }
@@ -290,49 +293,56 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         const float2 m = s_xy[k];
         const float4 co = s_co[k];
         const float4 cs = s_cs[k];   // (a', 2b', c', q'_min)
+        const float4 c = s_rgb[k];
         const float dx = fx - m.x;
         const float t0 = __fmul_rn(__fmul_rn(cs.x, dx), dx);
         const float t1 = __fmul_rn(cs.y, dx);
-        float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // this thread's sums over its pixels: colour gradient, and the moments
+        // E0 = sum e, E1 = sum e dy, E2 = sum e dy^2 of e = G dL/dalpha (unclamped alpha)
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f, E0 = 0.f, E1 = 0.f, E2 = 0.f;
         bool any = false;
-        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool have_c = false;
 #pragma unroll
         for (int j = 0; j < PIX; ++j) {
           if (pos > last[j]) continue;
           const float dy = fy[j] - m.y;
           const float qs = splat_q(t0, t1, dy, cs);
           if (qs < cs.w) continue;                   // alpha < 1/255
+          any = true;
           float gg;
           const float a = splat_alpha(qs, co.w, gg);
-          if (!have_c) {
-            c = s_rgb[k];
-            have_c = true;
-          }
-          any = true;
           const float ioma = rcp_approx(1.f - a);
-          T[j] *= ioma;
+          T[j] *= ioma;                              // T in front of this splat
           const float w = a * T[j];
-          acc[6] += w * g0[j];
-          acc[7] += w * g1[j];
-          acc[8] += w * g2[j];
-          const float dalpha = g0[j] * (c.x * T[j] - S0[j] * ioma) +
-                               g1[j] * (c.y * T[j] - S1[j] * ioma) +
-                               g2[j] * (c.z * T[j] - S2[j] * ioma);
-          S0[j] += c.x * w;
-          S1[j] += c.y * w;
-          S2[j] += c.z * w;
+          r0 += w * g0[j];
+          r1 += w * g1[j];
+          r2 += w * g2[j];
+          const float gc = g0[j] * c.x + g1[j] * c.y + g2[j] * c.z;
+          const float dalpha = T[j] * gc - ioma * P[j];
+          P[j] += w * gc;
           if (co.w * gg < kAlphaMax) {
-            acc[2] += gg * dalpha;
-            const float dq = -0.5f * co.w * gg * dalpha;   // dL/dq
-            acc[3] += dq * dx * dx;
-            acc[4] += dq * 2.f * dx * dy;
-            acc[5] += dq * dy * dy;
-            acc[0] -= dq * 2.f * (co.x * dx + co.y * dy);
-            acc[1] -= dq * 2.f * (co.y * dx + co.z * dy);
+            const float e = gg * dalpha;
+            const float ed = e * dy;
+            E0 += e;
+            E1 += ed;
+            E2 += ed * dy;
           }
         }
-        if (__any_sync(0xffffffffu, any)) warp_reduce_add9(acc, ws.grad2d + 3ull * s_id[k]);
+        if (__any_sync(0xffffffffu, any)) {
+          // dL/dq = -o/2 e; q = a dx^2 + 2 b dx dy + c dy^2, dq/du = -2 (a dx + b dy), ...
+          const float hq = -0.5f * co.w;
+          const float Q0 = hq * E0, Q1 = hq * E1;
+          float acc[9];
+          acc[0] = -2.f * (co.x * dx * Q0 + co.y * Q1);
+          acc[1] = -2.f * (co.y * dx * Q0 + co.z * Q1);
+          acc[2] = E0;
+          acc[3] = dx * dx * Q0;
+          acc[4] = 2.f * dx * Q1;
+          acc[5] = hq * E2;
+          acc[6] = r0;
+          acc[7] = r1;
+          acc[8] = r2;
+          warp_reduce_add9(acc, ws.grad2d + 3ull * s_id[k]);
+        }
       }
       bend = bstart;
     }
