@@ -36,9 +36,13 @@ METRIC = "1080p frames/s fwd & fwd+bwd it/s (3M Gaussians), batched vs per-view"
 WORKLOAD = "FLoD 5-level scene, level 5 (3M Gaussians, SH3), 1920x1080, fwd+bwd per level"
 # peak of plain float32 ALU work: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# algorithmic float32 work per (pixel, Gaussian) evaluation, FMA = 2 (derivation in the design doc)
-FLOP_FWD_EVAL = 25
-FLOP_BWD_EVAL = 80
+# FP32 operations (an FFMA counts 2) of the blending kernels: per evaluated (pixel, Gaussian)
+# pair -- the offset, q and its threshold test, with the per-column terms shared by the
+# thread's pixels -- and on top for each pair the forward blended (alpha, transmittance,
+# colour; backward: T recovery, colour, alpha and moment gradients). The nine-value warp
+# reduction is overhead, not counted.
+FLOP_FWD_EVAL, FLOP_FWD_BLEND = 8, 13
+FLOP_BWD_EVAL, FLOP_BWD_BLEND = 7, 31
 
 
 def parse():
@@ -346,8 +350,11 @@ def run_flod(a):
 
     fwd_evals = (ev_after[0] - ev_before[0]) / a.steps
     bwd_evals = (ev_after[1] - ev_before[1]) / a.steps
-    kernels = {"render_fwd": (stage_ms["render_fwd"], fwd_evals * FLOP_FWD_EVAL),
-               "blend_bwd": (stage_ms["blend_bwd"], bwd_evals * FLOP_BWD_EVAL)}
+    blended = (ev_after[2] - ev_before[2]) / a.steps
+    kernels = {"render_fwd": (stage_ms["render_fwd"],
+                              fwd_evals * FLOP_FWD_EVAL + blended * FLOP_FWD_BLEND),
+               "blend_bwd": (stage_ms["blend_bwd"],
+                             bwd_evals * FLOP_BWD_EVAL + blended * FLOP_BWD_BLEND)}
     dom = max(kernels, key=lambda k: kernels[k][0])
     d_ms, d_flop = kernels[dom]
     achieved = d_flop / (d_ms * 1e-3) / 1e12
@@ -372,7 +379,7 @@ def run_flod(a):
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "step_ms_median": statistics.median(step_ms),
             "wall_ms_per_step": 1e3 * t_wall / a.steps,
-            "evals_per_step": {"fwd": fwd_evals, "bwd": bwd_evals},
+            "evals_per_step": {"fwd": fwd_evals, "bwd": bwd_evals, "blended": blended},
             "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved,
                          "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / ALU_PEAK_TFLOPS, "traffic": None,

@@ -124,7 +124,8 @@ typedef struct {
   size_t pair_count;    /* uint64 pairs emitted by the last flod_bin_sort */
   size_t plan;          /* uint32[64] radix-sort plan; plan[63] = buffer index of the result;
                            uint64 at plan[48] / plan[50]: running count of (pixel, Gaussian)
-                           evaluations of the blending forward / backward kernels */
+                           evaluations of the blending forward / backward kernels; at
+                           plan[52]: of the pairs the forward blended */
   size_t xy;            /* float2 [units] projected mean (u, v) */
   size_t depth;         /* float [units] view-space z */
   size_t conic_o;       /* float4 [units] (a, b, c, opacity), q = a dx^2 + 2b dx dy + c dy^2 */

@@ -112,6 +112,7 @@ constexpr int kEmitSlice = 4096;     // output positions per emission slice
 constexpr int kQueueHeader = 66;     // queue[0..32] bucket counts, [33..65] offsets, then tiles
 constexpr int kPlanEvalFwd = 48;     // uint64 running count of forward evaluations
 constexpr int kPlanEvalBwd = 50;     // uint64 running count of backward evaluations
+constexpr int kPlanBlended = 52;     // uint64 running count of blended (pixel, Gaussian) pairs
 constexpr int kPlanFinal = 63;       // buffer holding the sorted result
 
 constexpr int kRadixBits = 9;                        // digit width of one sort pass

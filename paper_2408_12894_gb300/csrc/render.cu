@@ -25,7 +25,7 @@
 
 namespace flod {
 
-// one 64-bit atomic per CTA: the number of (pixel, Gaussian) evaluations of the launch
+// one 64-bit atomic per CTA: a count of (pixel, Gaussian) pairs of the launch
 __device__ __forceinline__ void add_evals(uint32_t* counter, uint32_t evals) {
   __shared__ unsigned long long s_ev;
   if (threadIdx.x == 0) s_ev = 0;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
   const int batch = b.cfg.batch;
-  uint32_t evals = 0;
+  uint32_t evals = 0, blended = 0;
   uint32_t tile;
   for (bool first = true; next_tile<PERSIST>(ws, b.tiles, 0, first, tile); first = false) {
     const ViewP& V = b.views[view_of_tile(b, tile)];
@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
             c2[j] += w * c.z;
             T[j] = Tn;
             last[j] = pos;
+            ++blended;
           }
           if ((k & 7) == 7) {              // every eighth splat: leave once all pixels stopped
             bool any_live = false;
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
     }
   }
   add_evals(ws.plan + kPlanEvalFwd, evals);
+  add_evals(ws.plan + kPlanBlended, blended);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -386,9 +386,10 @@ class Rasterizer:
                             grads_c, stream)
 
     def eval_counts(self):
-        """Running (forward, backward) counts of (pixel, Gaussian) evaluations."""
+        """Running counts of (pixel, Gaussian) pairs: (forward evaluations, backward
+        evaluations, pairs the forward blended)."""
         plan = self.region("plan", torch.int64, 32)
-        return int(plan[24].item()), int(plan[25].item())
+        return int(plan[24].item()), int(plan[25].item()), int(plan[26].item())
 
     def ensure_capacity(self) -> bool:
         """True if the last bin_sort fitted; otherwise regrow (caller re-runs the stages)."""
