@@ -103,14 +103,20 @@ __device__ __forceinline__ void geometry(const SetP& S, uint32_t gi, const ViewP
   G.det = G.A * G.C - G.B * G.B;
 }
 
-// Colour of a unit (and the pre-clamp value), SH of degree deg.
-__device__ __forceinline__ void sh_colour(const SetP& S, uint32_t gi, const ViewP& V, float* Y,
-                                          float dir[3], float& dlen, float raw[3]) {
+// Unit view direction from the camera centre to the mean, and its length.
+__device__ __forceinline__ void view_dir(const SetP& S, uint32_t gi, const ViewP& V, float dir[3],
+                                         float& dlen) {
   const float* mu = S.means + 3ull * gi;
   float dx = __ldg(mu) - V.cpx, dy = __ldg(mu + 1) - V.cpy, dz = __ldg(mu + 2) - V.cpz;
   dlen = sqrtf(dx * dx + dy * dy + dz * dz);
   float il = 1.f / dlen;
   dir[0] = dx * il; dir[1] = dy * il; dir[2] = dz * il;
+}
+
+// Colour of a unit (and the pre-clamp value), SH of degree deg.
+__device__ __forceinline__ void sh_colour(const SetP& S, uint32_t gi, const ViewP& V, float* Y,
+                                          float dir[3], float& dlen, float raw[3]) {
+  view_dir(S, gi, V, dir, dlen);
   const int K = (S.deg + 1) * (S.deg + 1);
   sh_basis(S.deg, dir[0], dir[1], dir[2], Y);
   raw[0] = raw[1] = raw[2] = 0.5f;
@@ -281,20 +287,36 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
   Geom G;
   geometry(S, gi, V, b.cfg, G);
 
-  // ---- colour -> SH coefficients and view direction
-  float Y[16], dir[3], dlen, raw[3];
-  sh_colour(S, gi, V, Y, dir, dlen, raw);
-  const float drgb[3] = {raw[0] > 0.f ? g2.x : 0.f, raw[1] > 0.f ? g2.y : 0.f,
-                         raw[2] > 0.f ? g2.z : 0.f};
+  // ---- colour -> SH coefficients and view direction. The forward stored max(raw, 0), so
+  // a channel is clamped (no gradient) exactly where the stored colour is 0.
+  const float4 rgb = ws.rgb[u];
+  const float drgb[3] = {rgb.x > 0.f ? g2.x : 0.f, rgb.y > 0.f ? g2.y : 0.f,
+                         rgb.z > 0.f ? g2.z : 0.f};
+  float Y[16], dir[3], dlen;
+  view_dir(S, gi, V, dir, dlen);
+  sh_basis(S.deg, dir[0], dir[1], dir[2], Y);
   float dmu[3] = {0.f, 0.f, 0.f};
   if (drgb[0] != 0.f || drgb[1] != 0.f || drgb[2] != 0.f) {
     const float* c = S.sh + 3ull * K * gi;
     float wk[16];
+    if (S.deg == 3) {
+      const float4* c4 = reinterpret_cast<const float4*>(c);
+      float cf[48];
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-      wk[k] = k < K ? __ldg(c + 3 * k) * drgb[0] + __ldg(c + 3 * k + 1) * drgb[1] +
-                          __ldg(c + 3 * k + 2) * drgb[2]
-                    : 0.f;
+      for (int i = 0; i < 12; ++i) {
+        const float4 v = __ldg(c4 + i);
+        cf[4 * i] = v.x; cf[4 * i + 1] = v.y; cf[4 * i + 2] = v.z; cf[4 * i + 3] = v.w;
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        wk[k] = cf[3 * k] * drgb[0] + cf[3 * k + 1] * drgb[1] + cf[3 * k + 2] * drgb[2];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        wk[k] = k < K ? __ldg(c + 3 * k) * drgb[0] + __ldg(c + 3 * k + 1) * drgb[1] +
+                            __ldg(c + 3 * k + 2) * drgb[2]
+                      : 0.f;
+    }
     float gx, gy, gz;
     sh_grad_dir(S.deg, dir[0], dir[1], dir[2], wk, gx, gy, gz);
     const float proj = gx * dir[0] + gy * dir[1] + gz * dir[2];
