@@ -136,6 +136,11 @@ typedef struct {
                            relative 2^-10) as (m, h, rx, ry): its rows are
                            x = u + m dy +- h sqrt(ry^2 - dy^2), its bounding half-widths rx,
                            ry; zero when the support is empty. Rule 2 bins by it */
+  size_t trec;          /* uint4 [units] tile record written by preprocess for the emission:
+                           x = tx0 | ty0 << 16 (first tile column and row), y = rows |
+                           mode << 16; mode 0: z, w hold up to 4 rows of (column offset,
+                           count) in 8 + 8 bits; mode 1: z = tiles per row; mode 2: rows are
+                           recomputed from xy and ext */
   size_t tiles_touched; /* uint32 [units], 0 when culled */
   size_t block_sums;    /* uint64 [units/1024 + 1] exclusive pair offsets per 1024 units */
   size_t slices;        /* uint32 [units/1024 + 1] exclusive count of 4096-pair emission slices */

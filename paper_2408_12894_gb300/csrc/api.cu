@@ -151,6 +151,7 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   L.rgb = take(16 * u);
   L.radius = take(4 * u);
   L.ext = take(16 * u);
+  L.trec = take(16 * u);
   L.tiles_touched = take(4 * u);
   L.block_sums = take(8 * (u / kScanBlock + 1));
   L.slices = take(4 * (u / kScanBlock + 1));
@@ -188,6 +189,7 @@ Ws ws_ptrs(void* base, const Plan& P) {
   w.rgb = reinterpret_cast<float4*>(b + L.rgb);
   w.radius = reinterpret_cast<float*>(b + L.radius);
   w.ext = reinterpret_cast<float4*>(b + L.ext);
+  w.trec = reinterpret_cast<uint4*>(b + L.trec);
   w.tiles_touched = reinterpret_cast<uint32_t*>(b + L.tiles_touched);
   w.block_sums = reinterpret_cast<unsigned long long*>(b + L.block_sums);
   w.slices = reinterpret_cast<uint32_t*>(b + L.slices);

@@ -225,27 +225,16 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
     }
     if (tid == 255) s_pre[kScanBlock] = run;
     const uint32_t r1 = min(r0 + (uint32_t)kEmitSlice, total);
-    // 2. tile rows of the slots that overlap the slice
+    // 2. tile rows of the slots that overlap the slice (from their tile records)
     uint32_t nrow[4];
+    uint4 rec[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       nrow[j] = 0;
       if (cnt[j] && pre[j] < r1 && pre[j] + cnt[j] > r0) {
-        const ViewP& V = b.views[view_of_unit(b, unit[j])];
-        const float2 xy = ws.xy[unit[j]];
-        float rx, ry;
-        if (b.cfg.extent_rule == 2) {
-          const float4 e = ws.ext[unit[j]];
-          rx = e.z;
-          ry = e.w;
-        } else {
-          rx = ry = ws.radius[unit[j]];
-        }
-        int px0, px1, py0, py1;
-        if (pixel_rect(xy.x, xy.y, rx, ry, V.width, V.height, px0, px1, py0, py1))
-          nrow[j] = (uint32_t)(py1 / b.cfg.tile_h - py0 / b.cfg.tile_h + 1);
-        else
-          set_status(ws.status, FLOD_DEV_TILESET);
+        rec[j] = ws.trec[unit[j]];
+        nrow[j] = rec[j].y & 0xffffu;
+        if (!nrow[j]) set_status(ws.status, FLOD_DEV_TILESET);
       }
     }
     uint32_t n_items;
@@ -274,6 +263,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
       const uint32_t i0 = ib + per * tid;
       int slot = -1;
       UnitTiles t;
+      uint4 rc = make_uint4(0u, 0u, 0u, 0u);
       uint32_t row_base = 0, tiles_x = 0;
       uint32_t nn[kEmitPerThread], tile0[kEmitPerThread];
       int sl[kEmitPerThread];
@@ -284,6 +274,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
         sl[k] = -1;
         const uint32_t i = i0 + k;
         if (k >= (int)per || i >= n_items) continue;
+        bool fresh = false;
         if (slot < 0) {                        // last slot whose first item is <= i
           int lo = 0, hi = kScanBlock - 1;
           while (lo < hi) {
@@ -291,17 +282,34 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
             if (s_row[mid] <= i) lo = mid; else hi = mid - 1;
           }
           slot = lo;
-          slot_tiles(b, ws, s_unit[slot], t, row_base, tiles_x);
+          fresh = true;
         }
         while (s_row[slot + 1] <= i) {         // next slot with rows
           ++slot;
-          if (s_row[slot + 1] > i) slot_tiles(b, ws, s_unit[slot], t, row_base, tiles_x);
+          fresh = true;
         }
-        const int ty = t.ty0 + (int)(i - s_row[slot]);
-        int cx0, cx1;
-        if (unit_row(t, ty, cx0, cx1)) {
-          nn[k] = (uint32_t)(cx1 - cx0 + 1);
-          tile0[k] = row_base + (uint32_t)ty * tiles_x + (uint32_t)cx0;   // row's first tile
+        if (fresh) {
+          const uint32_t uu = s_unit[slot];
+          rc = ws.trec[uu];
+          const ViewP& V = b.views[view_of_unit(b, uu)];
+          row_base = V.tile_off;
+          tiles_x = V.tiles_x;
+          if ((rc.y >> 16) == kRecCompute) slot_tiles(b, ws, uu, t, row_base, tiles_x);
+        }
+        const int r = (int)(i - s_row[slot]);
+        const uint32_t mode = rc.y >> 16;
+        const uint32_t tx0 = rc.x & 0xffffu, ty = (rc.x >> 16) + (uint32_t)r;
+        if (mode == kRecCompute) {
+          int cx0, cx1;
+          if (unit_row(t, t.ty0 + r, cx0, cx1)) {
+            nn[k] = (uint32_t)(cx1 - cx0 + 1);
+            tile0[k] = row_base + ty * tiles_x + (uint32_t)cx0;
+          }
+        } else {
+          uint32_t off = 0, cnt = rc.z;
+          if (mode == kRecTable) rec_row(rc, r, off, cnt);
+          nn[k] = cnt;
+          tile0[k] = row_base + ty * tiles_x + tx0 + off;
         }
         sl[k] = slot;
         mine += nn[k];

@@ -79,7 +79,8 @@ struct Ws {
   float4* conic_o;
   float4* rgb;
   float* radius;
-  float4* ext;             // (m, h, rx, ry) of the unit's tile set (see UnitTiles)
+  float4* ext;             // (m, h, rx, ry): the unit's support ellipse (see UnitTiles)
+  uint4* trec;             // the unit's tile record (see rec_row)
   uint32_t* tiles_touched;
   unsigned long long* block_sums;
   uint32_t* slices;
@@ -209,6 +210,22 @@ __device__ __forceinline__ bool unit_tiles(float u, float v, float4 e, int W, in
   t.th = th;
   t.rows = rows;
   return true;
+}
+
+// A unit's tile set as preprocess found it, for the emission ("tile record", uint4):
+//   x = tx0 | ty0 << 16       first tile column and row of the rectangle (within the view)
+//   y = rows | mode << 16     tile rows of the rectangle, and how the rows are given:
+//   mode kRecTable   z, w = up to 4 rows of (column offset from tx0, count) in 8 + 8 bits
+//   mode kRecUniform z = tile count of every row (offset 0: rectangle rules)
+//   mode kRecCompute the rows are recomputed from (u, v, ext) with unit_row
+constexpr uint32_t kRecTable = 0, kRecUniform = 1, kRecCompute = 2;
+constexpr int kRecRows = 4;
+
+__device__ __forceinline__ void rec_row(const uint4 r, int row, uint32_t& off, uint32_t& cnt) {
+  const uint32_t word = row < 2 ? r.z : r.w;
+  const uint32_t h = (word >> (16 * (row & 1))) & 0xffffu;
+  off = h & 0xffu;
+  cnt = h >> 8;
 }
 
 // Tile columns [cx0, cx1] of tile row ty (ty0 <= ty <= ty1); false if the row has none.

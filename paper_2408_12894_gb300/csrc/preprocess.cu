@@ -189,12 +189,37 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batc
                       V.height, b.cfg.tile_w, b.cfg.tile_h, rows, t);
     }
   }
-  // tile count: the rows of the tile rectangle
+  // tile count: the rows of the tile rectangle; the first rows also go to the tile record
+  uint4 rec = make_uint4(0u, 0u, 0u, 0u);
   if (ok) {
-    for (int ty = t.ty0; ty <= t.ty1; ++ty) {
-      int cx0, cx1;
-      if (unit_row(t, ty, cx0, cx1)) touched += (uint32_t)(cx1 - cx0 + 1);
+    const int tx0 = t.px0 / t.tw;
+    const uint32_t nrows = (uint32_t)(t.ty1 - t.ty0 + 1);
+    uint32_t mode = kRecTable;
+    if (!t.rows) {
+      touched = nrows * (uint32_t)(t.px1 / t.tw - tx0 + 1);
+      mode = kRecUniform;
+      rec.z = (uint32_t)(t.px1 / t.tw - tx0 + 1);
+    } else {
+      if (nrows > (uint32_t)kRecRows) mode = kRecCompute;
+      for (int ty = t.ty0; ty <= t.ty1; ++ty) {
+        int cx0, cx1;
+        uint32_t off = 0, cnt = 0;
+        if (unit_row(t, ty, cx0, cx1)) {
+          cnt = (uint32_t)(cx1 - cx0 + 1);
+          off = (uint32_t)(cx0 - tx0);
+          touched += cnt;
+        }
+        const int r = ty - t.ty0;
+        if (r < kRecRows) {
+          if (off > 255u || cnt > 255u) mode = kRecCompute;
+          const uint32_t h = (off & 0xffu) | (cnt & 0xffu) << 8;
+          if (r < 2) rec.z |= h << (16 * r);
+          else rec.w |= h << (16 * (r - 2));
+        }
+      }
     }
+    rec.x = (uint32_t)tx0 | (uint32_t)t.ty0 << 16;
+    rec.y = nrows | mode << 16;
   }
   ok = ok && touched > 0;
   if (ok) {
@@ -209,6 +234,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batc
     xy = make_float2(0.f, 0.f);
     rad = 0.f;
     ext = make_float4(0.f, 0.f, 0.f, 0.f);
+    rec = make_uint4(0u, 0u, 0u, 0u);
     touched = 0;
   }
   if (in_range) {
@@ -218,6 +244,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batc
     ws.rgb[u] = rgb;
     ws.radius[u] = rad;
     ws.ext[u] = ext;
+    ws.trec[u] = rec;
     ws.tiles_touched[u] = touched;
   }
 }

@@ -67,7 +67,7 @@ class Grads(C.Structure):
 
 class WsLayout(C.Structure):
     _fields_ = [(n, C.c_size_t) for n in ("total", "status", "pair_count", "plan", "xy", "depth",
-                                          "conic_o", "rgb", "radius", "ext", "tiles_touched",
+                                          "conic_o", "rgb", "radius", "ext", "trec", "tiles_touched",
                                           "block_sums", "slices")] + \
                [("ukeys", C.c_size_t * 2), ("uvals", C.c_size_t * 2),
                 ("keys", C.c_size_t * 2), ("vals", C.c_size_t * 2)] + \

@@ -48,6 +48,7 @@ def units(rast, view: int, n: int) -> dict:
         "rgb": rast.region("rgb", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n],
         "radius": rast.region("radius", torch.float32, U)[u0:u0 + n],
         "ext": rast.region("ext", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n],
+        "trec": rast.region("trec", torch.int32, 4 * U).view(-1, 4)[u0:u0 + n],
         "tiles_touched": rast.region("tiles_touched", torch.int32, U)[u0:u0 + n],
     }
     return {k: v.cpu().numpy() for k, v in out.items()}
@@ -117,6 +118,40 @@ def unit_tile_sets_f32(u, v, r, ext, valid, cam, ocfg):
     return touched, tr[:4], segs
 
 
+def tile_records(f, ocfg):
+    """The per-unit tile record the emission reads (uint32 [n, 4]), from a unit dict with
+    "tile_rect", "segments" and "valid": x = tx0 | ty0 << 16, y = rows | mode << 16; mode 0
+    holds up to 4 rows of (column offset, count) bytes in z, w; mode 1 (rectangle rules) the
+    per-row count in z; mode 2 (more rows, or a byte overflows) is recomputed by the kernel."""
+    tx0, tx1, ty0, ty1 = (np.asarray(a, dtype=np.int64) for a in f["tile_rect"])
+    n = tx0.size
+    valid = np.asarray(f["valid"], dtype=bool)
+    rec = np.zeros((n, 4), dtype=np.uint32)
+    rows = np.where(valid, ty1 - ty0 + 1, 0)
+    rec[:, 0] = np.where(valid, tx0 | (ty0 << 16), 0)
+    if ocfg.extent_rule != 2:
+        rec[:, 1] = np.where(valid, rows | (1 << 16), 0)
+        rec[:, 2] = np.where(valid, tx1 - tx0 + 1, 0)
+        return rec
+    mode = np.where(rows > 4, 2, 0)
+    su, sy, sx0, sx1 = (np.asarray(a, dtype=np.int64) for a in f["segments"])
+    keep = valid[su]
+    su, sy, sx0, sx1 = su[keep], sy[keep], sx0[keep], sx1[keep]
+    r = sy - ty0[su]
+    off, cnt = sx0 - tx0[su], sx1 - sx0 + 1
+    first = r < 4
+    over = np.zeros(n, bool)
+    np.logical_or.at(over, su[first], (off[first] > 255) | (cnt[first] > 255))
+    mode = np.where(over, 2, mode)
+    h = (off & 0xff) | ((cnt & 0xff) << 8)
+    for rr in range(4):
+        sel = first & (r == rr)
+        word, shift = 2 + rr // 2, 16 * (rr % 2)
+        np.bitwise_or.at(rec[:, word], su[sel], (h[sel] << shift).astype(np.uint32))
+    rec[:, 1] = np.where(valid, rows | (mode << 16), 0)
+    return rec
+
+
 def oracle_units_f32(pre, cam, ocfg):
     """The oracle's FP64 preprocess rounded to float32, with the tile sets decided in float32
     by the same rule (so an integer stage fed with it has one exact answer)."""
@@ -173,6 +208,8 @@ def inject_units(rast, view: int, f: dict):
     rast.region("radius", torch.float32, U)[u0:u0 + n] = torch.as_tensor(f["r"], device=dev)
     rast.region("ext", torch.float32, 4 * U).view(-1, 4)[u0:u0 + n] = \
         torch.as_tensor(np.ascontiguousarray(f["ext"], dtype=np.float32), device=dev)
+    rec = tile_records(f, oracle_cfg(rast.cfg)).view(np.int32)
+    rast.region("trec", torch.int32, 4 * U).view(-1, 4)[u0:u0 + n] = torch.as_tensor(rec, device=dev)
     tt = np.where(f["valid"], f["tiles_touched"], 0).astype(np.int32)
     rast.region("tiles_touched", torch.int32, U)[u0:u0 + n] = torch.as_tensor(tt, device=dev)
     if "conic" in f:

@@ -4,7 +4,7 @@ import pytest
 import torch
 
 from gpu_helpers import (oracle_cfg, oracle_pre, rasterizer, rect_boundary_distance,
-                         unit_tile_sets_f32, units)
+                         tile_records, unit_tile_sets_f32, units)
 from paper_2408_12894_gb300 import flod, synth
 
 pytestmark = pytest.mark.gpu
@@ -46,9 +46,14 @@ def _check_view(rast, view, g, s_min, cam):
     sh = np.maximum(np.abs(ext_o[both, :2]).max(axis=1, keepdims=True), 1e-3)
     np.testing.assert_allclose(ext_g[both, :2] / sh, ext_o[both, :2] / sh, atol=2e-4)
     # the tile count is exactly the float32 rule applied to the kernel's own (u, v, ext)
-    tt_mirror, _, _ = unit_tile_sets_f32(got["xy"][:, 0], got["xy"][:, 1], got["radius"], ext_g,
-                                         valid_g, cam, ocfg)
+    tt_mirror, tr_mirror, seg_mirror = unit_tile_sets_f32(got["xy"][:, 0], got["xy"][:, 1],
+                                                          got["radius"], ext_g, valid_g, cam, ocfg)
     assert np.array_equal(got["tiles_touched"], tt_mirror)
+    # and so is the tile record the emission reads (rows and first row columns)
+    rec = tile_records({"tile_rect": tr_mirror, "segments": seg_mirror, "valid": valid_g}, ocfg)
+    assert np.array_equal(got["trec"].view(np.uint32)[:, :2], rec[:, :2])
+    table = (rec[:, 1] >> 16) == 0
+    assert np.array_equal(got["trec"].view(np.uint32)[table], rec[table])
     if ocfg.extent_rule != 1:
         assert np.all(ext_g[valid_g, 3] > 0)
     # and the FP64 rule's count almost everywhere
