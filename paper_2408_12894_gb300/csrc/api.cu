@@ -77,6 +77,7 @@ struct Plan {
   uint32_t tiles_x[FLOD_MAX_VIEWS], tiles_y[FLOD_MAX_VIEWS], cap[FLOD_MAX_VIEWS];
   uint32_t max_parts;
   int n_passes;
+  int tile_bits;
 };
 
 flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* views, int n_views,
@@ -129,6 +130,7 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   int tile_bits = 1;
   while (tile_bits < 31 && (1ull << tile_bits) < t) ++tile_bits;
   P.n_passes = (tile_bits + kRadixBits - 1) / kRadixBits;   // tile digits over the pairs
+  P.tile_bits = tile_bits;
   const uint64_t parts_pairs = (pair_capacity + kSortPart - 1) / kSortPart;
   const uint64_t parts_units = (u + kSortPart - 1) / kSortPart;
   P.max_parts = (uint32_t)(parts_pairs > parts_units ? parts_pairs : parts_units);
@@ -350,7 +352,7 @@ flod_status flod_bin_sort(const flod_gaussians* sets, int n_sets, const flod_vie
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int n_passes = P.n_passes;
   return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {
-    return launch_binning(B, w, n_passes, dev->res_sort, dev->res_small,
+    return launch_binning(B, w, n_passes, P.tile_bits, dev->res_sort, dev->res_small,
                           reinterpret_cast<unsigned long long*>(d_pair_count),
                           cfg->persistent != 0, st);
   });

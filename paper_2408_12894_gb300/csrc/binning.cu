@@ -414,21 +414,37 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
   }
 }
 
+// Tile ranges from the sorted tile keys: four consecutive keys per thread (one 16-byte load),
+// a range starts or ends where a key differs from its neighbour.
 __global__ void __launch_bounds__(256) k_ranges(Ws ws, uint32_t n_tiles) {
   const unsigned long long P0 = *ws.pair_count;
   const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
   const uint32_t* keys = ws.keys[ws.plan[kPlanFinal]];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-    const uint32_t t = keys[i];
-    if (t >= n_tiles) continue;   // only after an inconsistent tile set (FLOD_DEV_TILESET)
-    if (i == 0 || keys[i - 1] != t) ws.ranges[t].x = i;
-    if (i == P - 1 || keys[i + 1] != t) ws.ranges[t].y = i + 1;
+  constexpr uint32_t kNone = 0xffffffffu;   // never a tile id
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; 4ull * q < P; q += gridDim.x * blockDim.x) {
+    const uint32_t i0 = 4u * q;
+    uint32_t k[4];
+    if (i0 + 3 < P) {
+      const uint4 v = reinterpret_cast<const uint4*>(keys)[q];
+      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j] = i0 + j < P ? keys[i0 + j] : kNone;
+    }
+    const uint32_t prev = i0 ? keys[i0 - 1] : kNone;
+    const uint32_t next = i0 + 4 < P ? keys[i0 + 4] : kNone;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t t = k[j];
+      if (t >= n_tiles) continue;   // past the end, or an inconsistent tile set (FLOD_DEV_TILESET)
+      const uint32_t before = j ? k[j - 1] : prev;
+      const uint32_t after = j < 3 ? k[j + 1] : next;
+      if (before != t) ws.ranges[t].x = i0 + j;
+      if (after != t) ws.ranges[t].y = i0 + j + 1;
+    }
   }
 }
 
-// Largest-first render order: every tile goes to bucket floor(log2(pairs)) + 1 (0 for an
-// empty tile), buckets are laid out from the largest down, and tiles land in their bucket
-// in arrival order. Persistent render CTAs then take the most expensive tiles first.
 __global__ void __launch_bounds__(256) k_queue_count(Ws ws, uint32_t n_tiles) {
   __shared__ uint32_t h[33];
   if (threadIdx.x < 33) h[threadIdx.x] = 0;
@@ -462,7 +478,8 @@ __global__ void __launch_bounds__(256) k_queue_fill(Ws ws, uint32_t n_tiles) {
 }
 
 template <int MAXV>
-cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int resident_sort,
+cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int tile_bits,
+                           int resident_sort,
                            int resident_small, unsigned long long* d_pair_count, bool build_queue,
                            cudaStream_t st) {
   const uint32_t nblocks = b.units / kScanBlock;
@@ -478,7 +495,9 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
   k_scan_blocks<<<1, 1024, 0, st>>>(ws, nblocks, d_pair_count);
   if (nblocks) k_emit<MAXV><<<resident_small, 256, 0, st>>>(b, ws, nblocks);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_pair_sort(ws, n_passes, resident_small, resident_sort, st)) != cudaSuccess) return e;
+  if ((e = launch_pair_sort(ws, n_passes, tile_bits, resident_small, resident_sort, st)) !=
+      cudaSuccess)
+    return e;
   k_ranges<<<resident_small, 256, 0, st>>>(ws, b.tiles);
   if (build_queue && b.tiles) {
     if ((e = cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t) * kQueueHeader, st)) != cudaSuccess)
@@ -491,9 +510,9 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
   return cudaGetLastError();
 }
 
-template cudaError_t launch_binning<kMaxViewsSmall>(const BatchS&, const Ws&, int, int, int,
+template cudaError_t launch_binning<kMaxViewsSmall>(const BatchS&, const Ws&, int, int, int, int,
                                                     unsigned long long*, bool, cudaStream_t);
-template cudaError_t launch_binning<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, int, int, int,
+template cudaError_t launch_binning<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, int, int, int, int,
                                                     unsigned long long*, bool, cudaStream_t);
 
 }  // namespace flod

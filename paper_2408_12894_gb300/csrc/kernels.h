@@ -22,14 +22,15 @@ cudaError_t launch_preprocess_bwd(const Batch<MAXV>& b, const Ws& ws, const Grad
 
 // binning.cu: block sums -> scan -> emit -> (sort) -> ranges
 template <int MAXV>
-cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int resident_sort,
+cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int tile_bits,
+                           int resident_sort,
                            int resident_small, unsigned long long* d_pair_count, bool build_queue,
                            cudaStream_t st);
 
 // sort.cu
 cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st);
-cudaError_t launch_pair_sort(const Ws& ws, int n_digits, int resident_small, int resident_sort,
-                             cudaStream_t st);
+cudaError_t launch_pair_sort(const Ws& ws, int n_digits, int tile_bits, int resident_small,
+                             int resident_sort, cudaStream_t st);
 int sort_kernel_smem_bytes();
 cudaError_t sort_kernel_prepare();           // opt-in shared memory size
 const void* sort_kernel_ptr();

@@ -55,7 +55,14 @@ struct Stage {
   int slot0;                         // first plan slot (digit d uses slot slot0 + d)
   int nparts_word;                   // plan word holding the partition count
   int final_word;                    // plan word receiving the result's buffer index
+  uint32_t shifts;                   // digit d: bits [shift_d, shift_d + width_d) of the key,
+  uint32_t widths;                   //   shift_d, width_d = byte d of shifts, widths
 };
+
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, const Stage& s, int d) {
+  const uint32_t sh = (s.shifts >> (8 * d)) & 0xffu, wd = (s.widths >> (8 * d)) & 0xffu;
+  return (key >> sh) & ((1u << wd) - 1u);
+}
 
 __device__ __forceinline__ uint32_t stage_count(const Stage& s) {
   if (!s.count) return s.fixed_count;
@@ -80,8 +87,7 @@ __global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st, int n_digits
     const uint32_t key = ws.tiles_touched[u] ? __float_as_uint(ws.depth[u]) : 0xffffffffu;
     st.keys[0][u] = key;
     st.vals[0][u] = u;
-    for (int d = 0; d < n_digits; ++d)
-      atomicAdd(&h[d * kRadixBins + ((key >> (kRadixBits * d)) & (kRadixBins - 1))], 1u);
+    for (int d = 0; d < n_digits; ++d) atomicAdd(&h[d * kRadixBins + digit_of(key, st, d)], 1u);
   }
   __syncthreads();
   block_hist_flush(h, ws.hist + st.slot0 * kRadixBins, n_digits);
@@ -102,8 +108,7 @@ __global__ void __launch_bounds__(256) k_hist(Ws ws, Stage st, int n_digits) {
   const uint32_t stride = gridDim.x * 256u;
   for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < P; i += stride) {
     const uint32_t k = keys[i];
-    for (int d = 0; d < n_digits; ++d)
-      atomicAdd(&h[d * kRadixBins + ((k >> (kRadixBits * d)) & (kRadixBins - 1))], 1u);
+    for (int d = 0; d < n_digits; ++d) atomicAdd(&h[d * kRadixBins + digit_of(k, st, d)], 1u);
   }
   __syncthreads();
   block_hist_flush(h, ws.hist + st.slot0 * kRadixBins, n_digits);
@@ -180,7 +185,9 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
   unsigned long long* lb = ws.lookback + (size_t)lbt * ws.max_parts * kRadixBins;
   unsigned long long* lb_next = ws.lookback + (size_t)(lbt ^ 1) * ws.max_parts * kRadixBins;
   const uint32_t* goff = ws.hist + slot * kRadixBins;
-  const int shift = kRadixBits * digit;
+  const int shift = (int)((st.shifts >> (8 * digit)) & 0xffu);
+  const uint32_t dmask = (1u << ((st.widths >> (8 * digit)) & 0xffu)) - 1u;
+  const bool live_d = (uint32_t)threadIdx.x <= dmask;   // digit values this pass can take
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int d = tid;   // digit value owned in the partition steps
@@ -206,7 +213,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
       const bool valid = wbase + r * 32 < P;
-      const uint32_t dg = (k[r] >> shift) & (kRadixBins - 1);
+      const uint32_t dg = (k[r] >> shift) & dmask;
       // lanes holding the same digit (a lane past the end matches only itself)
       const uint32_t peers = __match_any_sync(0xffffffffu, valid ? dg : 0x10000u | (uint32_t)lane);
       uint32_t before = 0;
@@ -225,9 +232,12 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
       sm.whist[w][d] = total;
       total += c;
     }
-    // publish the aggregate (or the inclusive prefix for the first partition)
-    if (part == 0) st_relaxed(lb + d, kFlagInc | total);
-    else st_relaxed(lb + (size_t)part * kRadixBins + d, kFlagAgg | total);
+    // publish the aggregate (or the inclusive prefix for the first partition); values the
+    // digit cannot take have no run and no look-back
+    if (live_d) {
+      if (part == 0) st_relaxed(lb + d, kFlagInc | total);
+      else st_relaxed(lb + (size_t)part * kRadixBins + d, kFlagAgg | total);
+    }
     lb_next[(size_t)part * kRadixBins + d] = 0;
     uint32_t x = total;
 #pragma unroll
@@ -247,7 +257,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
       if (wbase + r * 32 < P) {
-        const uint32_t dd = (k[r] >> shift) & (kRadixBins - 1);
+        const uint32_t dd = (k[r] >> shift) & dmask;
         const uint32_t pos = sm.local_start[dd] + sm.whist[wid][dd] + rank[r];
         sm.keys[pos] = k[r];
         sm.vals[pos] = v[r];
@@ -256,7 +266,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
     // windowed look-back: read up to kWindow predecessors at once, nearest first; sum their
     // aggregates up to the nearest inclusive prefix; re-poll from the first one not ready
     unsigned long long excl = 0;
-    if (part > 0) {
+    if (part > 0 && live_d) {
       int q = (int)part - 1;
       uint32_t spins = 0;
       bool done = false;
@@ -295,7 +305,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
     const uint32_t nvalid = min((uint32_t)kSortPart, P - base);
     for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
       const uint32_t key = sm.keys[i];
-      const uint32_t dd = (key >> shift) & (kRadixBins - 1);
+      const uint32_t dd = (key >> shift) & dmask;
       const uint32_t dst = sm.gbase[dd] + (i - sm.local_start[dd]);
       kout[dst] = key;
       vout[dst] = sm.vals[i];
@@ -325,10 +335,13 @@ static Stage unit_stage(const Ws& ws) {
   s.slot0 = 0;
   s.nparts_word = kPlanNPartsUnits;
   s.final_word = kPlanFinalUnits;
+  s.shifts = 0x18100800u;   // four 8-bit digits of the 32 depth bits
+  s.widths = 0x08080808u;
   return s;
 }
 
-static Stage pair_stage(const Ws& ws) {
+// The tile bits split into n_digits digits of near-equal width (each at most 9 bits).
+static Stage pair_stage(const Ws& ws, int n_digits, int tile_bits) {
   Stage s;
   s.keys[0] = ws.keys[0];
   s.keys[1] = ws.keys[1];
@@ -340,10 +353,18 @@ static Stage pair_stage(const Ws& ws) {
   s.slot0 = 4;
   s.nparts_word = kPlanNParts;
   s.final_word = kPlanFinal;
+  s.shifts = s.widths = 0;
+  int shift = 0;
+  for (int d = 0; d < n_digits; ++d) {
+    const int w = tile_bits / n_digits + (d < tile_bits % n_digits ? 1 : 0);
+    s.shifts |= (uint32_t)shift << (8 * d);
+    s.widths |= (uint32_t)w << (8 * d);
+    shift += w;
+  }
   return s;
 }
 
-// Stage "units": depth digits (32 bits -> 4 passes).
+// Stage "units": depth digits (32 bits -> 4 passes of 8 bits).
 cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st) {
   const Stage s = unit_stage(ws);
   const int n_digits = 4;
@@ -357,9 +378,9 @@ cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort
 }
 
 // Stage "pairs": tile digits (n_digits passes over the emitted pairs).
-cudaError_t launch_pair_sort(const Ws& ws, int n_digits, int resident_small, int resident_sort,
-                             cudaStream_t st) {
-  const Stage s = pair_stage(ws);
+cudaError_t launch_pair_sort(const Ws& ws, int n_digits, int tile_bits, int resident_small,
+                             int resident_sort, cudaStream_t st) {
+  const Stage s = pair_stage(ws, n_digits, tile_bits);
   cudaError_t e = cudaMemsetAsync(ws.hist + 4 * kRadixBins, 0, sizeof(uint32_t) * 4 * kRadixBins, st);
   if (e != cudaSuccess) return e;
   k_hist<<<resident_small, 256, 0, st>>>(ws, s, n_digits);
