@@ -45,6 +45,26 @@ FLOP_FWD_EVAL, FLOP_FWD_BLEND = 8, 13
 FLOP_BWD_EVAL, FLOP_BWD_BLEND = 7, 31
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from its committed full-size ncu summary, or None when
+    there is none or the kernel's sources changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_dram_level5_3M_1080p.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("|", "#", " ")):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    try:
+        srcs = [p.strip() for p in fields["sources"].split(",")]
+        sha = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in srcs)).hexdigest()
+        return int(fields["traffic_bytes_per_launch"]) if sha == fields["sources_sha256"] else None
+    except (KeyError, OSError, ValueError):
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,7 +402,8 @@ def run_flod(a):
             "evals_per_step": {"fwd": fwd_evals, "bwd": bwd_evals, "blended": blended},
             "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved,
                          "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / ALU_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / ALU_PEAK_TFLOPS,
+                         "traffic": measured_traffic("k_render_bwd") if dom == "blend_bwd" else None,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": "it/s",
                     "h2d_bytes_per_step": int(dL.numel() * 4),
