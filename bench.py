@@ -416,10 +416,10 @@ def run_flod(a):
     achieved = d_flop / (d_ms * 1e-3) / 1e12
     n_tiles = int(rast.layout.tiles)
     n_passes = (max(1, math.ceil(math.log2(max(n_tiles, 2)))) + 8) // 9   # 9-bit tile digits
-    # preprocess 1; bin_sort: unit keys, plan, 4 depth passes, block sums, scan, emit,
-    # pair histogram, plan, n_passes tile passes, ranges; render_fwd 1; blend_bwd 1;
+    # preprocess 1; bin_sort: unit keys, 4 depth passes of 3 kernels (count, scan, scatter),
+    # block sums, scan, emit, n_passes tile passes of 3, ranges; render_fwd 1; blend_bwd 1;
     # preprocess_bwd 1 (memsets not counted)
-    launches_per_step = 1 + (6 + 5 + n_passes + 1) + 1 + 1 + 1
+    launches_per_step = 1 + (1 + 12 + 3 + 3 * n_passes + 1) + 1 + 1 + 1
 
     if rank == 0:
         line = {

@@ -59,7 +59,8 @@ typedef enum {
 
 /* Device status bits (flod_read_status). */
 #define FLOD_DEV_CAPACITY 0x1u /* pairs exceeded pair_capacity: pairs beyond it dropped */
-#define FLOD_DEV_TIMEOUT 0x2u  /* radix-sort look-back wait gave up */
+#define FLOD_DEV_TIMEOUT 0x2u  /* a bounded device-side wait gave up (reserved: no kernel of
+                                  this version waits on another CTA) */
 #define FLOD_DEV_TILESET 0x4u  /* emission listed another tile count than tiles_touched
                                   (only with inconsistent per-unit inputs in the workspace) */
 
@@ -149,7 +150,7 @@ typedef struct {
   size_t keys[2];       /* uint32 [pair_capacity] x 2: tile ids of the pairs (keys[0] = emitted) */
   size_t vals[2];       /* uint32 [pair_capacity] x 2: units of the pairs */
   size_t hist;          /* radix-sort digit histograms */
-  size_t lookback;      /* radix-sort decoupled look-back tables */
+  size_t counts;        /* uint32 [512][partitions]: radix sort, per-partition digit counts */
   size_t ranges;        /* uint32x2 [tiles] [start, end) in the sorted pair list */
   size_t grad2d;        /* float4 [units][3]: (du, dv, dopacity, 0), (da, db, dc, 0), (dr, dg, db, 0) */
   size_t queue;         /* uint32 [tiles + 128]: 66 header words, then the largest-first tile order */
@@ -190,10 +191,10 @@ flod_status flod_preprocess(const flod_gaussians *sets, int n_sets, const flod_v
 
 /* (tile, depth) binning and sort: the pairs (unit, covered tile) end up ordered by the key
  * (global tile << 32) | float bits of t_z, ties by unit index -- the stable sort of the pairs
- * emitted in unit order. It is a stable LSD radix sort (9-bit digits, onesweep passes with
- * decoupled look-back) whose depth digits are sorted over units before the pairs are
- * emitted, since all pairs of a unit share them, and whose tile digits are sorted over the
- * pairs. Then the [start, end) range of every tile. The result is vals[plan[63]] (units)
+ * emitted in unit order. It is a stable LSD radix sort (reduce-then-scan passes over
+ * 4,096-key partitions; four 8-bit depth digits, tile digits of at most 9 bits) whose depth
+ * digits are sorted over units before the pairs are emitted, since all pairs of a unit share
+ * them, and whose tile digits are sorted over the pairs. Then the [start, end) range of every tile. The result is vals[plan[63]] (units)
  * with keys[plan[63]] (tile ids). Writes the pair total to *d_pair_count (device, may be
  * NULL) and to the workspace. Pairs beyond pair_capacity are dropped and FLOD_DEV_CAPACITY
  * is set. */

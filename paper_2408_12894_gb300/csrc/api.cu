@@ -166,7 +166,7 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   L.vals[0] = take(4 * pair_capacity);
   L.vals[1] = take(4 * pair_capacity);
   L.hist = take(4 * kPlanPasses * kRadixBins);
-  L.lookback = take(8ull * 2 * P.max_parts * kRadixBins);
+  L.counts = take(4ull * P.max_parts * kRadixBins);
   L.ranges = take(8 * t);
   L.grad2d = take(48 * u);
   L.queue = take(4 * (t + 128));
@@ -202,7 +202,7 @@ Ws ws_ptrs(void* base, const Plan& P) {
     w.vals[i] = reinterpret_cast<uint32_t*>(b + L.vals[i]);
   }
   w.hist = reinterpret_cast<uint32_t*>(b + L.hist);
-  w.lookback = reinterpret_cast<unsigned long long*>(b + L.lookback);
+  w.counts = reinterpret_cast<uint32_t*>(b + L.counts);
   w.ranges = reinterpret_cast<uint2*>(b + L.ranges);
   w.grad2d = reinterpret_cast<float4*>(b + L.grad2d);
   w.queue = reinterpret_cast<uint32_t*>(b + L.queue);

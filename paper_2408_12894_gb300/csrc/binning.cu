@@ -105,7 +105,8 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
     uint32_t nparts = (uint32_t)((pe + kSortPart - 1) / kSortPart);
     ws.plan[kPlanNParts] = nparts;
 #pragma unroll
-    for (int p = 4; p < kPlanPasses; ++p) ws.plan[kPlanCounter + p] = 0;   // pair-stage tickets
+    for (int p = 4; p < kPlanPasses; ++p) ws.plan[kPlanCounter + p] = 0;   // pair-stage scan tickets
+    ws.plan[kPlanSrc + 4] = 0;                                             // pair stage reads buffer 0
     ws.plan[kPlanQueue] = 0;
     ws.plan[kPlanQueue + 1] = 0;
     ws.plan[kPlanSlices] = carry_sl;

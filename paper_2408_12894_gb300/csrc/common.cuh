@@ -89,7 +89,7 @@ struct Ws {
   uint32_t* keys[2];       // pair-stage sort: tile keys
   uint32_t* vals[2];       // pair-stage sort: unit indices (the result is what renders read)
   uint32_t* hist;
-  unsigned long long* lookback;
+  uint32_t* counts;        // radix sort: per-partition digit counts, digit-major
   uint2* ranges;
   float4* grad2d;
   uint32_t* queue;
@@ -102,8 +102,7 @@ struct Ws {
 constexpr int kPlanPasses = 8;       // slots 0-3: depth digits over units; 4-7: tile digits over pairs
 constexpr int kPlanActive = 0;       // plan[kPlanActive + p] = 1 if pass p moves keys
 constexpr int kPlanSrc = 8;          // plan[kPlanSrc + p] = source buffer of pass p
-constexpr int kPlanLb = 16;          // plan[kPlanLb + p] = look-back table of pass p
-constexpr int kPlanCounter = 24;     // plan[kPlanCounter + p] = partition ticket counter
+constexpr int kPlanCounter = 24;     // plan[kPlanCounter + p] = finished digit-scan CTAs of pass p
 constexpr int kPlanNParts = 40;      // number of partitions
 constexpr int kPlanQueue = 41;       // render work-queue ticket counter (x2: fwd, bwd)
 constexpr int kPlanSlices = 43;      // number of key-emission slices

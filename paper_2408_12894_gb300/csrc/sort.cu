@@ -1,6 +1,4 @@
-// Stable LSD radix sort of the (tile, depth) pairs, 9-bit digits, one "onesweep" pass per
-// digit with decoupled look-back (Merrill & Garland's single-pass prefix scan, as used by
-// onesweep sorting), all sizes read on the device.
+// Stable LSD radix sort of the (tile, depth) pairs, all sizes read on the device.
 //
 // Every pair of a unit carries the same 32 depth bits, so the depth digits (the low half of
 // the key) are sorted over units before any pair exists (stage "units": key = depth bits,
@@ -10,40 +8,23 @@
 // (tile << 32 | depth bits) over pairs emitted in unit order: within a tile by depth, ties
 // by unit index.
 //
-//   k_unit_keys  unit keys (depth bits, or all ones for a unit with no tile) and the digit
-//                histograms of stage "units"; clears the first look-back table.
-//   k_hist       the digit histograms of the pair keys; clears the first look-back table.
-//   k_plan       per digit: exclusive digit offsets; a digit on which all keys agree is
-//                marked inactive and costs nothing; ping-pong buffer and table per pass.
-//   k_pass       persistent CTAs take 4096-key partitions in ticket order. Per partition:
-//                warp-level ranking with one match.any per key (stable: lane, round, warp
-//                order = input order), publish the per-digit counts (aggregate), reorder the
-//                partition in shared memory, look back over predecessors until an inclusive
-//                prefix is found, publish the inclusive prefix, write each digit's run.
-//
-// Every wait on a predecessor is bounded; when the bound is hit the kernel sets
-// FLOD_DEV_TIMEOUT in the status word and continues (the output is then invalid, the
-// caller sees the status).
+// Each digit is one reduce-then-scan pass over 4,096-key partitions (the classic
+// three-phase radix pass, with the scan spread over one CTA per digit value):
+//   k_count  per partition, its digit histogram -> counts[digit value][partition]
+//   k_scan   one CTA per digit value: exclusive scan of its counts over the partitions and
+//            their total; the CTA that finishes last (a ticket, nothing waits) turns the
+//            totals into digit bases and writes the pass plan: whether the pass moves keys
+//            (a digit on which all keys agree costs no scatter), its source buffer, the next
+//            pass's source
+//   k_pass   per partition: warp-level ranking, the lanes of equal digit found with one
+//            ballot per digit bit (stable: lane, round, warp order = input order), digit
+//            offsets within the partition, reorder in shared memory, and a coalesced
+//            scatter of each digit's run to base[digit] + counts[digit][partition] + offset.
+// No CTA ever waits for another, so no pass can hang on a CTA that is not scheduled.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace flod {
-
-// look-back words: 2 flag bits over a 62-bit count
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagInc = 2ull << 62;
-constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
-constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr int kWindow = 8;         // predecessors read per look-back step
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 // One sort stage: ping-pong key/value buffers, its element count and its plan slots.
 struct Stage {
@@ -59,97 +40,144 @@ struct Stage {
   uint32_t widths;                   //   shift_d, width_d = byte d of shifts, widths
 };
 
-__device__ __forceinline__ uint32_t digit_of(uint32_t key, const Stage& s, int d) {
-  const uint32_t sh = (s.shifts >> (8 * d)) & 0xffu, wd = (s.widths >> (8 * d)) & 0xffu;
-  return (key >> sh) & ((1u << wd) - 1u);
-}
-
 __device__ __forceinline__ uint32_t stage_count(const Stage& s) {
   if (!s.count) return s.fixed_count;
   const unsigned long long c = *s.count;
   return (uint32_t)(c < s.cap ? c : s.cap);
 }
 
-__device__ __forceinline__ void block_hist_flush(const uint32_t* h, uint32_t* hist, int n_digits) {
-  for (int i = threadIdx.x; i < n_digits * kRadixBins; i += blockDim.x)
-    if (h[i]) atomicAdd(&hist[i], h[i]);
+__device__ __forceinline__ const uint32_t* src_keys(const Stage& s, int src) {
+  return src ? s.keys[1] : s.keys[0];
 }
 
 // Stage "units": key = float bits of the view-space depth of a unit with tiles (positive, so
-// the bits order like the values), all ones otherwise; value = unit index.
-__global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st, int n_digits) {
-  __shared__ uint32_t h[4 * kRadixBins];
-  for (int i = threadIdx.x; i < 4 * kRadixBins; i += 256) h[i] = 0;
-  __syncthreads();
+// the bits order like the values), all ones otherwise; value = unit index. Also resets the
+// stage's plan words.
+__global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st) {
   const uint32_t U = st.fixed_count;
-  const uint32_t stride = gridDim.x * 256u;
-  for (uint32_t u = blockIdx.x * 256u + threadIdx.x; u < U; u += stride) {
-    const uint32_t key = ws.tiles_touched[u] ? __float_as_uint(ws.depth[u]) : 0xffffffffu;
-    st.keys[0][u] = key;
+  for (uint32_t u = blockIdx.x * 256u + threadIdx.x; u < U; u += gridDim.x * 256u) {
+    st.keys[0][u] = ws.tiles_touched[u] ? __float_as_uint(ws.depth[u]) : 0xffffffffu;
     st.vals[0][u] = u;
-    for (int d = 0; d < n_digits; ++d) atomicAdd(&h[d * kRadixBins + digit_of(key, st, d)], 1u);
   }
-  __syncthreads();
-  block_hist_flush(h, ws.hist + st.slot0 * kRadixBins, n_digits);
-  const uint32_t nparts = (U + kSortPart - 1) / kSortPart;
-  for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < nparts * (uint32_t)kRadixBins; i += stride)
-    ws.lookback[i] = 0;
   if (blockIdx.x == 0 && threadIdx.x < 4) ws.plan[kPlanCounter + st.slot0 + threadIdx.x] = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ws.plan[st.nparts_word] = nparts;
-}
-
-// Stage "pairs": histograms of the tile keys the emission wrote.
-__global__ void __launch_bounds__(256) k_hist(Ws ws, Stage st, int n_digits) {
-  __shared__ uint32_t h[4 * kRadixBins];
-  for (int i = threadIdx.x; i < 4 * kRadixBins; i += 256) h[i] = 0;
-  __syncthreads();
-  const uint32_t P = stage_count(st);
-  const uint32_t* keys = st.keys[0];
-  const uint32_t stride = gridDim.x * 256u;
-  for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < P; i += stride) {
-    const uint32_t k = keys[i];
-    for (int d = 0; d < n_digits; ++d) atomicAdd(&h[d * kRadixBins + digit_of(k, st, d)], 1u);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ws.plan[st.nparts_word] = (U + kSortPart - 1) / kSortPart;
+    ws.plan[kPlanSrc + st.slot0] = 0;
   }
-  __syncthreads();
-  block_hist_flush(h, ws.hist + st.slot0 * kRadixBins, n_digits);
-  const uint32_t nparts = ws.plan[st.nparts_word];
-  for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < nparts * (uint32_t)kRadixBins; i += stride)
-    ws.lookback[i] = 0;
 }
 
-__global__ void __launch_bounds__(kRadixBins) k_plan(Ws ws, Stage st, int n_digits) {
-  __shared__ uint32_t wsum[kRadixBins / 32];
+// Phase 1: digit histogram of every partition, stored digit-major.
+__global__ void __launch_bounds__(256) k_count(Ws ws, Stage st, int digit) {
+  __shared__ uint32_t h[kRadixBins];
+  const int slot = st.slot0 + digit;
+  const uint32_t* __restrict__ kin = src_keys(st, (int)ws.plan[kPlanSrc + slot]);
   const uint32_t P = stage_count(st);
-  const int d = threadIdx.x, lane = d & 31, wid = d >> 5;
-  int src = 0, nact = 0;
-  for (int p = 0; p < 4; ++p) {
-    const int slot = st.slot0 + p;
-    const uint32_t c = p < n_digits ? ws.hist[slot * kRadixBins + d] : 0u;
-    const int one_bin = __syncthreads_or(c == P);
-    const bool active = p < n_digits && P > 0 && !one_bin;
-    uint32_t x = c;
+  const uint32_t nparts = ws.plan[st.nparts_word];
+  const int shift = (int)((st.shifts >> (8 * digit)) & 0xffu);
+  const uint32_t width = (st.widths >> (8 * digit)) & 0xffu;
+  const uint32_t dmask = (1u << width) - 1u, nbins = 1u << width;
+  const int tid = threadIdx.x;
+  for (uint32_t part = blockIdx.x; part < nparts; part += gridDim.x) {
+    for (uint32_t d = tid; d < nbins; d += 256) h[d] = 0;
+    __syncthreads();
+    const uint32_t base = part * (uint32_t)kSortPart;
+#pragma unroll
+    for (int r = 0; r < kSortPart / 1024; ++r) {    // 16 keys per thread, 16-byte loads
+      const uint32_t i = base + 4u * (r * 256u + tid);
+      if (i + 3 < P) {
+        const uint4 v = reinterpret_cast<const uint4*>(kin)[i >> 2];
+        atomicAdd(&h[(v.x >> shift) & dmask], 1u);
+        atomicAdd(&h[(v.y >> shift) & dmask], 1u);
+        atomicAdd(&h[(v.z >> shift) & dmask], 1u);
+        atomicAdd(&h[(v.w >> shift) & dmask], 1u);
+      } else {
+        for (uint32_t j = 0; j < 4; ++j)
+          if (i + j < P) atomicAdd(&h[(kin[i + j] >> shift) & dmask], 1u);
+      }
+    }
+    __syncthreads();
+    for (uint32_t d = tid; d < nbins; d += 256) ws.counts[(size_t)d * ws.max_parts + part] = h[d];
+    __syncthreads();
+  }
+}
+
+// Phase 2: one CTA per digit value (grid = 2^width): exclusive scan of its partition counts
+// in place and its total; the last CTA to finish writes the digit bases and the pass plan.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_scan(Ws ws, Stage st, int digit, int last) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  __shared__ uint32_t s_carry;
+  __shared__ int s_last;
+  const int slot = st.slot0 + digit;
+  const uint32_t nparts = ws.plan[st.nparts_word];
+  const uint32_t nbins = 1u << ((st.widths >> (8 * digit)) & 0xffu);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint32_t* col = ws.counts + (size_t)blockIdx.x * ws.max_parts;
+  uint32_t* tot = ws.hist + slot * kRadixBins;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t b0 = 0; b0 < nparts; b0 += 4u * kScanThreads) {
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t i = b0 + 4u * tid + j;
+      v[j] = i < nparts ? col[i] : 0u;
+      s += v[j];
+    }
+    uint32_t x = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) wsum[wid] = x;
+    if (lane == 31) warp_tot[wid] = x;
     __syncthreads();
-    uint32_t pre = 0;
-    for (int w = 0; w < wid; ++w) pre += wsum[w];
-    ws.hist[slot * kRadixBins + d] = pre + x - c;
+    uint32_t run = s_carry, all = 0;
+    for (int q = 0; q < kScanThreads / 32; ++q) {
+      if (q < wid) run += warp_tot[q];
+      all += warp_tot[q];
+    }
+    run += x - s;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t i = b0 + 4u * tid + j;
+      if (i < nparts) col[i] = run;
+      run += v[j];
+    }
     __syncthreads();
-    if (d == 0) {
-      ws.plan[kPlanActive + slot] = active ? 1u : 0u;
-      ws.plan[kPlanSrc + slot] = (uint32_t)src;
-      ws.plan[kPlanLb + slot] = (uint32_t)(nact & 1);
-    }
-    if (active) {
-      src ^= 1;
-      ++nact;
-    }
+    if (tid == 0) s_carry += all;
+    __syncthreads();
   }
-  if (d == 0) ws.plan[st.final_word] = (uint32_t)src;
+  if (tid == 0) {
+    tot[blockIdx.x] = s_carry;
+    __threadfence();
+    s_last = atomicAdd(&ws.plan[kPlanCounter + slot], 1u) == nbins - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // the last CTA: totals -> exclusive digit bases; the plan of this pass
+  __threadfence();
+  const uint32_t P = stage_count(st);
+  const uint32_t t = (uint32_t)tid < nbins ? reinterpret_cast<volatile uint32_t*>(tot)[tid] : 0u;
+  const int one_bin = __syncthreads_or(t == P);
+  uint32_t x = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int q = 0; q < wid; ++q) pre += warp_tot[q];
+  if ((uint32_t)tid < nbins) tot[tid] = pre + x - t;
+  if (tid == 0) {
+    const uint32_t active = (P > 0 && !one_bin) ? 1u : 0u;
+    const uint32_t src = ws.plan[kPlanSrc + slot];
+    ws.plan[kPlanActive + slot] = active;
+    if (last) ws.plan[st.final_word] = src ^ active;
+    else ws.plan[kPlanSrc + slot + 1] = src ^ active;
+  }
 }
 
 constexpr int kSortWarps = kSortThreads / 32;
@@ -162,10 +190,9 @@ struct SortSmem {
   uint32_t local_start[kRadixBins];
   uint32_t gbase[kRadixBins];
   uint32_t wsum[kSortWarps];
-  uint32_t part;
 };
 
-// One digit pass. kSortThreads threads, kSortKeysPerThread keys each: warp w ranks the
+// Phase 3. kSortThreads threads, kSortKeysPerThread keys each: warp w ranks the
 // 32 * kSortKeysPerThread consecutive keys starting at w * 32 * kSortKeysPerThread, round by
 // round, so (warp, round, lane) order is input order and the ranking is stable. Thread d
 // then owns digit value d for the partition-level steps.
@@ -175,29 +202,25 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
   const int slot = st.slot0 + digit;
   if (!ws.plan[kPlanActive + slot]) return;
   const int src = (int)ws.plan[kPlanSrc + slot];
-  const int lbt = (int)ws.plan[kPlanLb + slot];
   const uint32_t* __restrict__ kin = src ? st.keys[1] : st.keys[0];
   const uint32_t* __restrict__ vin = src ? st.vals[1] : st.vals[0];
   uint32_t* __restrict__ kout = src ? st.keys[0] : st.keys[1];
   uint32_t* __restrict__ vout = src ? st.vals[0] : st.vals[1];
   const uint32_t P = stage_count(st);
   const uint32_t nparts = ws.plan[st.nparts_word];
-  unsigned long long* lb = ws.lookback + (size_t)lbt * ws.max_parts * kRadixBins;
-  unsigned long long* lb_next = ws.lookback + (size_t)(lbt ^ 1) * ws.max_parts * kRadixBins;
   const uint32_t* goff = ws.hist + slot * kRadixBins;
   const int shift = (int)((st.shifts >> (8 * digit)) & 0xffu);
-  const uint32_t dmask = (1u << ((st.widths >> (8 * digit)) & 0xffu)) - 1u;
-  const bool live_d = (uint32_t)threadIdx.x <= dmask;   // digit values this pass can take
+  const int width = (int)((st.widths >> (8 * digit)) & 0xffu);
+  const uint32_t dmask = (1u << width) - 1u;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int d = tid;   // digit value owned in the partition steps
 
-  for (;;) {
-    if (tid == 0) sm.part = atomicAdd(&ws.plan[kPlanCounter + slot], 1u);
+  for (uint32_t part = blockIdx.x; part < nparts; part += gridDim.x) {
     for (int i = tid; i < kSortWarps * kRadixBins; i += kSortThreads) (&sm.whist[0][0])[i] = 0;
+    // this partition's global offset of every digit value (the scan of phase 2)
+    if ((uint32_t)d <= dmask) sm.gbase[d] = goff[d] + ws.counts[(size_t)d * ws.max_parts + part];
     __syncthreads();
-    const uint32_t part = sm.part;
-    if (part >= nparts) break;
     const uint32_t base = part * (uint32_t)kSortPart;
     const uint32_t wbase = base + wid * (32 * kSortKeysPerThread) + lane;
 
@@ -214,8 +237,13 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
     for (int r = 0; r < kSortKeysPerThread; ++r) {
       const bool valid = wbase + r * 32 < P;
       const uint32_t dg = (k[r] >> shift) & dmask;
-      // lanes holding the same digit (a lane past the end matches only itself)
-      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? dg : 0x10000u | (uint32_t)lane);
+      // lanes holding the same digit, one ballot per digit bit (valid lanes only)
+      uint32_t peers = __ballot_sync(0xffffffffu, valid);
+      for (int b = 0; b < width; ++b) {
+        const bool bit = (dg >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+      }
       uint32_t before = 0;
       if (valid) before = sm.whist[wid][dg];
       __syncwarp();
@@ -232,17 +260,10 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
       sm.whist[w][d] = total;
       total += c;
     }
-    // publish the aggregate (or the inclusive prefix for the first partition); values the
-    // digit cannot take have no run and no look-back
-    if (live_d) {
-      if (part == 0) st_relaxed(lb + d, kFlagInc | total);
-      else st_relaxed(lb + (size_t)part * kRadixBins + d, kFlagAgg | total);
-    }
-    lb_next[(size_t)part * kRadixBins + d] = 0;
     uint32_t x = total;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) sm.wsum[wid] = x;
@@ -253,7 +274,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
       sm.local_start[d] = pre + x - total;
     }
     __syncthreads();
-    // reorder the partition in shared memory (needs no global offset)
+    // reorder the partition in shared memory
 #pragma unroll
     for (int r = 0; r < kSortKeysPerThread; ++r) {
       if (wbase + r * 32 < P) {
@@ -263,44 +284,6 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
         sm.vals[pos] = v[r];
       }
     }
-    // windowed look-back: read up to kWindow predecessors at once, nearest first; sum their
-    // aggregates up to the nearest inclusive prefix; re-poll from the first one not ready
-    unsigned long long excl = 0;
-    if (part > 0 && live_d) {
-      int q = (int)part - 1;
-      uint32_t spins = 0;
-      bool done = false;
-      while (!done && q >= 0) {
-        unsigned long long wv[kWindow];
-#pragma unroll
-        for (int i = 0; i < kWindow; ++i)
-          wv[i] = (q - i >= 0) ? ld_relaxed(lb + (size_t)(q - i) * kRadixBins + d) : kFlagInc;
-        int consumed = 0;
-        bool stalled = false;
-#pragma unroll
-        for (int i = 0; i < kWindow; ++i) {
-          if (done || stalled) continue;
-          const unsigned long long flag = wv[i] & ~kValMask;
-          if (flag == 0) {
-            stalled = true;
-            continue;
-          }
-          if (q - i >= 0) excl += wv[i] & kValMask;
-          ++consumed;
-          if (flag == kFlagInc) done = true;
-        }
-        q -= consumed;
-        if (stalled && !done) {
-          if (++spins > kSpinLimit) {
-            set_status(ws.status, FLOD_DEV_TIMEOUT);
-            break;
-          }
-          if (spins > 8) __nanosleep(64);
-        }
-      }
-      st_relaxed(lb + (size_t)part * kRadixBins + d, kFlagInc | ((excl + total) & kValMask));
-    }
-    sm.gbase[d] = goff[d] + (uint32_t)excl;
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortPart, P - base);
     for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
@@ -364,30 +347,30 @@ static Stage pair_stage(const Ws& ws, int n_digits, int tile_bits) {
   return s;
 }
 
-// Stage "units": depth digits (32 bits -> 4 passes of 8 bits).
-cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st) {
-  const Stage s = unit_stage(ws);
-  const int n_digits = 4;
-  cudaError_t e = cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * 4 * kRadixBins, st);
-  if (e != cudaSuccess) return e;
-  k_unit_keys<<<resident_small, 256, 0, st>>>(ws, s, n_digits);
-  k_plan<<<1, kRadixBins, 0, st>>>(ws, s, n_digits);
-  for (int p = 0; p < n_digits; ++p)
+static cudaError_t run_passes(const Ws& ws, const Stage& s, int n_digits, int resident_small,
+                              int resident_sort, cudaStream_t st) {
+  for (int p = 0; p < n_digits; ++p) {
+    const uint32_t nbins = 1u << ((s.widths >> (8 * p)) & 0xffu);
+    k_count<<<resident_small, 256, 0, st>>>(ws, s, p);
+    k_scan<<<nbins, kScanThreads, 0, st>>>(ws, s, p, p + 1 == n_digits ? 1 : 0);
     k_pass<<<resident_sort, kSortThreads, sizeof(SortSmem), st>>>(ws, s, p);
+  }
   return cudaGetLastError();
 }
 
-// Stage "pairs": tile digits (n_digits passes over the emitted pairs).
+// Stage "units": depth digits (32 bits -> 4 passes of 8 bits).
+cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st) {
+  const Stage s = unit_stage(ws);
+  k_unit_keys<<<resident_small, 256, 0, st>>>(ws, s);
+  return run_passes(ws, s, 4, resident_small, resident_sort, st);
+}
+
+// Stage "pairs": tile digits (n_digits passes over the emitted pairs). The emission's scan
+// kernel has reset the stage's plan words.
 cudaError_t launch_pair_sort(const Ws& ws, int n_digits, int tile_bits, int resident_small,
                              int resident_sort, cudaStream_t st) {
-  const Stage s = pair_stage(ws, n_digits, tile_bits);
-  cudaError_t e = cudaMemsetAsync(ws.hist + 4 * kRadixBins, 0, sizeof(uint32_t) * 4 * kRadixBins, st);
-  if (e != cudaSuccess) return e;
-  k_hist<<<resident_small, 256, 0, st>>>(ws, s, n_digits);
-  k_plan<<<1, kRadixBins, 0, st>>>(ws, s, n_digits);
-  for (int p = 0; p < n_digits; ++p)
-    k_pass<<<resident_sort, kSortThreads, sizeof(SortSmem), st>>>(ws, s, p);
-  return cudaGetLastError();
+  return run_passes(ws, pair_stage(ws, n_digits, tile_bits), n_digits, resident_small,
+                    resident_sort, st);
 }
 
 }  // namespace flod

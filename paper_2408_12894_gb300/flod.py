@@ -71,7 +71,7 @@ class WsLayout(C.Structure):
                                           "block_sums", "slices")] + \
                [("ukeys", C.c_size_t * 2), ("uvals", C.c_size_t * 2),
                 ("keys", C.c_size_t * 2), ("vals", C.c_size_t * 2)] + \
-               [(n, C.c_size_t) for n in ("hist", "lookback", "ranges", "grad2d", "queue")] + \
+               [(n, C.c_size_t) for n in ("hist", "counts", "ranges", "grad2d", "queue")] + \
                [(n, C.c_uint64) for n in ("units", "tiles", "pixels", "pair_capacity")]
 
 
