@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
   const int d = tid;   // digit value owned in the partition steps
 
   for (uint32_t part = blockIdx.x; part < nparts; part += gridDim.x) {
-    for (int i = tid; i < kSortWarps * kRadixBins; i += kSortThreads) (&sm.whist[0][0])[i] = 0;
+    for (int i = tid; i < (kSortWarps << width); i += kSortThreads)   // the bins this digit has
+      sm.whist[i >> width][i & dmask] = 0;
     // this partition's global offset of every digit value (the scan of phase 2)
     if ((uint32_t)d <= dmask) sm.gbase[d] = goff[d] + ws.counts[(size_t)d * ws.max_parts + part];
     __syncthreads();
@@ -254,11 +255,13 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
     __syncthreads();
     // digit d: exclusive prefix over warps and the partition's digit total
     uint32_t total = 0;
+    if ((uint32_t)d <= dmask) {
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-      const uint32_t c = sm.whist[w][d];
-      sm.whist[w][d] = total;
-      total += c;
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = sm.whist[w][d];
+        sm.whist[w][d] = total;
+        total += c;
+      }
     }
     uint32_t x = total;
 #pragma unroll
