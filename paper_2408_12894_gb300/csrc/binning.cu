@@ -11,6 +11,9 @@
 
 namespace flod {
 
+constexpr uint32_t kLightPairs = 16 * kEmitSlice;   // blocks up to this many pairs: k_emit_light
+constexpr uint32_t kBigUnit = 32;                    // units above this many tiles: warp-wide
+
 // Pair count of every 1024 slots of the depth-sorted unit order.
 __global__ void __launch_bounds__(256) k_block_sums(Ws ws) {
   __shared__ uint32_t red[8];
@@ -46,7 +49,8 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
   for (uint32_t base = 0; base < nblocks; base += 1024) {
     const uint32_t i = base + tid;
     unsigned long long v = i < nblocks ? ws.block_sums[i] : 0ull;
-    const uint32_t sl = (uint32_t)((v + kEmitSlice - 1) / kEmitSlice);   // emission slices
+    // emission slices, for the blocks the light emission leaves out
+    const uint32_t sl = v > kLightPairs ? (uint32_t)((v + kEmitSlice - 1) / kEmitSlice) : 0u;
     unsigned long long x = v;
     uint32_t xs = sl;
 #pragma unroll
@@ -415,6 +419,134 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
   }
 }
 
+// Key emission of a light block (at most kLightPairs pairs), one CTA per 1024-slot block:
+// the block's pair counts are scanned in shared memory; each thread writes the tiles of its
+// four units one after the other, row by row from their tile records; units of more than
+// kBigUnit tiles are written by their whole warp, row by row with one lane per tile. Heavier
+// blocks are left to the sliced k_emit.
+template <int MAXV>
+__device__ __forceinline__ bool rec_row_tiles(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
+                                              const uint4& rc, const UnitTiles& t, uint32_t r,
+                                              uint32_t row_base, uint32_t tiles_x, uint32_t& n,
+                                              uint32_t& tile0) {
+  const uint32_t mode = rc.y >> 16;
+  const uint32_t ty = (rc.x >> 16) + r;
+  if (mode == kRecCompute) {
+    int cx0, cx1;
+    if (!unit_row(t, t.ty0 + (int)r, cx0, cx1)) return false;
+    n = (uint32_t)(cx1 - cx0 + 1);
+    tile0 = row_base + ty * tiles_x + (uint32_t)cx0;
+    return true;
+  }
+  uint32_t off = 0, c = rc.z;
+  if (mode == kRecTable) rec_row(rc, (int)r, off, c);
+  n = c;
+  tile0 = row_base + ty * tiles_x + (rc.x & 0xffffu) + off;
+  return c > 0;
+}
+
+template <int MAXV>
+__global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  __shared__ uint32_t warp_tot[8];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]] + (size_t)blockIdx.x * kScanBlock;
+  const uint4 un = reinterpret_cast<const uint4*>(order)[tid];
+  const uint32_t unit[4] = {un.x, un.y, un.z, un.w};
+  uint32_t cnt[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cnt[j] = ws.tiles_touched[unit[j]];
+  uint32_t total;
+  uint32_t run = block_excl_sum(cnt[0] + cnt[1] + cnt[2] + cnt[3], warp_tot, total);
+  if (total == 0 || total > kLightPairs) return;   // nothing, or the sliced emission's
+  const unsigned long long base = ws.block_sums[blockIdx.x];
+  const unsigned long long cap = ws.pair_capacity;
+  uint32_t* keys = ws.keys[0];
+  uint32_t* vals = ws.vals[0];
+  uint32_t pre[4], big = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    pre[j] = run;
+    run += cnt[j];
+    if (cnt[j] > kBigUnit) big |= 1u << j;
+  }
+  // 1. my units, one after the other
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!cnt[j] || (big >> j & 1u)) continue;
+    const uint32_t u = unit[j];
+    const uint4 rc = ws.trec[u];
+    const ViewP& V = b.views[view_of_unit(b, u)];
+    uint32_t row_base = V.tile_off, tiles_x = V.tiles_x;
+    UnitTiles t;
+    if ((rc.y >> 16) == kRecCompute) slot_tiles(b, ws, u, t, row_base, tiles_x);
+    unsigned long long p = base + pre[j];
+    const unsigned long long end = p + cnt[j];
+    const uint32_t nrows = rc.y & 0xffffu;
+    for (uint32_t r = 0; r < nrows && p < end; ++r) {
+      uint32_t n, tile0;
+      if (!rec_row_tiles(b, ws, u, rc, t, r, row_base, tiles_x, n, tile0)) continue;
+      for (uint32_t c = 0; c < n && p < end; ++c, ++p) {
+        if (p < cap) {
+          keys[p] = tile0 + c;
+          vals[p] = u;
+        }
+      }
+    }
+    if (p != end) set_status(ws.status, FLOD_DEV_TILESET);
+  }
+  // 2. big units of my warp, by the whole warp: rows in chunks of 32 (one per lane), then
+  //    each row's tiles one per lane
+  uint32_t todo = __ballot_sync(0xffffffffu, big != 0);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    const uint32_t my_j = big ? (uint32_t)(__ffs(big) - 1) : 0u;
+    const uint32_t j = __shfl_sync(0xffffffffu, my_j, src);
+    uint32_t su = unit[0], sp = pre[0], sc = cnt[0];
+#pragma unroll
+    for (int q = 1; q < 4; ++q)
+      if ((uint32_t)q == my_j) { su = unit[q]; sp = pre[q]; sc = cnt[q]; }
+    const uint32_t u = __shfl_sync(0xffffffffu, su, src);
+    const unsigned long long p0 = base + __shfl_sync(0xffffffffu, sp, src);
+    const uint32_t n_all = __shfl_sync(0xffffffffu, sc, src);
+    if (lane == src) big &= ~(1u << j);
+    todo = __ballot_sync(0xffffffffu, big != 0);
+    const uint4 rc = ws.trec[u];
+    const ViewP& V = b.views[view_of_unit(b, u)];
+    uint32_t row_base = V.tile_off, tiles_x = V.tiles_x;
+    UnitTiles t;
+    if ((rc.y >> 16) == kRecCompute) slot_tiles(b, ws, u, t, row_base, tiles_x);
+    const uint32_t nrows = rc.y & 0xffffu;
+    uint32_t done = 0;
+    for (uint32_t r0 = 0; r0 < nrows; r0 += 32) {
+      const uint32_t r = r0 + lane;
+      uint32_t rn = 0, rt0 = 0;
+      if (r < nrows && !rec_row_tiles(b, ws, u, rc, t, r, row_base, tiles_x, rn, rt0)) rn = 0;
+      uint32_t incl = rn;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t rpos = done + incl - rn;
+      const uint32_t rows_here = min(32u, nrows - r0);
+      for (uint32_t i = 0; i < rows_here; ++i) {
+        const uint32_t ni = __shfl_sync(0xffffffffu, rn, i);
+        const uint32_t ti = __shfl_sync(0xffffffffu, rt0, i);
+        const uint32_t pi = __shfl_sync(0xffffffffu, rpos, i);
+        for (uint32_t c = lane; c < ni && pi + c < n_all; c += 32) {
+          const unsigned long long p = p0 + pi + c;
+          if (p < cap) {
+            keys[p] = ti + c;
+            vals[p] = u;
+          }
+        }
+      }
+      done += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0 && done != n_all) set_status(ws.status, FLOD_DEV_TILESET);
+  }
+}
+
 // Tile ranges from the sorted tile keys: four consecutive keys per thread (one 16-byte load),
 // a range starts or ends where a key differs from its neighbour.
 __global__ void __launch_bounds__(256) k_ranges(Ws ws, uint32_t n_tiles) {
@@ -494,7 +626,10 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
     k_block_sums<<<nblocks, 256, 0, st>>>(ws);
   }
   k_scan_blocks<<<1, 1024, 0, st>>>(ws, nblocks, d_pair_count);
-  if (nblocks) k_emit<MAXV><<<resident_small, 256, 0, st>>>(b, ws, nblocks);
+  if (nblocks) {
+    k_emit_light<MAXV><<<nblocks, 256, 0, st>>>(b, ws);
+    k_emit<MAXV><<<resident_small, 256, 0, st>>>(b, ws, nblocks);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_pair_sort(ws, n_passes, tile_bits, resident_small, resident_sort, st)) !=
       cudaSuccess)
