@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
       }
       __syncthreads();
       if (!done) {
+#pragma unroll 4
         for (int k = 0; k < cnt; ++k) {
           const float4 mq = s_xq[k];
           const float4 cs = s_cs[k];
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         s_rgb[k] = ws.rgb[id];
       }
       __syncthreads();
+#pragma unroll 4
       for (int k = cnt - 1; k >= 0; --k) {
         const uint32_t pos = bstart - rg.x + (uint32_t)k + 1u;
         const float2 m = s_xy[k];
