@@ -18,9 +18,14 @@ constexpr uint32_t kBigUnit = 32;                    // units above this many ti
 __global__ void __launch_bounds__(256) k_block_sums(Ws ws) {
   __shared__ uint32_t red[8];
   const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
-  const uint4 o = reinterpret_cast<const uint4*>(order)[blockIdx.x * 256u + threadIdx.x];
-  uint32_t s = ws.tiles_touched[o.x] + ws.tiles_touched[o.y] + ws.tiles_touched[o.z] +
-               ws.tiles_touched[o.w];
+  const uint32_t nvis = visible_units(ws);
+  const uint32_t s0 = blockIdx.x * 1024u + 4u * threadIdx.x;
+  uint32_t s = 0;
+  if (s0 < nvis) {   // slots past the visible units hold no unit
+    const uint4 o = reinterpret_cast<const uint4*>(order)[blockIdx.x * 256u + threadIdx.x];
+    s = ws.tiles_touched[o.x] + (s0 + 1 < nvis ? ws.tiles_touched[o.y] : 0u) +
+        (s0 + 2 < nvis ? ws.tiles_touched[o.z] : 0u) + (s0 + 3 < nvis ? ws.tiles_touched[o.w] : 0u);
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -188,6 +193,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
   const uint32_t n_slices = ws.plan[kPlanSlices];
   const unsigned long long cap = ws.pair_capacity;
   const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
+  const uint32_t nvis = visible_units(ws);
   uint32_t* keys = ws.keys[0];
   uint32_t* vals = ws.vals[0];
   for (uint32_t it = 0;; ++it) {
@@ -210,13 +216,15 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
     __syncthreads();
     const uint32_t blk = s_blkmap[it & 255u];
     const uint32_t r0 = (w - ws.slices[blk]) * (uint32_t)kEmitSlice;
-    // 1. slot start positions
-    const uint4 un = reinterpret_cast<const uint4*>(order)[blk * 256u + tid];
+    // 1. slot start positions (slots past the visible units hold no unit)
+    const uint32_t s0 = blk * 1024u + 4u * tid;
+    uint4 un = make_uint4(0u, 0u, 0u, 0u);
+    if (s0 < nvis) un = reinterpret_cast<const uint4*>(order)[blk * 256u + tid];
     const uint32_t unit[4] = {un.x, un.y, un.z, un.w};
     uint32_t cnt[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      cnt[j] = ws.tiles_touched[unit[j]];
+      cnt[j] = s0 + j < nvis ? ws.tiles_touched[unit[j]] : 0u;
       s_unit[4 * tid + j] = unit[j];
     }
     uint32_t total;
@@ -450,11 +458,14 @@ __global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batc
   __shared__ uint32_t warp_tot[8];
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]] + (size_t)blockIdx.x * kScanBlock;
-  const uint4 un = reinterpret_cast<const uint4*>(order)[tid];
+  const uint32_t nvis = visible_units(ws);
+  const uint32_t s0 = blockIdx.x * kScanBlock + 4u * tid;
+  uint4 un = make_uint4(0u, 0u, 0u, 0u);
+  if (s0 < nvis) un = reinterpret_cast<const uint4*>(order)[tid];
   const uint32_t unit[4] = {un.x, un.y, un.z, un.w};
   uint32_t cnt[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) cnt[j] = ws.tiles_touched[unit[j]];
+  for (int j = 0; j < 4; ++j) cnt[j] = s0 + j < nvis ? ws.tiles_touched[unit[j]] : 0u;
   uint32_t total;
   uint32_t run = block_excl_sum(cnt[0] + cnt[1] + cnt[2] + cnt[3], warp_tot, total);
   if (total == 0 || total > kLightPairs) return;   // nothing, or the sliced emission's

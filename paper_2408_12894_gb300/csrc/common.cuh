@@ -102,6 +102,7 @@ struct Ws {
 constexpr int kPlanPasses = 8;       // slots 0-3: depth digits over units; 4-7: tile digits over pairs
 constexpr int kPlanActive = 0;       // plan[kPlanActive + p] = 1 if pass p moves keys
 constexpr int kPlanSrc = 8;          // plan[kPlanSrc + p] = source buffer of pass p
+constexpr int kPlanNVis = 16;        // uint64 at plan[16]: units with tiles (the sorted unit slots)
 constexpr int kPlanCounter = 24;     // plan[kPlanCounter + p] = finished digit-scan CTAs of pass p
 constexpr int kPlanNParts = 40;      // number of partitions
 constexpr int kPlanQueue = 41;       // render work-queue ticket counter (x2: fwd, bwd)
@@ -295,6 +296,11 @@ __device__ __forceinline__ float splat_qmin(float o) {
 __device__ __forceinline__ float splat_alpha(float qs, float o, float& g) {
   g = ex2_approx(qs);
   return fminf(kAlphaMax, __fmul_rn(o, g));
+}
+
+// Number of depth-sorted unit slots (units with at least one tile).
+__device__ __forceinline__ uint32_t visible_units(const Ws& ws) {
+  return (uint32_t)*reinterpret_cast<const unsigned long long*>(ws.plan + kPlanNVis);
 }
 
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {

@@ -152,6 +152,10 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batc
   int si = 0;
   uint32_t gi = 0;
   bool ok = in_range && unit_source(b, V, u - V.unit_off, si, gi);
+  if (!ok) {   // padding, or past the view's selection: nothing reads it but its tile count
+    if (in_range) ws.tiles_touched[u] = 0;
+    return;
+  }
   float2 xy = make_float2(0.f, 0.f);
   float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 rgb = make_float4(0.f, 0.f, 0.f, 0.f);

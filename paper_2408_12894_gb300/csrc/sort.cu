@@ -50,19 +50,84 @@ __device__ __forceinline__ const uint32_t* src_keys(const Stage& s, int src) {
   return src ? s.keys[1] : s.keys[0];
 }
 
-// Stage "units": key = float bits of the view-space depth of a unit with tiles (positive, so
-// the bits order like the values), all ones otherwise; value = unit index. Also resets the
-// stage's plan words.
-__global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st) {
-  const uint32_t U = st.fixed_count;
-  for (uint32_t u = blockIdx.x * 256u + threadIdx.x; u < U; u += gridDim.x * 256u) {
-    st.keys[0][u] = ws.tiles_touched[u] ? __float_as_uint(ws.depth[u]) : 0xffffffffu;
-    st.vals[0][u] = u;
+// Stage "units": only units with tiles take part. Per 1024 units their count (k_vis_count),
+// an exclusive scan of those counts with the total (k_vis_scan, one CTA; the total is the
+// stage's element count), then the keys in unit order (k_unit_keys): key = float bits of the
+// view-space depth (positive, so the bits order like the values), value = unit index.
+__global__ void __launch_bounds__(256) k_vis_count(Ws ws) {
+  __shared__ uint32_t red[8];
+  const uint4 t = reinterpret_cast<const uint4*>(ws.tiles_touched)[blockIdx.x * 256u + threadIdx.x];
+  uint32_t s = (t.x != 0) + (t.y != 0) + (t.z != 0) + (t.w != 0);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) c += red[w];
+    ws.slices[blockIdx.x] = c;
   }
-  if (blockIdx.x == 0 && threadIdx.x < 4) ws.plan[kPlanCounter + st.slot0 + threadIdx.x] = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ws.plan[st.nparts_word] = (U + kSortPart - 1) / kSortPart;
+}
+
+__global__ void __launch_bounds__(1024) k_vis_scan(Ws ws, Stage st, uint32_t nblocks) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t b0 = 0; b0 < nblocks; b0 += 1024) {
+    const uint32_t i = b0 + tid;
+    const uint32_t v = i < nblocks ? ws.slices[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    uint32_t pre = s_carry, all = 0;
+    for (int q = 0; q < 32; ++q) {
+      if (q < wid) pre += warp_tot[q];
+      all += warp_tot[q];
+    }
+    if (i < nblocks) ws.slices[i] = pre + x - v;
+    __syncthreads();
+    if (tid == 0) s_carry += all;
+    __syncthreads();
+  }
+  if (tid < 4) ws.plan[kPlanCounter + st.slot0 + tid] = 0;
+  if (tid == 0) {
+    *reinterpret_cast<unsigned long long*>(ws.plan + kPlanNVis) = s_carry;
+    ws.plan[st.nparts_word] = (s_carry + kSortPart - 1) / kSortPart;
     ws.plan[kPlanSrc + st.slot0] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st) {
+  __shared__ uint32_t red[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t u0 = blockIdx.x * 1024u + 4u * tid;
+  const uint4 t = reinterpret_cast<const uint4*>(ws.tiles_touched)[blockIdx.x * 256u + tid];
+  const uint32_t vis[4] = {t.x != 0, t.y != 0, t.z != 0, t.w != 0};
+  const uint32_t s = vis[0] + vis[1] + vis[2] + vis[3];
+  uint32_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) red[wid] = x;
+  __syncthreads();
+  uint32_t pos = ws.slices[blockIdx.x] + x - s;
+  for (int q = 0; q < wid; ++q) pos += red[q];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!vis[j]) continue;
+    st.keys[0][pos] = __float_as_uint(ws.depth[u0 + j]);
+    st.vals[0][pos] = u0 + j;
+    ++pos;
   }
 }
 
@@ -315,8 +380,8 @@ static Stage unit_stage(const Ws& ws) {
   s.keys[1] = ws.ukeys[1];
   s.vals[0] = ws.uvals[0];
   s.vals[1] = ws.uvals[1];
-  s.count = nullptr;
-  s.fixed_count = ws.units;
+  s.count = reinterpret_cast<const unsigned long long*>(ws.plan + kPlanNVis);
+  s.fixed_count = 0;
   s.cap = ws.units;
   s.slot0 = 0;
   s.nparts_word = kPlanNPartsUnits;
@@ -361,10 +426,13 @@ static cudaError_t run_passes(const Ws& ws, const Stage& s, int n_digits, int re
   return cudaGetLastError();
 }
 
-// Stage "units": depth digits (32 bits -> 4 passes of 8 bits).
+// Stage "units": depth digits (32 bits -> 4 passes of 8 bits) of the units with tiles.
 cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st) {
   const Stage s = unit_stage(ws);
-  k_unit_keys<<<resident_small, 256, 0, st>>>(ws, s);
+  const uint32_t nblocks = ws.units / kScanBlock;
+  k_vis_count<<<nblocks, 256, 0, st>>>(ws);
+  k_vis_scan<<<1, 1024, 0, st>>>(ws, s, nblocks);
+  k_unit_keys<<<nblocks, 256, 0, st>>>(ws, s);
   return run_passes(ws, s, 4, resident_small, resident_sort, st);
 }
 
