@@ -103,6 +103,8 @@ constexpr int kPlanPasses = 8;       // slots 0-3: depth digits over units; 4-7:
 constexpr int kPlanActive = 0;       // plan[kPlanActive + p] = 1 if pass p moves keys
 constexpr int kPlanSrc = 8;          // plan[kPlanSrc + p] = source buffer of pass p
 constexpr int kPlanNVis = 16;        // uint64 at plan[16]: units with tiles (the sorted unit slots)
+constexpr int kPlanDepthMin = 18;    // smallest depth bits of those units
+constexpr int kPlanKeyBits = 20;     // significant bits of (depth bits - smallest)
 constexpr int kPlanCounter = 24;     // plan[kPlanCounter + p] = finished digit-scan CTAs of pass p
 constexpr int kPlanNParts = 40;      // number of partitions
 constexpr int kPlanQueue = 41;       // render work-queue ticket counter (x2: fwd, bwd)

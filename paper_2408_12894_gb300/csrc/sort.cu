@@ -38,7 +38,13 @@ struct Stage {
   int final_word;                    // plan word receiving the result's buffer index
   uint32_t shifts;                   // digit d: bits [shift_d, shift_d + width_d) of the key,
   uint32_t widths;                   //   shift_d, width_d = byte d of shifts, widths
+  int keybits_word;                  // plan word with the keys' significant bits, or -1
 };
+
+// Whether digit d has any significant key bits (digits above them are skipped outright).
+__device__ __forceinline__ bool digit_live(const Ws& ws, const Stage& s, int d) {
+  return s.keybits_word < 0 || ((s.shifts >> (8 * d)) & 0xffu) < ws.plan[s.keybits_word];
+}
 
 __device__ __forceinline__ uint32_t stage_count(const Stage& s) {
   if (!s.count) return s.fixed_count;
@@ -50,35 +56,66 @@ __device__ __forceinline__ const uint32_t* src_keys(const Stage& s, int src) {
   return src ? s.keys[1] : s.keys[0];
 }
 
-// Stage "units": only units with tiles take part. Per 1024 units their count (k_vis_count),
-// an exclusive scan of those counts with the total (k_vis_scan, one CTA; the total is the
-// stage's element count), then the keys in unit order (k_unit_keys): key = float bits of the
-// view-space depth (positive, so the bits order like the values), value = unit index.
+// Stage "units": only units with tiles take part. Per 1024 units their count and the
+// smallest and largest depth bits (k_vis_count), an exclusive scan of those counts with the
+// total (k_vis_scan, one CTA; the total is the stage's element count), then the keys in unit
+// order (k_unit_keys): key = float bits of the view-space depth minus the smallest (depths
+// are positive, so the bits order like the values, and the difference keeps that order with
+// fewer significant bits: digits above them are skipped), value = unit index.
 __global__ void __launch_bounds__(256) k_vis_count(Ws ws) {
-  __shared__ uint32_t red[8];
-  const uint4 t = reinterpret_cast<const uint4*>(ws.tiles_touched)[blockIdx.x * 256u + threadIdx.x];
-  uint32_t s = (t.x != 0) + (t.y != 0) + (t.z != 0) + (t.w != 0);
+  __shared__ uint32_t red[3][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t i4 = blockIdx.x * 256u + threadIdx.x;
+  const uint4 t = reinterpret_cast<const uint4*>(ws.tiles_touched)[i4];
+  const uint4 d = reinterpret_cast<const uint4*>(ws.depth)[i4];   // the float bits
+  const uint32_t vis[4] = {t.x != 0, t.y != 0, t.z != 0, t.w != 0};
+  const uint32_t bits[4] = {d.x, d.y, d.z, d.w};
+  uint32_t s = 0, lo = 0xffffffffu, hi = 0u;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  for (int j = 0; j < 4; ++j) {
+    if (!vis[j]) continue;
+    ++s;
+    lo = min(lo, bits[j]);
+    hi = max(hi, bits[j]);
+  }
+  s = __reduce_add_sync(0xffffffffu, s);
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if (lane == 0) {
+    red[0][wid] = s;
+    red[1][wid] = lo;
+    red[2][wid] = hi;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t c = 0;
+    uint32_t c = 0, l = 0xffffffffu, h = 0u;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) c += red[w];
+    for (int w = 0; w < 8; ++w) {
+      c += red[0][w];
+      l = min(l, red[1][w]);
+      h = max(h, red[2][w]);
+    }
     ws.slices[blockIdx.x] = c;
+    ws.block_sums[blockIdx.x] = (unsigned long long)h << 32 | l;   // scratch until the scan
   }
 }
 
 __global__ void __launch_bounds__(1024) k_vis_scan(Ws ws, Stage st, uint32_t nblocks) {
-  __shared__ uint32_t warp_tot[32];
-  __shared__ uint32_t s_carry;
+  __shared__ uint32_t warp_tot[32], warp_lo[32], warp_hi[32];
+  __shared__ uint32_t s_carry, s_lo, s_hi;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) s_carry = 0;
+  if (tid == 0) {
+    s_carry = 0;
+    s_lo = 0xffffffffu;
+    s_hi = 0u;
+  }
   __syncthreads();
   for (uint32_t b0 = 0; b0 < nblocks; b0 += 1024) {
     const uint32_t i = b0 + tid;
     const uint32_t v = i < nblocks ? ws.slices[i] : 0u;
+    const unsigned long long mm = i < nblocks ? ws.block_sums[i] : 0xffffffffull;
+    const uint32_t lo = __reduce_min_sync(0xffffffffu, (uint32_t)mm);
+    const uint32_t hi = __reduce_max_sync(0xffffffffu, (uint32_t)(mm >> 32));
     uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -86,6 +123,10 @@ __global__ void __launch_bounds__(1024) k_vis_scan(Ws ws, Stage st, uint32_t nbl
       if (lane >= o) x += y;
     }
     if (lane == 31) warp_tot[wid] = x;
+    if (lane == 0) {
+      warp_lo[wid] = lo;
+      warp_hi[wid] = hi;
+    }
     __syncthreads();
     uint32_t pre = s_carry, all = 0;
     for (int q = 0; q < 32; ++q) {
@@ -94,11 +135,21 @@ __global__ void __launch_bounds__(1024) k_vis_scan(Ws ws, Stage st, uint32_t nbl
     }
     if (i < nblocks) ws.slices[i] = pre + x - v;
     __syncthreads();
-    if (tid == 0) s_carry += all;
+    if (tid == 0) {
+      s_carry += all;
+      for (int q = 0; q < 32; ++q) {
+        s_lo = min(s_lo, warp_lo[q]);
+        s_hi = max(s_hi, warp_hi[q]);
+      }
+    }
     __syncthreads();
   }
   if (tid < 4) ws.plan[kPlanCounter + st.slot0 + tid] = 0;
   if (tid == 0) {
+    // keys become depth bits minus the smallest: same order, fewer significant bits
+    const uint32_t span = (s_carry && s_hi >= s_lo) ? s_hi - s_lo : 0u;
+    ws.plan[kPlanDepthMin] = s_lo;
+    ws.plan[kPlanKeyBits] = span ? 32u - (uint32_t)__clz(span) : 0u;
     *reinterpret_cast<unsigned long long*>(ws.plan + kPlanNVis) = s_carry;
     ws.plan[st.nparts_word] = (s_carry + kSortPart - 1) / kSortPart;
     ws.plan[kPlanSrc + st.slot0] = 0;
@@ -122,10 +173,11 @@ __global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st) {
   __syncthreads();
   uint32_t pos = ws.slices[blockIdx.x] + x - s;
   for (int q = 0; q < wid; ++q) pos += red[q];
+  const uint32_t lo = ws.plan[kPlanDepthMin];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (!vis[j]) continue;
-    st.keys[0][pos] = __float_as_uint(ws.depth[u0 + j]);
+    st.keys[0][pos] = __float_as_uint(ws.depth[u0 + j]) - lo;
     st.vals[0][pos] = u0 + j;
     ++pos;
   }
@@ -134,6 +186,7 @@ __global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st) {
 // Phase 1: digit histogram of every partition, stored digit-major.
 __global__ void __launch_bounds__(256) k_count(Ws ws, Stage st, int digit) {
   __shared__ uint32_t h[kRadixBins];
+  if (!digit_live(ws, st, digit)) return;
   const int slot = st.slot0 + digit;
   const uint32_t* __restrict__ kin = src_keys(st, (int)ws.plan[kPlanSrc + slot]);
   const uint32_t P = stage_count(st);
@@ -179,6 +232,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Ws ws, Stage st, int digi
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   uint32_t* col = ws.counts + (size_t)blockIdx.x * ws.max_parts;
   uint32_t* tot = ws.hist + slot * kRadixBins;
+  if (!digit_live(ws, st, digit)) {   // all keys agree on this digit: the pass moves nothing
+    if (blockIdx.x == 0 && tid == 0) {
+      const uint32_t src = ws.plan[kPlanSrc + slot];
+      ws.plan[kPlanActive + slot] = 0;
+      if (last) ws.plan[st.final_word] = src;
+      else ws.plan[kPlanSrc + slot + 1] = src;
+    }
+    return;
+  }
   if (tid == 0) s_carry = 0;
   __syncthreads();
   for (uint32_t b0 = 0; b0 < nparts; b0 += 4u * kScanThreads) {
@@ -388,6 +450,7 @@ static Stage unit_stage(const Ws& ws) {
   s.final_word = kPlanFinalUnits;
   s.shifts = 0x18100800u;   // four 8-bit digits of the 32 depth bits
   s.widths = 0x08080808u;
+  s.keybits_word = kPlanKeyBits;
   return s;
 }
 
@@ -404,6 +467,7 @@ static Stage pair_stage(const Ws& ws, int n_digits, int tile_bits) {
   s.slot0 = 4;
   s.nparts_word = kPlanNParts;
   s.final_word = kPlanFinal;
+  s.keybits_word = -1;
   s.shifts = s.widths = 0;
   int shift = 0;
   for (int d = 0; d < n_digits; ++d) {
