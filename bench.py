@@ -416,10 +416,11 @@ def run_flod(a):
     achieved = d_flop / (d_ms * 1e-3) / 1e12
     n_tiles = int(rast.layout.tiles)
     n_passes = (max(1, math.ceil(math.log2(max(n_tiles, 2)))) + 8) // 9   # 9-bit tile digits
-    # preprocess 1; bin_sort: unit keys, 4 depth passes of 3 kernels (count, scan, scatter),
-    # block sums, scan, emit, n_passes tile passes of 3, ranges; render_fwd 1; blend_bwd 1;
-    # preprocess_bwd 1 (memsets not counted)
-    launches_per_step = 1 + (1 + 12 + 3 + 3 * n_passes + 1) + 1 + 1 + 1
+    # preprocess 1; bin_sort: visible counts, their scan, unit keys, 4 depth passes of 3
+    # kernels (count, scan, scatter; a pass above the keys' significant bits exits at once),
+    # block sums, scan, light and sliced emission, n_passes tile passes of 3, ranges;
+    # render_fwd 1; blend_bwd 1; preprocess_bwd 1 (memsets not counted)
+    launches_per_step = 1 + (3 + 12 + 4 + 3 * n_passes + 1) + 1 + 1 + 1
 
     if rank == 0:
         line = {
@@ -526,7 +527,7 @@ def selective_section(a):
             st.run()
         ms = timed(frame, max(a.steps, len(path)), 3)
         units = st.rast.layout.units
-        per_frame_bytes = [int(n * 236 + units * 52 + st.rast.pair_capacity * 24 + w * h * 20)
+        per_frame_bytes = [int(n * (236 + 84) + units * 4 + st.rast.pair_capacity * 16 + w * h * 20)
                            for n in sel]
         out["resolutions"][f"{w}x{h}"] = {
             "fps": 1e3 / ms, "ms_per_frame": ms,
