@@ -229,7 +229,12 @@ void fill_batch(Batch<MAXV>& B, const flod_gaussians* sets, int n_sets, const fl
   for (int c = 0; c < 3; ++c) B.cfg.bg[c] = cfg->bg[c];
   for (int s = 0; s < n_sets; ++s) {
     const flod_gaussians& g = sets[s];
-    B.sets[s] = SetP{g.means, g.quats, g.s_opt, g.opacity_logit, g.sh, g.n, g.sh_degree, g.s_min};
+    const bool al = !((reinterpret_cast<uintptr_t>(g.means) | reinterpret_cast<uintptr_t>(g.quats) |
+                       reinterpret_cast<uintptr_t>(g.s_opt) |
+                       reinterpret_cast<uintptr_t>(g.opacity_logit) |
+                       reinterpret_cast<uintptr_t>(g.sh)) & 15u);
+    B.sets[s] = SetP{g.means, g.quats, g.s_opt, g.opacity_logit, g.sh, g.n, g.sh_degree, g.s_min,
+                     al ? 1 : 0};
   }
   for (int v = 0; v < n_views; ++v) {
     const flod_view& V = views[v];

@@ -47,6 +47,7 @@ struct SetP {
   const float* sh;
   int n, deg;
   float s_min;
+  int bulk_ok;   // every array 16-byte aligned: chunks of 256 Gaussians can be bulk-copied
 };
 
 struct CfgP {

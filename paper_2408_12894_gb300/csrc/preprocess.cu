@@ -1,6 +1,8 @@
 // Per-(view, Gaussian) preprocess and its backward.
 //
-// Forward (one thread per unit): Eq. 4 constrained scale s = exp(s_opt) + s_min (Sec. 4.1),
+// Forward (one thread per unit; a CTA's 128 Gaussians of one set are first bulk-copied into
+// shared memory by TMA when they form a whole aligned chunk): Eq. 4 constrained scale
+// s = exp(s_opt) + s_min (Sec. 4.1),
 // Eq. 1 covariance through M = R diag(s) (Sigma = M M^T, Sec. 3), the local-affine
 // projection of Eq. 2 (Sigma' = (J W M)(J W M)^T + dilation I), conic, opacity, the
 // opacity-aware extent, the tile set (rectangle, or ellipse rows) and the SH colour.
@@ -58,7 +60,7 @@ struct Geom {
 __device__ __forceinline__ void geometry(const SetP& S, uint32_t gi, const ViewP& V,
                                          const CfgP& cfg, Geom& G) {
   const float* mu = S.means + 3ull * gi;
-  const float4 q = __ldg(reinterpret_cast<const float4*>(S.quats) + gi);
+  const float4 q = reinterpret_cast<const float4*>(S.quats)[gi];
   const float* so = S.s_opt + 3ull * gi;
   float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
   G.qinv = 1.f / sqrtf(qq);
@@ -66,10 +68,10 @@ __device__ __forceinline__ void geometry(const SetP& S, uint32_t gi, const ViewP
   quat_rot(G.qn[0], G.qn[1], G.qn[2], G.qn[3], G.R);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    G.es[k] = expf(__ldg(so + k));
+    G.es[k] = expf(so[k]);
     G.s[k] = G.es[k] + S.s_min;
   }
-  const float mx = __ldg(mu), my = __ldg(mu + 1), mz = __ldg(mu + 2);
+  const float mx = mu[0], my = mu[1], mz = mu[2];
   const float* W = V.vm;
   G.t[0] = W[0] * mx + W[1] * my + W[2] * mz + W[3];
   G.t[1] = W[4] * mx + W[5] * my + W[6] * mz + W[7];
@@ -107,7 +109,7 @@ __device__ __forceinline__ void geometry(const SetP& S, uint32_t gi, const ViewP
 __device__ __forceinline__ void view_dir(const SetP& S, uint32_t gi, const ViewP& V, float dir[3],
                                          float& dlen) {
   const float* mu = S.means + 3ull * gi;
-  float dx = __ldg(mu) - V.cpx, dy = __ldg(mu + 1) - V.cpy, dz = __ldg(mu + 2) - V.cpz;
+  float dx = mu[0] - V.cpx, dy = mu[1] - V.cpy, dz = mu[2] - V.cpz;
   dlen = sqrtf(dx * dx + dy * dy + dz * dz);
   float il = 1.f / dlen;
   dir[0] = dx * il; dir[1] = dy * il; dir[2] = dz * il;
@@ -126,7 +128,7 @@ __device__ __forceinline__ void sh_colour(const SetP& S, uint32_t gi, const View
     float cf[48];
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      float4 v = __ldg(c4 + i);
+      float4 v = c4[i];
       cf[4 * i] = v.x; cf[4 * i + 1] = v.y; cf[4 * i + 2] = v.z; cf[4 * i + 3] = v.w;
     }
 #pragma unroll
@@ -137,24 +139,98 @@ __device__ __forceinline__ void sh_colour(const SetP& S, uint32_t gi, const View
     }
   } else {
     for (int k = 0; k < K; ++k) {
-      raw[0] += Y[k] * __ldg(c + 3 * k);
-      raw[1] += Y[k] * __ldg(c + 3 * k + 1);
-      raw[2] += Y[k] * __ldg(c + 3 * k + 2);
+      raw[0] += Y[k] * c[3 * k];
+      raw[1] += Y[k] * c[3 * k + 1];
+      raw[2] += Y[k] * c[3 * k + 2];
     }
   }
 }
 
+// Bulk (TMA) staging of a CTA's kStageN consecutive Gaussians: one thread arms an mbarrier with
+// the byte count and issues one cp.async.bulk per parameter array; every thread then waits
+// on the barrier (bounded) and reads its Gaussian from shared memory.
+constexpr int kStageN = 128;
+constexpr uint32_t kBulkSpinLimit = 1u << 26;
+struct PreStage {
+  float sh[kStageN * 48];
+  float means[kStageN * 3];
+  float4 quats[kStageN];
+  float s_opt[kStageN * 3];
+  float logit[kStageN];
+  unsigned long long bar;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Waits for phase 0 of the barrier; false if the bound ran out.
+__device__ __forceinline__ bool bulk_wait(uint32_t bar) {
+  for (uint32_t i = 0; i < kBulkSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(bar) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 template <int MAXV>
-__global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batch<MAXV> b, Ws ws) {
-  const uint32_t u = blockIdx.x * 256u + threadIdx.x;
+__global__ void __launch_bounds__(kStageN) k_preprocess(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  extern __shared__ __align__(16) unsigned char pre_smem[];
+  PreStage& stg = *reinterpret_cast<PreStage*>(pre_smem);
+  const uint32_t u = blockIdx.x * (uint32_t)kStageN + threadIdx.x;
   const bool in_range = u < b.units;   // always true (units are padded to 1024); kept for safety
   const ViewP& V = b.views[view_of_unit(b, in_range ? u : 0u)];
+  // a whole chunk of one set (no selection, all kStageN Gaussians present): bulk-copy it
+  const uint32_t local0 = blockIdx.x * (uint32_t)kStageN - V.unit_off;
+  const SetP& S0 = b.sets[V.sel ? 0 : V.set];
+  const bool staged = !V.sel && S0.bulk_ok && local0 + kStageN <= V.cap &&
+                      local0 + kStageN <= (uint32_t)S0.n;
+  if (staged) {
+    const uint32_t bar = smem_addr(&stg.bar);
+    const int K = (S0.deg + 1) * (S0.deg + 1);
+    const uint32_t shb = kStageN * 12u * (uint32_t)K;   // 3 K floats per Gaussian
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                   ::"r"(bar), "r"(shb + kStageN * (12u + 16u + 12u + 4u)) : "memory");
+      bulk_load(stg.sh, S0.sh + 3ull * K * local0, shb, bar);
+      bulk_load(stg.means, S0.means + 3ull * local0, kStageN * 12u, bar);
+      bulk_load(stg.quats, S0.quats + 4ull * local0, kStageN * 16u, bar);
+      bulk_load(stg.s_opt, S0.s_opt + 3ull * local0, kStageN * 12u, bar);
+      bulk_load(stg.logit, S0.logit + local0, kStageN * 4u, bar);
+    }
+    __syncthreads();
+    if (!bulk_wait(bar)) {
+      set_status(ws.status, FLOD_DEV_TIMEOUT);
+      if (!bulk_wait(bar)) return;   // copies still in flight: leave the shared memory alone
+    }
+  }
   int si = 0;
   uint32_t gi = 0;
   bool ok = in_range && unit_source(b, V, u - V.unit_off, si, gi);
   if (!ok) {   // padding, or past the view's selection: nothing reads it but its tile count
     if (in_range) ws.tiles_touched[u] = 0;
     return;
+  }
+  const uint32_t gl = staged ? threadIdx.x : gi;     // index into the parameter arrays used
+  // the parameter arrays this unit reads: the staged chunk, or the set in global memory
+  SetP S = b.sets[si];
+  if (staged) {
+    S.sh = stg.sh;
+    S.means = stg.means;
+    S.quats = reinterpret_cast<const float*>(stg.quats);
+    S.s_opt = stg.s_opt;
+    S.logit = stg.logit;
   }
   float2 xy = make_float2(0.f, 0.f);
   float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -165,10 +241,9 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batc
   Geom G;
   UnitTiles t;
   if (ok) {
-    const SetP& S = b.sets[si];
-    geometry(S, gi, V, b.cfg, G);
+    geometry(S, gl, V, b.cfg, G);
     ok = G.t[2] > b.cfg.z_near && G.det > 0.f;
-    o = 1.f / (1.f + expf(-__ldg(S.logit + gi)));
+    o = 1.f / (1.f + expf(-S.logit[gl]));
     if (ok) {
       float lmax = 0.5f * (G.A + G.C) + sqrtf(fmaxf(0.25f * (G.A - G.C) * (G.A - G.C) + G.B * G.B, 0.f));
       const float tau = 2.f * logf(255.f * o);   // alpha >= 1/255 <=> q <= tau
@@ -227,12 +302,11 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ Batc
   }
   ok = ok && touched > 0;
   if (ok) {
-    const SetP& S = b.sets[si];
     float id = 1.f / G.det;
     co = make_float4(G.C * id, -G.B * id, G.A * id, o);
     depth = G.t[2];
     float Y[16], dir[3], dlen, raw[3];
-    sh_colour(S, gi, V, Y, dir, dlen, raw);
+    sh_colour(S, gl, V, Y, dir, dlen, raw);
     rgb = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), 0.f);
   } else {
     xy = make_float2(0.f, 0.f);
@@ -475,7 +549,14 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
 template <int MAXV>
 cudaError_t launch_preprocess(const Batch<MAXV>& b, const Ws& ws, cudaStream_t st) {
   if (b.units == 0) return cudaSuccess;
-  k_preprocess<MAXV><<<(b.units + 255) / 256, 256, 0, st>>>(b, ws);
+  static bool attr = false;   // one opt-in per template instance
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_preprocess<MAXV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PreStage));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_preprocess<MAXV><<<(b.units + kStageN - 1) / kStageN, kStageN, sizeof(PreStage), st>>>(b, ws);
   return cudaGetLastError();
 }
 
