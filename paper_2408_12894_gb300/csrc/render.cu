@@ -18,6 +18,12 @@
 // reduces the nine per-Gaussian gradients with a transposing butterfly and the owning lanes
 // add them with atomics; warps where no pixel touches the Gaussian skip the reduction.
 //
+// Both walks take a thread's pixels in pairs (rows 2p, 2p + 1 of its column): the pair's
+// values sit in the two halves of a float2 and every operation on them is one packed
+// float32 instruction (add/mul/fma .f32x2), with the per-Gaussian operands stored twice in
+// shared memory so that one 16-byte load yields two ready pair operands. A pixel of a pair
+// that does not blend the splat gets G = 0, which leaves its T, colour and P unchanged.
+//
 // Launch modes: one CTA per tile in tile order, or persistent CTAs (about the number that
 // fit on the GPU) taking tiles from the largest-first queue that flod_bin_sort builds.
 #include "common.cuh"
@@ -58,19 +64,30 @@ __device__ __forceinline__ bool next_tile(const Ws& ws, uint32_t n_tiles, int co
 // ---------------------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------------------
+// Pairs of float32 values in one instruction (sm_100 and later): the two pixels of a pair
+// share every per-Gaussian operand, so one packed instruction does the work of two scalar ones.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 template <int MAXV, int PIX, bool PERSIST>
 __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant__ Batch<MAXV> b,
                                                           Ws ws, float* __restrict__ out_rgb,
                                                           float* __restrict__ out_T,
                                                           uint32_t* __restrict__ out_nc) {
-  __shared__ float4 s_xq[256];    // mean x, y and the skip threshold q'_min
-  __shared__ float4 s_cs[256];
-  __shared__ float4 s_rgb[256];
+  static_assert(PIX % 2 == 0, "pixels are walked in pairs");
+  constexpr int NP = PIX / 2;
+  __shared__ float4 s_x[256];     // (mean x, a', 2b', q'_min)
+  __shared__ float4 s_y[256];     // (-mean y, -mean y, c', c')
+  __shared__ float4 s_o[256];     // (-o, -o, r, r)
+  __shared__ float4 s_c[256];     // (g, g, b, b)
   const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
   const int tw = b.cfg.tile_w;
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
   const int batch = b.cfg.batch;
+  const float2 one2 = dup2(1.f);
   uint32_t evals = 0, blended = 0;
   uint32_t tile;
   for (bool first = true; next_tile<PERSIST>(ws, b.tiles, 0, first, tile); first = false) {
@@ -80,17 +97,21 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
     const int py0 = (int)(lt / V.tiles_x) * b.cfg.tile_h + (tid / tw) * PIX;
     const uint2 rg = ws.ranges[tile];
     const float fx = (float)px + 0.5f;
-    float T[PIX], c0[PIX], c1[PIX], c2[PIX], fy[PIX];
+    // per pixel pair: T and the colour sums (negated); per pixel: liveness, stop position
+    float2 T[NP], NC0[NP], NC1[NP], NC2[NP], FY[NP];
     uint32_t last[PIX], stop[PIX];
     bool live[PIX];
     bool done = true;
 #pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      T[p] = one2;
+      NC0[p] = NC1[p] = NC2[p] = dup2(0.f);
+      FY[p] = make_float2((float)(py0 + 2 * p) + 0.5f, (float)(py0 + 2 * p + 1) + 0.5f);
+    }
+#pragma unroll
     for (int j = 0; j < PIX; ++j) {
-      T[j] = 1.f;
-      c0[j] = c1[j] = c2[j] = 0.f;
       last[j] = 0;
       stop[j] = 0;
-      fy[j] = (float)(py0 + j) + 0.5f;
       live[j] = px < V.width && py0 + j < V.height;
       done = done && !live[j];
     }
@@ -102,40 +123,63 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
         const uint32_t id = vals[start + k];
         const float2 m = ws.xy[id];
         const float4 co = ws.conic_o[id];
-        s_xq[k] = make_float4(m.x, m.y, splat_qmin(co.w), 0.f);
-        s_cs[k] = scale_conic(co);
-        s_rgb[k] = ws.rgb[id];
+        const float4 cs = scale_conic(co);
+        const float4 c = ws.rgb[id];
+        s_x[k] = make_float4(m.x, cs.x, cs.y, splat_qmin(co.w));
+        s_y[k] = make_float4(-m.y, -m.y, cs.z, cs.z);
+        s_o[k] = make_float4(-co.w, -co.w, c.x, c.x);
+        s_c[k] = make_float4(c.y, c.y, c.z, c.z);
       }
       __syncthreads();
       if (!done) {
 #pragma unroll 4
         for (int k = 0; k < cnt; ++k) {
-          const float4 mq = s_xq[k];
-          const float4 cs = s_cs[k];
-          const float dx = fx - mq.x;
-          const float t0 = __fmul_rn(__fmul_rn(cs.x, dx), dx);
-          const float t1 = __fmul_rn(cs.y, dx);
+          const float4 sx = s_x[k];
+          const float4 sy = s_y[k];
+          const float dx = fx - sx.x;
+          const float2 t0 = dup2(__fmul_rn(__fmul_rn(sx.y, dx), dx));
+          const float2 t1 = dup2(__fmul_rn(sx.z, dx));
+          const float2 nmy = make_float2(sy.x, sy.y), cz = make_float2(sy.z, sy.w);
           ++pos;
 #pragma unroll
-          for (int j = 0; j < PIX; ++j) {
-            const float qs = splat_q(t0, t1, fy[j] - mq.y, cs);
-            if (!live[j] || qs < mq.z) continue;     // stopped, or alpha < 1/255
-            float g;
-            const float a = splat_alpha(qs, cs.w, g);
-            const float Tn = T[j] * (1.f - a);
-            if (Tn < kTMin) {
-              live[j] = false;
-              stop[j] = pos;
-              continue;
+          for (int p = 0; p < NP; ++p) {
+            const float2 dy = add2(FY[p], nmy);
+            const float2 q = fma2(dy, fma2(cz, dy, t1), t0);
+            const bool pa = live[2 * p] && !(q.x < sx.w);       // live and alpha >= 1/255
+            const bool pb = live[2 * p + 1] && !(q.y < sx.w);
+            if (!(pa || pb)) continue;
+            const float4 so = s_o[k];
+            float2 g;
+            g.x = pa ? ex2_approx(q.x) : 0.f;
+            g.y = pb ? ex2_approx(q.y) : 0.f;
+            const float2 nog = mul2(make_float2(so.x, so.y), g);   // -o G
+            float2 na = make_float2(fmaxf(-kAlphaMax, nog.x), fmaxf(-kAlphaMax, nog.y));
+            float2 Tn = mul2(T[p], add2(one2, na));                // T (1 - alpha)
+            const bool sa = Tn.x < kTMin, sb = Tn.y < kTMin;      // only a blended pixel can
+            if (sa || sb) {                                       // fall below: it stops here
+              if (sa) {
+                live[2 * p] = false;
+                stop[2 * p] = pos;
+                na.x = 0.f;
+                Tn.x = T[p].x;
+              }
+              if (sb) {
+                live[2 * p + 1] = false;
+                stop[2 * p + 1] = pos;
+                na.y = 0.f;
+                Tn.y = T[p].y;
+              }
             }
-            const float4 c = s_rgb[k];
-            const float w = a * T[j];
-            c0[j] += w * c.x;
-            c1[j] += w * c.y;
-            c2[j] += w * c.z;
-            T[j] = Tn;
-            last[j] = pos;
-            ++blended;
+            const float4 sc = s_c[k];
+            const float2 nw = mul2(na, T[p]);                      // -alpha T
+            NC0[p] = fma2(nw, make_float2(so.z, so.w), NC0[p]);
+            NC1[p] = fma2(nw, make_float2(sc.x, sc.y), NC1[p]);
+            NC2[p] = fma2(nw, make_float2(sc.z, sc.w), NC2[p]);
+            T[p] = Tn;
+            const bool ba = pa && !sa, bb = pb && !sb;
+            last[2 * p] = ba ? pos : last[2 * p];
+            last[2 * p + 1] = bb ? pos : last[2 * p + 1];
+            blended += (uint32_t)ba + (uint32_t)bb;
           }
           if ((k & 7) == 7) {              // every eighth splat: leave once all pixels stopped
             bool any_live = false;
@@ -160,13 +204,16 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
     for (int j = 0; j < PIX; ++j) {
       const int py = py0 + j;
       if (px < V.width && py < V.height) {
+        const int p = j / 2;
+        const bool hi = j & 1;
+        const float t = hi ? T[p].y : T[p].x;
         evals += live[j] ? pos : stop[j];
-        const uint64_t p = (uint64_t)py * V.width + px;
-        out_rgb[3 * V.pix_off + p] = c0[j] + T[j] * b.cfg.bg[0];
-        out_rgb[3 * V.pix_off + npix + p] = c1[j] + T[j] * b.cfg.bg[1];
-        out_rgb[3 * V.pix_off + 2 * npix + p] = c2[j] + T[j] * b.cfg.bg[2];
-        out_T[V.pix_off + p] = T[j];
-        out_nc[V.pix_off + p] = last[j];
+        const uint64_t i = (uint64_t)py * V.width + px;
+        out_rgb[3 * V.pix_off + i] = t * b.cfg.bg[0] - (hi ? NC0[p].y : NC0[p].x);
+        out_rgb[3 * V.pix_off + npix + i] = t * b.cfg.bg[1] - (hi ? NC1[p].y : NC1[p].x);
+        out_rgb[3 * V.pix_off + 2 * npix + i] = t * b.cfg.bg[2] - (hi ? NC2[p].y : NC2[p].x);
+        out_T[V.pix_off + i] = t;
+        out_nc[V.pix_off + i] = last[j];
       }
     }
   }
@@ -226,17 +273,23 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
                                                           Ws ws, const float* __restrict__ dL,
                                                           const float* __restrict__ fwd_T,
                                                           const uint32_t* __restrict__ fwd_nc) {
+  static_assert(PIX % 2 == 0, "pixels are walked in pairs");
+  constexpr int NP = PIX / 2;
+  // per staged Gaussian: the scalars of its column terms, and the operands the pixel pairs
+  // share, each stored twice so that one 16-byte load yields two pair operands
   __shared__ uint32_t s_id[256];
-  __shared__ float2 s_xy[256];
-  __shared__ float4 s_co[256];
-  __shared__ float4 s_cs[256];
-  __shared__ float4 s_rgb[256];
+  __shared__ float4 s_x[256];     // (mean x, a', 2b', q'_min)
+  __shared__ float4 s_y[256];     // (-mean y, -mean y, c', c')
+  __shared__ float4 s_o[256];     // (-o, -o, r, r)
+  __shared__ float4 s_c[256];     // (g, g, b, b)
+  __shared__ float4 s_co[256];    // (a, b, c, o): the conic for the gradient expansion
   __shared__ uint32_t s_max;
   const uint32_t* __restrict__ vals = ws.vals[ws.plan[kPlanFinal]];
   const int tw = b.cfg.tile_w;
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
   const int batch = b.cfg.batch;
+  const float2 one2 = dup2(1.f);
   uint32_t evals = 0;
   uint32_t tile;
   for (bool first = true; next_tile<PERSIST>(ws, b.tiles, 1, first, tile); first = false) {
@@ -247,28 +300,38 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
     const uint2 rg = ws.ranges[tile];
     const float fx = (float)px + 0.5f;
     const uint64_t npix = (uint64_t)V.width * V.height;
-    // per pixel: T, the upstream gradient g, and P = g . (colour behind the current splat,
-    // background included), the only use of that colour in the chain rule
-    float T[PIX], g0[PIX], g1[PIX], g2[PIX], P[PIX], fy[PIX];
+    // per pixel pair: T, the upstream gradient g, and NP = -g . (colour behind the current
+    // splat, background included), the only use of that colour in the chain rule
+    float2 T[NP], G0[NP], G1[NP], G2[NP], NPb[NP], FY[NP];
     uint32_t last[PIX];
     uint32_t my_max = 0;
 #pragma unroll
-    for (int j = 0; j < PIX; ++j) {
-      const int py = py0 + j;
-      fy[j] = (float)py + 0.5f;
-      T[j] = g0[j] = g1[j] = g2[j] = 0.f;
-      last[j] = 0;
-      if (px < V.width && py < V.height) {
-        const uint64_t p = (uint64_t)py * V.width + px;
-        T[j] = fwd_T[V.pix_off + p];
-        last[j] = fwd_nc[V.pix_off + p];
-        g0[j] = dL[3 * V.pix_off + p];
-        g1[j] = dL[3 * V.pix_off + npix + p];
-        g2[j] = dL[3 * V.pix_off + 2 * npix + p];
+    for (int p = 0; p < NP; ++p) {
+      float t[2] = {0.f, 0.f}, g0[2] = {0.f, 0.f}, g1[2] = {0.f, 0.f}, g2[2] = {0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * p + h;
+        const int py = py0 + j;
+        last[j] = 0;
+        if (px < V.width && py < V.height) {
+          const uint64_t i = (uint64_t)py * V.width + px;
+          t[h] = fwd_T[V.pix_off + i];
+          last[j] = fwd_nc[V.pix_off + i];
+          g0[h] = dL[3 * V.pix_off + i];
+          g1[h] = dL[3 * V.pix_off + npix + i];
+          g2[h] = dL[3 * V.pix_off + 2 * npix + i];
+        }
+        my_max = max(my_max, last[j]);
+        evals += last[j];
       }
-      P[j] = T[j] * (g0[j] * b.cfg.bg[0] + g1[j] * b.cfg.bg[1] + g2[j] * b.cfg.bg[2]);
-      my_max = max(my_max, last[j]);
-      evals += last[j];
+      T[p] = make_float2(t[0], t[1]);
+      G0[p] = make_float2(g0[0], g0[1]);
+      G1[p] = make_float2(g1[0], g1[1]);
+      G2[p] = make_float2(g2[0], g2[1]);
+      FY[p] = make_float2((float)(py0 + 2 * p) + 0.5f, (float)(py0 + 2 * p + 1) + 0.5f);
+      const float2 gb = fma2(G2[p], dup2(b.cfg.bg[2]),
+                             fma2(G1[p], dup2(b.cfg.bg[1]), mul2(G0[p], dup2(b.cfg.bg[0]))));
+      NPb[p] = mul2(dup2(-1.f), mul2(T[p], gb));
     }
     if (tid == 0) s_max = 0;
     __syncthreads();
@@ -282,69 +345,83 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
       for (int k = tid; k < cnt; k += nthr) {
         const uint32_t id = vals[bstart + k];
         s_id[k] = id;
-        s_xy[k] = ws.xy[id];
+        const float2 m = ws.xy[id];
         const float4 co = ws.conic_o[id];
+        const float4 cs = scale_conic(co);
+        const float4 c = ws.rgb[id];
+        s_x[k] = make_float4(m.x, cs.x, cs.y, splat_qmin(co.w));
+        s_y[k] = make_float4(-m.y, -m.y, cs.z, cs.z);
+        s_o[k] = make_float4(-co.w, -co.w, c.x, c.x);
+        s_c[k] = make_float4(c.y, c.y, c.z, c.z);
         s_co[k] = co;
-        float4 cs = scale_conic(co);
-        cs.w = splat_qmin(co.w);     // the opacity stays in s_co
-        s_cs[k] = cs;
-        s_rgb[k] = ws.rgb[id];
       }
       __syncthreads();
 #pragma unroll 4
       for (int k = cnt - 1; k >= 0; --k) {
         const uint32_t pos = bstart - rg.x + (uint32_t)k + 1u;
-        const float2 m = s_xy[k];
-        const float4 co = s_co[k];
-        const float4 cs = s_cs[k];   // (a', 2b', c', q'_min)
-        const float4 c = s_rgb[k];
-        const float dx = fx - m.x;
-        const float t0 = __fmul_rn(__fmul_rn(cs.x, dx), dx);
-        const float t1 = __fmul_rn(cs.y, dx);
-        // this thread's sums over its pixels: colour gradient, and the moments
-        // E0 = sum e, E1 = sum e dy, E2 = sum e dy^2 of e = G dL/dalpha (unclamped alpha)
-        float r0 = 0.f, r1 = 0.f, r2 = 0.f, E0 = 0.f, E1 = 0.f, E2 = 0.f;
+        const float4 sx = s_x[k];
+        const float4 sy = s_y[k];
+        const float dx = fx - sx.x;
+        const float2 t0 = dup2(__fmul_rn(__fmul_rn(sx.y, dx), dx));
+        const float2 t1 = dup2(__fmul_rn(sx.z, dx));
+        const float2 nmy = make_float2(sy.x, sy.y), cz = make_float2(sy.z, sy.w);
+        // this thread's sums over its pixels (pairwise): colour gradient (negated), and the
+        // moments E0 = sum e, E1 = sum e dy, E2 = sum e dy^2 of e = G dL/dalpha (unclamped)
+        float2 nR0 = dup2(0.f), nR1 = dup2(0.f), nR2 = dup2(0.f);
+        float2 E0 = dup2(0.f), E1 = dup2(0.f), E2 = dup2(0.f);
         bool any = false;
 #pragma unroll
-        for (int j = 0; j < PIX; ++j) {
-          if (pos > last[j]) continue;
-          const float dy = fy[j] - m.y;
-          const float qs = splat_q(t0, t1, dy, cs);
-          if (qs < cs.w) continue;                   // alpha < 1/255
+        for (int p = 0; p < NP; ++p) {
+          const float2 dy = add2(FY[p], nmy);
+          const float2 q = fma2(dy, fma2(cz, dy, t1), t0);
+          const bool pa = pos <= last[2 * p] && !(q.x < sx.w);      // alpha >= 1/255
+          const bool pb = pos <= last[2 * p + 1] && !(q.y < sx.w);
+          if (!(pa || pb)) continue;
           any = true;
-          float gg;
-          const float a = splat_alpha(qs, co.w, gg);
-          const float ioma = rcp_approx(1.f - a);
-          T[j] *= ioma;                              // T in front of this splat
-          const float w = a * T[j];
-          r0 += w * g0[j];
-          r1 += w * g1[j];
-          r2 += w * g2[j];
-          const float gc = g0[j] * c.x + g1[j] * c.y + g2[j] * c.z;
-          const float dalpha = T[j] * gc - ioma * P[j];
-          P[j] += w * gc;
-          if (co.w * gg < kAlphaMax) {
-            const float e = gg * dalpha;
-            const float ed = e * dy;
-            E0 += e;
-            E1 += ed;
-            E2 += ed * dy;
-          }
+          const float4 so = s_o[k];
+          const float4 sc = s_c[k];
+          float2 g;                                   // G = 2^q' (0: pixel not blended)
+          g.x = pa ? ex2_approx(q.x) : 0.f;
+          g.y = pb ? ex2_approx(q.y) : 0.f;
+          const float2 nog = mul2(make_float2(so.x, so.y), g);      // -o G
+          const float2 na = make_float2(fmaxf(-kAlphaMax, nog.x), fmaxf(-kAlphaMax, nog.y));
+          const float2 oma = add2(one2, na);                       // 1 - alpha
+          const float2 ioma = make_float2(pa ? rcp_approx(oma.x) : 1.f,
+                                          pb ? rcp_approx(oma.y) : 1.f);
+          T[p] = mul2(T[p], ioma);                                 // T in front of this splat
+          const float2 nw = mul2(na, T[p]);                        // -alpha T
+          nR0 = fma2(nw, G0[p], nR0);
+          nR1 = fma2(nw, G1[p], nR1);
+          nR2 = fma2(nw, G2[p], nR2);
+          const float2 gc = fma2(G2[p], make_float2(sc.z, sc.w),
+                                 fma2(G1[p], make_float2(sc.x, sc.y),
+                                      mul2(G0[p], make_float2(so.z, so.w))));
+          const float2 dal = fma2(ioma, NPb[p], mul2(T[p], gc));  // T (g.c) - P / (1 - alpha)
+          NPb[p] = fma2(nw, gc, NPb[p]);                           // P += alpha T (g.c)
+          const float2 ge = make_float2(nog.x > -kAlphaMax ? g.x : 0.f,
+                                        nog.y > -kAlphaMax ? g.y : 0.f);
+          const float2 e = mul2(ge, dal);
+          const float2 ed = mul2(e, dy);
+          E0 = add2(E0, e);
+          E1 = add2(E1, ed);
+          E2 = fma2(ed, dy, E2);
         }
         if (__any_sync(0xffffffffu, any)) {
           // dL/dq = -o/2 e; q = a dx^2 + 2 b dx dy + c dy^2, dq/du = -2 (a dx + b dy), ...
+          const float4 co = s_co[k];
           const float hq = -0.5f * co.w;
-          const float Q0 = hq * E0, Q1 = hq * E1;
+          const float e0 = E0.x + E0.y, e1 = E1.x + E1.y, e2 = E2.x + E2.y;
+          const float Q0 = hq * e0, Q1 = hq * e1;
           float acc[9];
           acc[0] = -2.f * (co.x * dx * Q0 + co.y * Q1);
           acc[1] = -2.f * (co.y * dx * Q0 + co.z * Q1);
-          acc[2] = E0;
+          acc[2] = e0;
           acc[3] = dx * dx * Q0;
           acc[4] = 2.f * dx * Q1;
-          acc[5] = hq * E2;
-          acc[6] = r0;
-          acc[7] = r1;
-          acc[8] = r2;
+          acc[5] = hq * e2;
+          acc[6] = -(nR0.x + nR0.y);
+          acc[7] = -(nR1.x + nR1.y);
+          acc[8] = -(nR2.x + nR2.y);
           warp_reduce_add9(acc, ws.grad2d + 3ull * s_id[k]);
         }
       }
