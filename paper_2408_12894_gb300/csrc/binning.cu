@@ -14,18 +14,24 @@ namespace flod {
 constexpr uint32_t kLightPairs = 16 * kEmitSlice;   // blocks up to this many pairs: k_emit_light
 constexpr uint32_t kBigUnit = 32;                    // units above this many tiles: warp-wide
 
-// Pair count of every 1024 slots of the depth-sorted unit order.
+// Pair count of every 1024 slots of the depth-sorted unit order. The tile count of every slot
+// is also stored in slot order (in the unit sort's key buffer 0, free once the sort is done;
+// 0 past the visible units), so that the emission reads it without a gather.
 __global__ void __launch_bounds__(256) k_block_sums(Ws ws) {
   __shared__ uint32_t red[8];
   const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
   const uint32_t nvis = visible_units(ws);
   const uint32_t s0 = blockIdx.x * 1024u + 4u * threadIdx.x;
-  uint32_t s = 0;
+  uint4 c = make_uint4(0u, 0u, 0u, 0u);
   if (s0 < nvis) {   // slots past the visible units hold no unit
     const uint4 o = reinterpret_cast<const uint4*>(order)[blockIdx.x * 256u + threadIdx.x];
-    s = ws.tiles_touched[o.x] + (s0 + 1 < nvis ? ws.tiles_touched[o.y] : 0u) +
-        (s0 + 2 < nvis ? ws.tiles_touched[o.z] : 0u) + (s0 + 3 < nvis ? ws.tiles_touched[o.w] : 0u);
+    c.x = ws.tiles_touched[o.x];
+    c.y = s0 + 1 < nvis ? ws.tiles_touched[o.y] : 0u;
+    c.z = s0 + 2 < nvis ? ws.tiles_touched[o.z] : 0u;
+    c.w = s0 + 3 < nvis ? ws.tiles_touched[o.w] : 0u;
   }
+  reinterpret_cast<uint4*>(slot_counts(ws))[blockIdx.x * 256u + threadIdx.x] = c;
+  uint32_t s = c.x + c.y + c.z + c.w;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -427,11 +433,18 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
   }
 }
 
-// Key emission of a light block (at most kLightPairs pairs), one CTA per 1024-slot block:
-// the block's pair counts are scanned in shared memory; each thread writes the tiles of its
-// four units one after the other, row by row from their tile records; units of more than
-// kBigUnit tiles are written by their whole warp, row by row with one lane per tile. Heavier
-// blocks are left to the sliced k_emit.
+// Key emission of a light block (at most kLightPairs pairs), one CTA per 1024-slot block.
+// Each warp owns 128 consecutive slots, taken as 4 rounds of 32 (one slot per lane); the
+// block's pair counts are scanned per warp and across the 8 warps. In a round:
+//   - "small" units (at most kBigUnit tiles, rows given by the tile record's table or uniform
+//     form) are written one pair per lane: the round's small pairs are numbered 0..n-1, lane
+//     i finds the unit holding pair i by a binary search over the units' first numbers
+//     (shuffles), decodes its tile from the unit's record and writes keys and values of 32
+//     consecutive positions of a unit run at once;
+//   - the other units are written by the whole warp, one after the other: rows 32 at a time
+//     (one per lane, their columns from the record or recomputed), then each row's tiles one
+//     per lane.
+// Heavier blocks are left to the sliced k_emit.
 template <int MAXV>
 __device__ __forceinline__ bool rec_row_tiles(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
                                               const uint4& rc, const UnitTiles& t, uint32_t r,
@@ -453,108 +466,196 @@ __device__ __forceinline__ bool rec_row_tiles(const Batch<MAXV>& b, const Ws& ws
   return c > 0;
 }
 
+// The whole warp writes the n_all pairs of unit u (tile record rc) from position p0 on.
 template <int MAXV>
-__global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batch<MAXV> b, Ws ws) {
-  __shared__ uint32_t warp_tot[8];
-  const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]] + (size_t)blockIdx.x * kScanBlock;
-  const uint32_t nvis = visible_units(ws);
-  const uint32_t s0 = blockIdx.x * kScanBlock + 4u * tid;
-  uint4 un = make_uint4(0u, 0u, 0u, 0u);
-  if (s0 < nvis) un = reinterpret_cast<const uint4*>(order)[tid];
-  const uint32_t unit[4] = {un.x, un.y, un.z, un.w};
-  uint32_t cnt[4];
+__device__ __forceinline__ void emit_unit_warp(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
+                                               const uint4& rc, unsigned long long p0,
+                                               uint32_t n_all, uint32_t* keys, uint32_t* vals,
+                                               unsigned long long cap) {
+  const int lane = threadIdx.x & 31;
+  const ViewP& V = b.views[view_of_unit(b, u)];
+  uint32_t row_base = V.tile_off, tiles_x = V.tiles_x;
+  UnitTiles t;
+  if ((rc.y >> 16) == kRecCompute) slot_tiles(b, ws, u, t, row_base, tiles_x);
+  const uint32_t nrows = rc.y & 0xffffu;
+  uint32_t done = 0;
+  for (uint32_t r0 = 0; r0 < nrows; r0 += 32) {
+    const uint32_t r = r0 + lane;
+    uint32_t rn = 0, rt0 = 0;
+    if (r < nrows && !rec_row_tiles(b, ws, u, rc, t, r, row_base, tiles_x, rn, rt0)) rn = 0;
+    uint32_t incl = rn;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) cnt[j] = s0 + j < nvis ? ws.tiles_touched[unit[j]] : 0u;
-  uint32_t total;
-  uint32_t run = block_excl_sum(cnt[0] + cnt[1] + cnt[2] + cnt[3], warp_tot, total);
-  if (total == 0 || total > kLightPairs) return;   // nothing, or the sliced emission's
-  const unsigned long long base = ws.block_sums[blockIdx.x];
-  const unsigned long long cap = ws.pair_capacity;
-  uint32_t* keys = ws.keys[0];
-  uint32_t* vals = ws.vals[0];
-  uint32_t pre[4], big = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    pre[j] = run;
-    run += cnt[j];
-    if (cnt[j] > kBigUnit) big |= 1u << j;
-  }
-  // 1. my units, one after the other
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (!cnt[j] || (big >> j & 1u)) continue;
-    const uint32_t u = unit[j];
-    const uint4 rc = ws.trec[u];
-    const ViewP& V = b.views[view_of_unit(b, u)];
-    uint32_t row_base = V.tile_off, tiles_x = V.tiles_x;
-    UnitTiles t;
-    if ((rc.y >> 16) == kRecCompute) slot_tiles(b, ws, u, t, row_base, tiles_x);
-    unsigned long long p = base + pre[j];
-    const unsigned long long end = p + cnt[j];
-    const uint32_t nrows = rc.y & 0xffffu;
-    for (uint32_t r = 0; r < nrows && p < end; ++r) {
-      uint32_t n, tile0;
-      if (!rec_row_tiles(b, ws, u, rc, t, r, row_base, tiles_x, n, tile0)) continue;
-      for (uint32_t c = 0; c < n && p < end; ++c, ++p) {
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t rpos = done + incl - rn;
+    const uint32_t rows_here = min(32u, nrows - r0);
+    for (uint32_t i = 0; i < rows_here; ++i) {
+      const uint32_t ni = __shfl_sync(0xffffffffu, rn, i);
+      const uint32_t ti = __shfl_sync(0xffffffffu, rt0, i);
+      const uint32_t pi = __shfl_sync(0xffffffffu, rpos, i);
+      for (uint32_t c = lane; c < ni && pi + c < n_all; c += 32) {
+        const unsigned long long p = p0 + pi + c;
         if (p < cap) {
-          keys[p] = tile0 + c;
+          keys[p] = ti + c;
           vals[p] = u;
         }
       }
     }
-    if (p != end) set_status(ws.status, FLOD_DEV_TILESET);
+    done += __shfl_sync(0xffffffffu, incl, 31);
   }
-  // 2. big units of my warp, by the whole warp: rows in chunks of 32 (one per lane), then
-  //    each row's tiles one per lane
-  uint32_t todo = __ballot_sync(0xffffffffu, big != 0);
-  while (todo) {
-    const int src = __ffs(todo) - 1;
-    const uint32_t my_j = big ? (uint32_t)(__ffs(big) - 1) : 0u;
-    const uint32_t j = __shfl_sync(0xffffffffu, my_j, src);
-    uint32_t su = unit[0], sp = pre[0], sc = cnt[0];
+  if (lane == 0 && done != n_all) set_status(ws.status, FLOD_DEV_TILESET);
+}
+
+// Tile (relative to the record's first row and column: row, column offset) of the j-th tile of
+// a small unit, rows in order. Table form: up to kRecRows rows of (offset, count); uniform
+// form: rows of z tiles from offset 0. False if j lies past the rows' tiles.
+__device__ __forceinline__ bool small_unit_tile(uint32_t y, uint32_t z, uint32_t w, uint32_t j,
+                                                uint32_t& row, uint32_t& col) {
+  if ((y >> 16) == kRecUniform) {
+    if (z == 0) return false;
+    row = j / z;
+    col = j - row * z;
+    return row < (y & 0xffffu);
+  }
+  const uint32_t nrows = y & 0xffffu;
+  row = 0;
 #pragma unroll
-    for (int q = 1; q < 4; ++q)
-      if ((uint32_t)q == my_j) { su = unit[q]; sp = pre[q]; sc = cnt[q]; }
-    const uint32_t u = __shfl_sync(0xffffffffu, su, src);
-    const unsigned long long p0 = base + __shfl_sync(0xffffffffu, sp, src);
-    const uint32_t n_all = __shfl_sync(0xffffffffu, sc, src);
-    if (lane == src) big &= ~(1u << j);
-    todo = __ballot_sync(0xffffffffu, big != 0);
-    const uint4 rc = ws.trec[u];
-    const ViewP& V = b.views[view_of_unit(b, u)];
-    uint32_t row_base = V.tile_off, tiles_x = V.tiles_x;
-    UnitTiles t;
-    if ((rc.y >> 16) == kRecCompute) slot_tiles(b, ws, u, t, row_base, tiles_x);
-    const uint32_t nrows = rc.y & 0xffffu;
-    uint32_t done = 0;
-    for (uint32_t r0 = 0; r0 < nrows; r0 += 32) {
-      const uint32_t r = r0 + lane;
-      uint32_t rn = 0, rt0 = 0;
-      if (r < nrows && !rec_row_tiles(b, ws, u, rc, t, r, row_base, tiles_x, rn, rt0)) rn = 0;
-      uint32_t incl = rn;
+  for (int r = 0; r < kRecRows; ++r) {
+    const uint32_t h = ((r < 2 ? z : w) >> (16 * (r & 1))) & 0xffffu;
+    const uint32_t n = (uint32_t)r < nrows ? h >> 8 : 0u;
+    if (j < n) {
+      col = (h & 0xffu) + j;
+      return true;
+    }
+    j -= n;
+    ++row;
+  }
+  return false;
+}
+
+template <int MAXV>
+__global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  constexpr int kRounds = kScanBlock / 256;   // rounds of 32 slots per warp
+  __shared__ uint32_t warp_tot[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const size_t slot0 = (size_t)blockIdx.x * kScanBlock + (size_t)wid * (32 * kRounds) + lane;
+  const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
+  const uint32_t* counts = slot_counts(ws);   // 0 past the visible units
+  uint32_t unit[kRounds], cnt[kRounds];
+  uint32_t wsum = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+  for (int r = 0; r < kRounds; ++r) {
+    cnt[r] = counts[slot0 + 32 * r];
+    unit[r] = order[slot0 + 32 * r];
+    wsum += cnt[r];
+  }
+  uint4 rc[kRounds];   // tile records, requested before the block scan
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r)
+    rc[r] = cnt[r] ? ws.trec[unit[r]] : make_uint4(0u, 0u, 0u, 0u);
+  wsum = __reduce_add_sync(0xffffffffu, wsum);
+  if (lane == 0) warp_tot[wid] = wsum;
+  __syncthreads();
+  uint32_t total = 0, wpre = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t t = warp_tot[q];
+    if (q < wid) wpre += t;
+    total += t;
+  }
+  if (total == 0 || total > kLightPairs) return;   // nothing, or the sliced emission's
+  const unsigned long long cap = ws.pair_capacity;
+  uint32_t* keys = ws.keys[0];
+  uint32_t* vals = ws.vals[0];
+  unsigned long long base = ws.block_sums[blockIdx.x] + wpre;
+#pragma unroll 1
+  for (int r = 0; r < kRounds; ++r) {
+    // this round's slot (a select chain keeps the per-round arrays in registers)
+    uint32_t c = cnt[0], u = unit[0];
+    uint4 rr = rc[0];
+#pragma unroll
+    for (int q = 1; q < kRounds; ++q)
+      if (q == r) {
+        c = cnt[q];
+        u = unit[q];
+        rr = rc[q];
       }
-      const uint32_t rpos = done + incl - rn;
-      const uint32_t rows_here = min(32u, nrows - r0);
-      for (uint32_t i = 0; i < rows_here; ++i) {
-        const uint32_t ni = __shfl_sync(0xffffffffu, rn, i);
-        const uint32_t ti = __shfl_sync(0xffffffffu, rt0, i);
-        const uint32_t pi = __shfl_sync(0xffffffffu, rpos, i);
-        for (uint32_t c = lane; c < ni && pi + c < n_all; c += 32) {
-          const unsigned long long p = p0 + pi + c;
-          if (p < cap) {
-            keys[p] = ti + c;
-            vals[p] = u;
-          }
+    const uint32_t mode = rr.y >> 16;
+    const bool small = c && c <= kBigUnit && mode != kRecCompute;
+    // one scan for both: all pairs (low 17 bits: a light block has at most 2^16) and the
+    // small units' pairs (high bits)
+    const uint32_t x = c | (small ? c : 0u) << 17;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t excl = (incl - x) & 0x1ffffu;           // first position (round-relative)
+    const uint32_t vstart = (incl - x) >> 17;               // first small-pair number
+    const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t vtot = rtot >> 17;
+    // small units: the tile of the rectangle's first row and column, the view's tile columns
+    uint32_t tb = 0, tx = 0;
+    if (small) {
+      const ViewP& V = b.views[view_of_unit(b, u)];
+      tx = V.tiles_x;
+      tb = V.tile_off + (rr.x >> 16) * tx + (rr.x & 0xffffu);
+    }
+    for (uint32_t i0 = 0; i0 < vtot; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      int v = 0;   // the last lane whose first small-pair number is <= i
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t sv = __shfl_sync(0xffffffffu, vstart, v + step);
+        if (sv <= i) v += step;
+      }
+      const uint32_t j = i - __shfl_sync(0xffffffffu, vstart, v);
+      const uint32_t pr = __shfl_sync(0xffffffffu, excl, v);
+      const uint32_t uv = __shfl_sync(0xffffffffu, u, v);
+      const uint32_t tbv = __shfl_sync(0xffffffffu, tb, v);
+      const uint32_t txv = __shfl_sync(0xffffffffu, tx, v);
+      const uint32_t yv = __shfl_sync(0xffffffffu, rr.y, v);
+      const uint32_t zv = __shfl_sync(0xffffffffu, rr.z, v);
+      const uint32_t wv = __shfl_sync(0xffffffffu, rr.w, v);
+      if (i < vtot) {
+        uint32_t row, col;
+        uint32_t key = 0xffffffffu;   // never a tile id: sorts after every tile, no range
+        if (small_unit_tile(yv, zv, wv, j, row, col)) key = tbv + row * txv + col;
+        else set_status(ws.status, FLOD_DEV_TILESET);
+        const unsigned long long p = base + pr + j;
+        if (p < cap) {
+          keys[p] = key;
+          vals[p] = uv;
         }
       }
-      done += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (lane == 0 && done != n_all) set_status(ws.status, FLOD_DEV_TILESET);
+    // a small unit whose rows hold more tiles than its count
+    if (small && (mode == kRecTable)) {
+      uint32_t sum = 0;
+#pragma unroll
+      for (int q = 0; q < kRecRows; ++q) {
+        const uint32_t h = ((q < 2 ? rr.z : rr.w) >> (16 * (q & 1))) & 0xffffu;
+        if ((uint32_t)q < (rr.y & 0xffffu)) sum += h >> 8;
+      }
+      if (sum != c) set_status(ws.status, FLOD_DEV_TILESET);
+    }
+    // the other units, by the whole warp
+    uint32_t todo = __ballot_sync(0xffffffffu, c && !small);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t us = __shfl_sync(0xffffffffu, u, src);
+      const uint4 rcs = make_uint4(__shfl_sync(0xffffffffu, rr.x, src),
+                                   __shfl_sync(0xffffffffu, rr.y, src),
+                                   __shfl_sync(0xffffffffu, rr.z, src),
+                                   __shfl_sync(0xffffffffu, rr.w, src));
+      emit_unit_warp(b, ws, us, rcs, base + __shfl_sync(0xffffffffu, excl, src),
+                     __shfl_sync(0xffffffffu, c, src), keys, vals, cap);
+    }
+    base += rtot & 0x1ffffu;
   }
 }
 

@@ -301,6 +301,10 @@ __device__ __forceinline__ float splat_alpha(float qs, float o, float& g) {
   return fminf(kAlphaMax, __fmul_rn(o, g));
 }
 
+// Tile count of every depth-sorted unit slot (written by the binning after the unit sort,
+// into the unit sort's key buffer 0, whose keys are no longer needed then).
+__device__ __forceinline__ uint32_t* slot_counts(const Ws& ws) { return ws.ukeys[0]; }
+
 // Number of depth-sorted unit slots (units with at least one tile).
 __device__ __forceinline__ uint32_t visible_units(const Ws& ws) {
   return (uint32_t)*reinterpret_cast<const unsigned long long*>(ws.plan + kPlanNVis);

@@ -323,6 +323,9 @@ struct SortSmem {
 // 32 * kSortKeysPerThread consecutive keys starting at w * 32 * kSortKeysPerThread, round by
 // round, so (warp, round, lane) order is input order and the ranking is stable. Thread d
 // then owns digit value d for the partition-level steps.
+// W: the digit's width in bits, a compile-time constant so that the ranking's ballot loop
+// unrolls (one instantiation per width 1..9).
+template <int W>
 __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int digit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
@@ -337,8 +340,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
   const uint32_t nparts = ws.plan[st.nparts_word];
   const uint32_t* goff = ws.hist + slot * kRadixBins;
   const int shift = (int)((st.shifts >> (8 * digit)) & 0xffu);
-  const int width = (int)((st.widths >> (8 * digit)) & 0xffu);
-  const uint32_t dmask = (1u << width) - 1u;
+  constexpr int width = W;
+  constexpr uint32_t dmask = (1u << W) - 1u;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int d = tid;   // digit value owned in the partition steps
@@ -367,6 +370,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
       const uint32_t dg = (k[r] >> shift) & dmask;
       // lanes holding the same digit, one ballot per digit bit (valid lanes only)
       uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
       for (int b = 0; b < width; ++b) {
         const bool bit = (dg >> b) & 1u;
         const uint32_t m = __ballot_sync(0xffffffffu, bit);
@@ -429,12 +433,23 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int d
 
 int sort_kernel_smem_bytes() { return (int)sizeof(SortSmem); }
 
+// The scatter kernel of each digit width (1..9 bits).
+using PassFn = void (*)(Ws, Stage, int);
+static const PassFn kPassFns[10] = {nullptr,   k_pass<1>, k_pass<2>, k_pass<3>, k_pass<4>,
+                                    k_pass<5>, k_pass<6>, k_pass<7>, k_pass<8>, k_pass<9>};
+
 cudaError_t sort_kernel_prepare() {
-  return cudaFuncSetAttribute(k_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(SortSmem));
+  for (int w = 1; w <= 9; ++w) {
+    const cudaError_t e = cudaFuncSetAttribute(kPassFns[w], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(SortSmem));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
-const void* sort_kernel_ptr() { return reinterpret_cast<const void*>(&k_pass); }
+// Occupancy is taken from the 8-bit instantiation (every width has the same launch shape
+// and shared memory, and at most the registers that two CTAs per SM allow).
+const void* sort_kernel_ptr() { return reinterpret_cast<const void*>(kPassFns[8]); }
 
 static Stage unit_stage(const Ws& ws) {
   Stage s;
@@ -482,10 +497,12 @@ static Stage pair_stage(const Ws& ws, int n_digits, int tile_bits) {
 static cudaError_t run_passes(const Ws& ws, const Stage& s, int n_digits, int resident_small,
                               int resident_sort, cudaStream_t st) {
   for (int p = 0; p < n_digits; ++p) {
-    const uint32_t nbins = 1u << ((s.widths >> (8 * p)) & 0xffu);
+    const int width = (int)((s.widths >> (8 * p)) & 0xffu);
+    if (width < 1 || width > 9) return cudaErrorInvalidValue;
+    const uint32_t nbins = 1u << width;
     k_count<<<resident_small, 256, 0, st>>>(ws, s, p);
     k_scan<<<nbins, kScanThreads, 0, st>>>(ws, s, p, p + 1 == n_digits ? 1 : 0);
-    k_pass<<<resident_sort, kSortThreads, sizeof(SortSmem), st>>>(ws, s, p);
+    kPassFns[width]<<<resident_sort, kSortThreads, sizeof(SortSmem), st>>>(ws, s, p);
   }
   return cudaGetLastError();
 }
