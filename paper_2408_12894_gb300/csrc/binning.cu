@@ -12,7 +12,19 @@
 namespace flod {
 
 constexpr uint32_t kLightPairs = 16 * kEmitSlice;   // blocks up to this many pairs: k_emit_light
-constexpr uint32_t kBigUnit = 32;                    // units above this many tiles: warp-wide
+constexpr uint32_t kBigPerWarp = 2;    // k_emit_big: units per warp, fetched together
+constexpr uint32_t kSmallTiles = 32;   // light emission, one pair per lane: units of at most
+                                       //   this many tiles, rows from their tile record
+
+// The list of units k_emit_big writes: entry e is (first position, unit), held in the pair
+// sort's second key and value buffers (free until the first tile pass writes them). Only
+// units with a first position below the pair capacity are listed, so the list (at most one
+// entry per position) always fits.
+struct BigUnits {
+  uint32_t* pos;
+  uint32_t* unit;
+};
+__device__ __forceinline__ BigUnits big_units(const Ws& ws) { return {ws.keys[1], ws.vals[1]}; }
 
 // Pair count of every 1024 slots of the depth-sorted unit order. The tile count of every slot
 // is also stored in slot order (in the unit sort's key buffer 0, free once the sort is done;
@@ -125,6 +137,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
     ws.plan[kPlanQueue] = 0;
     ws.plan[kPlanQueue + 1] = 0;
     ws.plan[kPlanSlices] = carry_sl;
+    ws.plan[kPlanBigUnits] = 0;
   }
 }
 
@@ -436,14 +449,15 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
 // Key emission of a light block (at most kLightPairs pairs), one CTA per 1024-slot block.
 // Each warp owns 128 consecutive slots, taken as 4 rounds of 32 (one slot per lane); the
 // block's pair counts are scanned per warp and across the 8 warps. In a round:
-//   - "small" units (at most kBigUnit tiles, rows given by the tile record's table or uniform
-//     form) are written one pair per lane: the round's small pairs are numbered 0..n-1, lane
-//     i finds the unit holding pair i by a binary search over the units' first numbers
-//     (shuffles), decodes its tile from the unit's record and writes keys and values of 32
-//     consecutive positions of a unit run at once;
-//   - the other units are written by the whole warp, one after the other: rows 32 at a time
+//   - "small" units (at most kSmallTiles tiles, rows given by the tile record's table or
+//     uniform form) are written one pair per lane: each unit's lane builds its row table, the
+//     round's small pairs are numbered 0..n-1, lane i finds the unit holding pair i by a
+//     binary search over the units' first numbers (shuffles) and its row from the row
+//     starts, and writes keys and values of 32 consecutive positions of a unit run at once;
+//   - the other units (more tiles, rows recomputed from the ellipse, or a record that does
+//     not add up) are listed for k_emit_big, where one warp writes each: rows 32 at a time
 //     (one per lane, their columns from the record or recomputed), then each row's tiles one
-//     per lane.
+//     per lane. A CTA's run time then no longer depends on how many of them its slots hold.
 // Heavier blocks are left to the sliced k_emit.
 template <int MAXV>
 __device__ __forceinline__ bool rec_row_tiles(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
@@ -466,20 +480,27 @@ __device__ __forceinline__ bool rec_row_tiles(const Batch<MAXV>& b, const Ws& ws
   return c > 0;
 }
 
-// The whole warp writes the n_all pairs of unit u (tile record rc) from position p0 on.
+// The whole warp writes the n_all pairs of unit u (tile record rc; centre xy and extent ext,
+// (m, h, rx, ry) or (0, 0, r, r), for rows recomputed) from position p0 on: rows 32 at a
+// time, one per lane (first tile and count, from the record or recomputed), then their pairs
+// one per lane.
 template <int MAXV>
 __device__ __forceinline__ void emit_unit_warp(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
-                                               const uint4& rc, unsigned long long p0,
-                                               uint32_t n_all, uint32_t* keys, uint32_t* vals,
+                                               const uint4& rc, float2 xy, float4 ext,
+                                               unsigned long long p0, uint32_t n_all,
+                                               uint32_t* keys, uint32_t* vals,
                                                unsigned long long cap) {
   const int lane = threadIdx.x & 31;
   const ViewP& V = b.views[view_of_unit(b, u)];
-  uint32_t row_base = V.tile_off, tiles_x = V.tiles_x;
+  const uint32_t row_base = V.tile_off, tiles_x = V.tiles_x;
   UnitTiles t;
-  if ((rc.y >> 16) == kRecCompute) slot_tiles(b, ws, u, t, row_base, tiles_x);
+  if ((rc.y >> 16) == kRecCompute)
+    unit_tiles(xy.x, xy.y, ext, V.width, V.height, b.cfg.tile_w, b.cfg.tile_h,
+               b.cfg.extent_rule == 2, t);
   const uint32_t nrows = rc.y & 0xffffu;
   uint32_t done = 0;
   for (uint32_t r0 = 0; r0 < nrows; r0 += 32) {
+    // rows r0..r0+31, one per lane: their first tile and tile count
     const uint32_t r = r0 + lane;
     uint32_t rn = 0, rt0 = 0;
     if (r < nrows && !rec_row_tiles(b, ws, u, rc, t, r, row_base, tiles_x, rn, rt0)) rn = 0;
@@ -489,56 +510,64 @@ __device__ __forceinline__ void emit_unit_warp(const Batch<MAXV>& b, const Ws& w
       const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    const uint32_t rpos = done + incl - rn;
-    const uint32_t rows_here = min(32u, nrows - r0);
-    for (uint32_t i = 0; i < rows_here; ++i) {
-      const uint32_t ni = __shfl_sync(0xffffffffu, rn, i);
-      const uint32_t ti = __shfl_sync(0xffffffffu, rt0, i);
-      const uint32_t pi = __shfl_sync(0xffffffffu, rpos, i);
-      for (uint32_t c = lane; c < ni && pi + c < n_all; c += 32) {
-        const unsigned long long p = p0 + pi + c;
+    const uint32_t excl = incl - rn;                      // the row's first pair (chunk-relative)
+    const uint32_t chunk = __shfl_sync(0xffffffffu, incl, 31);
+    // the chunk's pairs, one per lane: the row holding pair q is the last row whose first
+    // pair is <= q (a row without tiles shares its first pair with the next one)
+    for (uint32_t q0 = 0; q0 < chunk; q0 += 32) {
+      const uint32_t q = q0 + lane;
+      int v = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t ev = __shfl_sync(0xffffffffu, excl, v + step);
+        if (ev <= q) v += step;
+      }
+      const uint32_t tile = __shfl_sync(0xffffffffu, rt0, v) + (q - __shfl_sync(0xffffffffu, excl, v));
+      if (q < chunk && done + q < n_all) {
+        const unsigned long long p = p0 + done + q;
         if (p < cap) {
-          keys[p] = ti + c;
+          keys[p] = tile;
           vals[p] = u;
         }
       }
     }
-    done += __shfl_sync(0xffffffffu, incl, 31);
+    done += chunk;
   }
   if (lane == 0 && done != n_all) set_status(ws.status, FLOD_DEV_TILESET);
 }
 
-// Tile (relative to the record's first row and column: row, column offset) of the j-th tile of
-// a small unit, rows in order. Table form: up to kRecRows rows of (offset, count); uniform
-// form: rows of z tiles from offset 0. False if j lies past the rows' tiles.
-__device__ __forceinline__ bool small_unit_tile(uint32_t y, uint32_t z, uint32_t w, uint32_t j,
-                                                uint32_t& row, uint32_t& col) {
-  if ((y >> 16) == kRecUniform) {
-    if (z == 0) return false;
-    row = j / z;
-    col = j - row * z;
-    return row < (y & 0xffffu);
-  }
-  const uint32_t nrows = y & 0xffffu;
-  row = 0;
+// Row table of a small unit (rows given by its record's table or uniform form, at most
+// kRecRows rows): for row r, K_r = (tile id of the row's first tile) - (tiles in rows before
+// r), so that its j-th tile is K_row + j, where row = the number of rows r >= 1 starting at or
+// before j (cum = bytes 0..2: start of rows 1..3, 255 past the last row). False if the rows
+// do not hold exactly c tiles or the form has more rows.
+__device__ __forceinline__ bool small_unit_rows(const uint4& rc, uint32_t c, uint32_t tb,
+                                                uint32_t tx, uint4& K, uint32_t& cum) {
+  const uint32_t mode = rc.y >> 16, nrows = rc.y & 0xffffu;
+  if (mode == kRecCompute || nrows > (uint32_t)kRecRows) return false;
+  uint32_t k[kRecRows], start = 0;
+  cum = 0;
 #pragma unroll
   for (int r = 0; r < kRecRows; ++r) {
-    const uint32_t h = ((r < 2 ? z : w) >> (16 * (r & 1))) & 0xffffu;
-    const uint32_t n = (uint32_t)r < nrows ? h >> 8 : 0u;
-    if (j < n) {
-      col = (h & 0xffu) + j;
-      return true;
+    uint32_t off = 0, n = 0;
+    if ((uint32_t)r < nrows) {
+      if (mode == kRecUniform) n = rc.z;
+      else rec_row(rc, r, off, n);
     }
-    j -= n;
-    ++row;
+    if (r > 0) cum |= ((uint32_t)r < nrows ? start : 255u) << (8 * (r - 1));
+    k[r] = tb + (uint32_t)r * tx + off - start;
+    start += n;
   }
-  return false;
+  K = make_uint4(k[0], k[1], k[2], k[3]);
+  return start == c;
 }
 
 template <int MAXV>
-__global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+__global__ void __launch_bounds__(256, 4) k_emit_light(const __grid_constant__ Batch<MAXV> b, Ws ws) {
   constexpr int kRounds = kScanBlock / 256;   // rounds of 32 slots per warp
   __shared__ uint32_t warp_tot[8];
+  __shared__ uint4 s_K[8][32];                 // row tables of the round's small units
+  __shared__ uint32_t s_cum[8][32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const size_t slot0 = (size_t)blockIdx.x * kScanBlock + (size_t)wid * (32 * kRounds) + lane;
   const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
@@ -555,6 +584,14 @@ __global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batc
 #pragma unroll
   for (int r = 0; r < kRounds; ++r)
     rc[r] = cnt[r] ? ws.trec[unit[r]] : make_uint4(0u, 0u, 0u, 0u);
+  // the units whose rows are recomputed (taken by the whole warp later): their centre and
+  // extent brought into L2 now
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r)
+    if ((rc[r].y >> 16) == kRecCompute) {
+      prefetch_l2(ws.xy + unit[r]);
+      prefetch_l2(ws.ext + unit[r]);
+    }
   wsum = __reduce_add_sync(0xffffffffu, wsum);
   if (lane == 0) warp_tot[wid] = wsum;
   __syncthreads();
@@ -583,9 +620,20 @@ __global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batc
         rr = rc[q];
       }
     const uint32_t mode = rr.y >> 16;
-    const bool small = c && c <= kBigUnit && mode != kRecCompute;
+    // small units: their row table, for the lanes that write their pairs
+    bool small = false;
+    if (c && c <= kSmallTiles) {
+      const ViewP& V = b.views[view_of_unit(b, u)];
+      const uint32_t tx = V.tiles_x;
+      const uint32_t tb = V.tile_off + (rr.x >> 16) * tx + (rr.x & 0xffffu);
+      uint4 K;
+      uint32_t cum;
+      small = small_unit_rows(rr, c, tb, tx, K, cum);
+      s_K[wid][lane] = K;
+      s_cum[wid][lane] = cum;
+    }
     // one scan for both: all pairs (low 17 bits: a light block has at most 2^16) and the
-    // small units' pairs (high bits)
+    // small units' pairs (high bits: at most 32 x kSmallTiles)
     const uint32_t x = c | (small ? c : 0u) << 17;
     uint32_t incl = x;
 #pragma unroll
@@ -597,13 +645,7 @@ __global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batc
     const uint32_t vstart = (incl - x) >> 17;               // first small-pair number
     const uint32_t rtot = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t vtot = rtot >> 17;
-    // small units: the tile of the rectangle's first row and column, the view's tile columns
-    uint32_t tb = 0, tx = 0;
-    if (small) {
-      const ViewP& V = b.views[view_of_unit(b, u)];
-      tx = V.tiles_x;
-      tb = V.tile_off + (rr.x >> 16) * tx + (rr.x & 0xffffu);
-    }
+    __syncwarp();
     for (uint32_t i0 = 0; i0 < vtot; i0 += 32) {
       const uint32_t i = i0 + lane;
       int v = 0;   // the last lane whose first small-pair number is <= i
@@ -615,16 +657,12 @@ __global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batc
       const uint32_t j = i - __shfl_sync(0xffffffffu, vstart, v);
       const uint32_t pr = __shfl_sync(0xffffffffu, excl, v);
       const uint32_t uv = __shfl_sync(0xffffffffu, u, v);
-      const uint32_t tbv = __shfl_sync(0xffffffffu, tb, v);
-      const uint32_t txv = __shfl_sync(0xffffffffu, tx, v);
-      const uint32_t yv = __shfl_sync(0xffffffffu, rr.y, v);
-      const uint32_t zv = __shfl_sync(0xffffffffu, rr.z, v);
-      const uint32_t wv = __shfl_sync(0xffffffffu, rr.w, v);
       if (i < vtot) {
-        uint32_t row, col;
-        uint32_t key = 0xffffffffu;   // never a tile id: sorts after every tile, no range
-        if (small_unit_tile(yv, zv, wv, j, row, col)) key = tbv + row * txv + col;
-        else set_status(ws.status, FLOD_DEV_TILESET);
+        const uint4 K = s_K[wid][v];
+        const uint32_t cum = s_cum[wid][v];
+        const uint32_t row = (uint32_t)(j >= (cum & 0xffu)) + (uint32_t)(j >= ((cum >> 8) & 0xffu)) +
+                             (uint32_t)(j >= (cum >> 16));
+        const uint32_t key = (row == 0 ? K.x : row == 1 ? K.y : row == 2 ? K.z : K.w) + j;
         const unsigned long long p = base + pr + j;
         if (p < cap) {
           keys[p] = key;
@@ -632,30 +670,69 @@ __global__ void __launch_bounds__(256) k_emit_light(const __grid_constant__ Batc
         }
       }
     }
-    // a small unit whose rows hold more tiles than its count
-    if (small && (mode == kRecTable)) {
-      uint32_t sum = 0;
-#pragma unroll
-      for (int q = 0; q < kRecRows; ++q) {
-        const uint32_t h = ((q < 2 ? rr.z : rr.w) >> (16 * (q & 1))) & 0xffffu;
-        if ((uint32_t)q < (rr.y & 0xffffu)) sum += h >> 8;
+    __syncwarp();
+    // the other units: listed for k_emit_big (one warp per unit there)
+    const unsigned long long pos = base + excl;
+    const bool other = c && !small && pos < cap;
+    const uint32_t om = __ballot_sync(0xffffffffu, other);
+    if (om) {
+      uint32_t first = 0;
+      if (lane == 0) first = atomicAdd(&ws.plan[kPlanBigUnits], (uint32_t)__popc(om));
+      first = __shfl_sync(0xffffffffu, first, 0);
+      if (other) {
+        const uint32_t idx = first + (uint32_t)__popc(om & ((1u << lane) - 1u));
+        const BigUnits L = big_units(ws);
+        L.pos[idx] = (uint32_t)pos;
+        L.unit[idx] = u;
       }
-      if (sum != c) set_status(ws.status, FLOD_DEV_TILESET);
-    }
-    // the other units, by the whole warp
-    uint32_t todo = __ballot_sync(0xffffffffu, c && !small);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint32_t us = __shfl_sync(0xffffffffu, u, src);
-      const uint4 rcs = make_uint4(__shfl_sync(0xffffffffu, rr.x, src),
-                                   __shfl_sync(0xffffffffu, rr.y, src),
-                                   __shfl_sync(0xffffffffu, rr.z, src),
-                                   __shfl_sync(0xffffffffu, rr.w, src));
-      emit_unit_warp(b, ws, us, rcs, base + __shfl_sync(0xffffffffu, excl, src),
-                     __shfl_sync(0xffffffffu, c, src), keys, vals, cap);
     }
     base += rtot & 0x1ffffu;
+  }
+}
+
+// The units the light emission listed (more than kSmallTiles tiles, rows recomputed, or a
+// record that does not add up): each warp takes kBigPerWarp entries, its first lanes fetch
+// their units' data at once, then the warp writes the units one after the other.
+template <int MAXV>
+__global__ void __launch_bounds__(256) k_emit_big(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  constexpr uint32_t G = kBigPerWarp;
+  const uint32_t n = ws.plan[kPlanBigUnits];
+  const BigUnits L = big_units(ws);
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned long long cap = ws.pair_capacity;
+  const bool rows = b.cfg.extent_rule == 2;
+  for (uint32_t e0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; e0 < n; e0 += nw * G) {
+    // lanes 0..G-1 fetch one unit's data each, all requests in flight together
+    const uint32_t e = e0 + (uint32_t)lane;
+    uint32_t u = 0, pos = 0, c = 0;
+    uint4 rc = make_uint4(0u, 0u, 0u, 0u);
+    float2 xy = make_float2(0.f, 0.f);
+    float4 ext = make_float4(0.f, 0.f, 0.f, 0.f);
+    if ((uint32_t)lane < G && e < n) {
+      u = L.unit[e];
+      pos = L.pos[e];
+      c = ws.tiles_touched[u];
+      rc = ws.trec[u];
+      xy = ws.xy[u];
+      if (rows) {
+        ext = ws.ext[u];
+      } else {
+        const float r = ws.radius[u];
+        ext = make_float4(0.f, 0.f, r, r);
+      }
+    }
+    const int m = (int)min(G, n - e0);
+    for (int k = 0; k < m; ++k) {
+      const uint4 rk = make_uint4(__shfl_sync(0xffffffffu, rc.x, k), __shfl_sync(0xffffffffu, rc.y, k),
+                                  __shfl_sync(0xffffffffu, rc.z, k), __shfl_sync(0xffffffffu, rc.w, k));
+      const float2 xk = make_float2(__shfl_sync(0xffffffffu, xy.x, k), __shfl_sync(0xffffffffu, xy.y, k));
+      const float4 ek = make_float4(__shfl_sync(0xffffffffu, ext.x, k), __shfl_sync(0xffffffffu, ext.y, k),
+                                    __shfl_sync(0xffffffffu, ext.z, k), __shfl_sync(0xffffffffu, ext.w, k));
+      emit_unit_warp(b, ws, __shfl_sync(0xffffffffu, u, k), rk, xk, ek,
+                     __shfl_sync(0xffffffffu, pos, k), __shfl_sync(0xffffffffu, c, k), ws.keys[0],
+                     ws.vals[0], cap);
+    }
   }
 }
 
@@ -740,6 +817,7 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
   k_scan_blocks<<<1, 1024, 0, st>>>(ws, nblocks, d_pair_count);
   if (nblocks) {
     k_emit_light<MAXV><<<nblocks, 256, 0, st>>>(b, ws);
+    k_emit_big<MAXV><<<resident_small, 256, 0, st>>>(b, ws);
     k_emit<MAXV><<<resident_small, 256, 0, st>>>(b, ws, nblocks);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -112,6 +112,7 @@ constexpr int kPlanQueue = 41;       // render work-queue ticket counter (x2: fw
 constexpr int kPlanSlices = 43;      // number of key-emission slices
 constexpr int kPlanNPartsUnits = 44; // partitions of the unit-stage sort
 constexpr int kPlanFinalUnits = 45;  // buffer holding the depth-sorted unit order
+constexpr int kPlanBigUnits = 46;    // units the light emission leaves to k_emit_big
 constexpr int kEmitSlice = 4096;     // output positions per emission slice
 constexpr int kQueueHeader = 66;     // queue[0..32] bucket counts, [33..65] offsets, then tiles
 constexpr int kPlanEvalFwd = 48;     // uint64 running count of forward evaluations
@@ -168,14 +169,19 @@ __device__ __forceinline__ bool pixel_rect(float u, float v, float rx, float ry,
   return true;
 }
 
+// Tile sizes are powers of two (8, 16, 32 pixels: the configurations accepted), so the tile
+// of a (non-negative) pixel coordinate is a shift.
+__device__ __forceinline__ int tile_shift(int t) { return __ffs(t) - 1; }
+
 __device__ __forceinline__ bool tile_rect(float u, float v, float r, int W, int H, int tw,
                                           int th, int& tx0, int& tx1, int& ty0, int& ty1) {
   int px0, px1, py0, py1;
   if (!pixel_rect(u, v, r, r, W, H, px0, px1, py0, py1)) return false;
-  tx0 = px0 / tw;
-  tx1 = px1 / tw;
-  ty0 = py0 / th;
-  ty1 = py1 / th;
+  const int lw = tile_shift(tw), lh = tile_shift(th);
+  tx0 = px0 >> lw;
+  tx1 = px1 >> lw;
+  ty0 = py0 >> lh;
+  ty1 = py1 >> lh;
   return true;
 }
 
@@ -196,6 +202,7 @@ struct UnitTiles {
   int px0, px1, py0, py1;   // pixel rectangle (clamped to the image)
   int ty0, ty1;             // its tile rows
   int tw, th;
+  int lw;                   // log2 of the tile width
   bool rows;                // rule 2: per-row column ranges
 };
 
@@ -207,10 +214,12 @@ __device__ __forceinline__ bool unit_tiles(float u, float v, float4 e, int W, in
   t.e = e;
   t.ry2 = __fmul_rn(e.w, e.w);
   t.dyx = e.z > 0.f ? __fdiv_rn(__fmul_rn(e.x, t.ry2), e.z) : 0.f;
-  t.ty0 = t.py0 / th;
-  t.ty1 = t.py1 / th;
+  const int lh = tile_shift(th);
+  t.ty0 = t.py0 >> lh;
+  t.ty1 = t.py1 >> lh;
   t.tw = tw;
   t.th = th;
+  t.lw = tile_shift(tw);
   t.rows = rows;
   return true;
 }
@@ -234,8 +243,8 @@ __device__ __forceinline__ void rec_row(const uint4 r, int row, uint32_t& off, u
 // Tile columns [cx0, cx1] of tile row ty (ty0 <= ty <= ty1); false if the row has none.
 __device__ __forceinline__ bool unit_row(const UnitTiles& t, int ty, int& cx0, int& cx1) {
   if (!t.rows) {
-    cx0 = t.px0 / t.tw;
-    cx1 = t.px1 / t.tw;
+    cx0 = t.px0 >> t.lw;
+    cx1 = t.px1 >> t.lw;
     return true;
   }
   const int jy0 = max(ty * t.th, t.py0);
@@ -252,8 +261,8 @@ __device__ __forceinline__ bool unit_row(const UnitTiles& t, int ty, int& cx0, i
   const float c0 = fmaxf(ceilf(__fsub_rn(xl, 0.5f)), (float)t.px0);
   const float c1 = fminf(floorf(__fsub_rn(xr, 0.5f)), (float)t.px1);
   if (!(c0 <= c1)) return false;
-  cx0 = (int)c0 / t.tw;
-  cx1 = (int)c1 / t.tw;
+  cx0 = (int)c0 >> t.lw;
+  cx1 = (int)c1 >> t.lw;
   return true;
 }
 
@@ -299,6 +308,10 @@ __device__ __forceinline__ float splat_qmin(float o) {
 __device__ __forceinline__ float splat_alpha(float qs, float o, float& g) {
   g = ex2_approx(qs);
   return fminf(kAlphaMax, __fmul_rn(o, g));
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // Tile count of every depth-sorted unit slot (written by the binning after the unit sort,

@@ -271,13 +271,13 @@ __global__ void __launch_bounds__(kStageN) k_preprocess(const __grid_constant__ 
   // tile count: the rows of the tile rectangle; the first rows also go to the tile record
   uint4 rec = make_uint4(0u, 0u, 0u, 0u);
   if (ok) {
-    const int tx0 = t.px0 / t.tw;
+    const int tx0 = t.px0 >> t.lw;
     const uint32_t nrows = (uint32_t)(t.ty1 - t.ty0 + 1);
     uint32_t mode = kRecTable;
     if (!t.rows) {
-      touched = nrows * (uint32_t)(t.px1 / t.tw - tx0 + 1);
+      touched = nrows * (uint32_t)((t.px1 >> t.lw) - tx0 + 1);
       mode = kRecUniform;
-      rec.z = (uint32_t)(t.px1 / t.tw - tx0 + 1);
+      rec.z = (uint32_t)((t.px1 >> t.lw) - tx0 + 1);
     } else {
       if (nrows > (uint32_t)kRecRows) mode = kRecCompute;
       for (int ty = t.ty0; ty <= t.ty1; ++ty) {
