@@ -310,6 +310,46 @@ __device__ __forceinline__ float splat_alpha(float qs, float o, float& g) {
   return fminf(kAlphaMax, __fmul_rn(o, g));
 }
 
+// ---------------------------------------------------------------------------------------
+// Bulk (TMA) copies global -> shared memory completing on an mbarrier
+// ---------------------------------------------------------------------------------------
+constexpr uint32_t kBulkSpinLimit = 1u << 26;   // polls of a barrier before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// One arrival expected per phase; the fence makes the initialisation visible to the copies.
+__device__ __forceinline__ void bulk_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Arrive on the barrier announcing the bytes the copies of this phase bring.
+__device__ __forceinline__ void bulk_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Waits for the barrier's phase of the given parity to complete; false if the bound ran out.
+__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kBulkSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }

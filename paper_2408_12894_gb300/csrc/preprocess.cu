@@ -150,7 +150,6 @@ __device__ __forceinline__ void sh_colour(const SetP& S, uint32_t gi, const View
 // the byte count and issues one cp.async.bulk per parameter array; every thread then waits
 // on the barrier (bounded) and reads its Gaussian from shared memory.
 constexpr int kStageN = 128;
-constexpr uint32_t kBulkSpinLimit = 1u << 26;
 struct PreStage {
   float sh[kStageN * 48];
   float means[kStageN * 3];
@@ -159,28 +158,6 @@ struct PreStage {
   float logit[kStageN];
   unsigned long long bar;
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-
-// Waits for phase 0 of the barrier; false if the bound ran out.
-__device__ __forceinline__ bool bulk_wait(uint32_t bar) {
-  for (uint32_t i = 0; i < kBulkSpinLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
-        " selp.b32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(bar) : "memory");
-    if (done) return true;
-  }
-  return false;
-}
 
 template <int MAXV>
 __global__ void __launch_bounds__(kStageN) k_preprocess(const __grid_constant__ Batch<MAXV> b, Ws ws) {
@@ -199,10 +176,8 @@ __global__ void __launch_bounds__(kStageN) k_preprocess(const __grid_constant__ 
     const int K = (S0.deg + 1) * (S0.deg + 1);
     const uint32_t shb = kStageN * 12u * (uint32_t)K;   // 3 K floats per Gaussian
     if (threadIdx.x == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                   ::"r"(bar), "r"(shb + kStageN * (12u + 16u + 12u + 4u)) : "memory");
+      bulk_init(bar);
+      bulk_expect(bar, shb + kStageN * (12u + 16u + 12u + 4u));
       bulk_load(stg.sh, S0.sh + 3ull * K * local0, shb, bar);
       bulk_load(stg.means, S0.means + 3ull * local0, kStageN * 12u, bar);
       bulk_load(stg.quats, S0.quats + 4ull * local0, kStageN * 16u, bar);
@@ -210,9 +185,9 @@ __global__ void __launch_bounds__(kStageN) k_preprocess(const __grid_constant__ 
       bulk_load(stg.logit, S0.logit + local0, kStageN * 4u, bar);
     }
     __syncthreads();
-    if (!bulk_wait(bar)) {
+    if (!bulk_wait(bar, 0)) {
       set_status(ws.status, FLOD_DEV_TIMEOUT);
-      if (!bulk_wait(bar)) return;   // copies still in flight: leave the shared memory alone
+      if (!bulk_wait(bar, 0)) return;   // copies still in flight: leave the shared memory alone
     }
   }
   int si = 0;
