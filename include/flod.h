@@ -152,7 +152,7 @@ typedef struct {
   size_t hist;          /* radix-sort digit histograms */
   size_t counts;        /* uint32 [512][partitions]: radix sort, per-partition digit counts */
   size_t ranges;        /* uint32x2 [tiles] [start, end) in the sorted pair list */
-  size_t grad2d;        /* float4 [units][3]: (du, dv, dopacity, 0), (da, db, dc, 0), (dr, dg, db, 0) */
+  size_t grad2d;        /* float [units][9]: du, dv, dopacity, da, db, dc, dr, dg, db */
   size_t queue;         /* uint32 [tiles + 128]: 66 header words, then the largest-first tile order */
   uint64_t units;       /* total units (each view's capacity rounded up to 1024) */
   uint64_t tiles;       /* total tiles over all views */

@@ -168,7 +168,7 @@ flod_status make_plan(const flod_gaussians* sets, int n_sets, const flod_view* v
   L.hist = take(4 * kPlanPasses * kRadixBins);
   L.counts = take(4ull * P.max_parts * kRadixBins);
   L.ranges = take(8 * t);
-  L.grad2d = take(48 * u);
+  L.grad2d = take(36 * u);
   L.queue = take(4 * (t + 128));
   L.total = off;
   L.units = u;
@@ -204,7 +204,7 @@ Ws ws_ptrs(void* base, const Plan& P) {
   w.hist = reinterpret_cast<uint32_t*>(b + L.hist);
   w.counts = reinterpret_cast<uint32_t*>(b + L.counts);
   w.ranges = reinterpret_cast<uint2*>(b + L.ranges);
-  w.grad2d = reinterpret_cast<float4*>(b + L.grad2d);
+  w.grad2d = reinterpret_cast<float*>(b + L.grad2d);
   w.queue = reinterpret_cast<uint32_t*>(b + L.queue);
   w.pair_capacity = L.pair_capacity;
   w.max_parts = P.max_parts;
@@ -420,7 +420,7 @@ flod_status flod_blend_bwd(const flod_gaussians* sets, int n_sets, const flod_vi
   if (s != FLOD_OK) return s;
   const Ws w = ws_ptrs(ws, P);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (P.L.units && cudaMemsetAsync(w.grad2d, 0, 48 * P.L.units, st) != cudaSuccess)
+  if (P.L.units && cudaMemsetAsync(w.grad2d, 0, 36 * P.L.units, st) != cudaSuccess)
     return FLOD_ERR_CUDA;
   const bool pers = cfg->persistent != 0;
   return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {

@@ -92,7 +92,7 @@ struct Ws {
   uint32_t* hist;
   uint32_t* counts;        // radix sort: per-partition digit counts, digit-major
   uint2* ranges;
-  float4* grad2d;
+  float* grad2d;           // per unit 9 floats: du, dv, dopacity, da, db, dc, dr, dg, db
   uint32_t* queue;
   uint64_t pair_capacity;
   uint32_t max_parts;

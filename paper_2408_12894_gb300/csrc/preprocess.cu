@@ -361,9 +361,10 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
     if (mode == kGradOverwrite) zero_grads(GR, gi, K, S.deg);
     return;
   }
-  const float4 g0 = ws.grad2d[3ull * u];      // du, dv, dopacity
-  const float4 g1 = ws.grad2d[3ull * u + 1];  // da, db, dc
-  const float4 g2 = ws.grad2d[3ull * u + 2];  // dr, dg, db
+  const float* gr = ws.grad2d + 9ull * u;
+  const float3 g0 = make_float3(gr[0], gr[1], gr[2]);   // du, dv, dopacity
+  const float3 g1 = make_float3(gr[3], gr[4], gr[5]);   // da, db, dc
+  const float3 g2 = make_float3(gr[6], gr[7], gr[8]);   // dr, dg, db
   Geom G;
   geometry(S, gi, V, b.cfg, G);
 

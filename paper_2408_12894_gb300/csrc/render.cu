@@ -226,11 +226,11 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
 // ---------------------------------------------------------------------------------------
 
 // Sums nine per-lane values over the warp and adds each total to its slot of a unit's
-// 2D-gradient record (du, dv, dop | da, db, dc | dr, dg, db). A transposing butterfly: at
+// 2D-gradient record (du, dv, dop, da, db, dc, dr, dg, db). A transposing butterfly: at
 // each shuffle distance a lane keeps one half of its values, sends the other half to its
 // partner and adds what it receives, so after distances 16, 8, 4, 2 every lane holds one
 // partial sum; distance 1 completes it. 12 shuffles instead of 45.
-__device__ __forceinline__ void warp_reduce_add9(float (&v)[9], float4* rec) {
+__device__ __forceinline__ void warp_reduce_add9(float (&v)[9], float* rec) {
   const int lane = threadIdx.x & 31;
   const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
   float w[5];
@@ -265,7 +265,7 @@ __device__ __forceinline__ void warp_reduce_add9(float (&v)[9], float4* rec) {
   const int i2 = (b3 ? 3 : 0) + i3;             // index into w (valid < 5)
   const int i1 = (b4 ? 5 : 0) + i2;             // original index (valid < 9)
   if ((lane & 1) == 0 && i3 < 3 && i2 < 5 && i1 < 9 && z != 0.f)
-    atomicAdd(reinterpret_cast<float*>(rec) + i1 + i1 / 3, z);
+    atomicAdd(rec + i1, z);
 }
 
 // The backward stages at most 128 Gaussians per batch (the forward up to 256): half the
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
           acc[6] = -(nR0.x + nR0.y);
           acc[7] = -(nR1.x + nR1.y);
           acc[8] = -(nR2.x + nR2.y);
-          warp_reduce_add9(acc, ws.grad2d + 3ull * s_id[k]);
+          warp_reduce_add9(acc, ws.grad2d + 9ull * s_id[k]);
         }
       }
       bend = bstart;
