@@ -16,7 +16,8 @@
 // dy^2, dx, dy; dx is fixed per thread (one column), so a thread sums only the moments
 // (1, dy, dy^2) of dL/dq over its PIX pixels and expands them once per Gaussian. A warp then
 // reduces the nine per-Gaussian gradients with a transposing butterfly and the owning lanes
-// add them with atomics; warps where no pixel touches the Gaussian skip the reduction.
+// add them with atomics. A warp none of whose pixels blends a Gaussian skips it after one
+// vote; the others take every pixel pair without branching (G = 0 where a pixel does not blend).
 //
 // Both walks take a thread's pixels in pairs (rows 2p, 2p + 1 of its column): the pair's
 // values sit in the two halves of a float2 and every operation on them is one packed
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
       live[j] = px < V.width && py0 + j < V.height;
       done = done && !live[j];
     }
+    done = __all_sync(0xffffffffu, done);   // warps walk and stop together (votes below)
     uint32_t pos = 0;   // Gaussians of the tile list walked so far
     for (uint32_t start = rg.x; start < rg.y; start += batch) {
       if (__syncthreads_count(done) == nthr) break;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
       }
       __syncthreads();
       if (!done) {
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < cnt; ++k) {
           const float4 sx = s_x[k];
           const float4 sy = s_y[k];
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
             const float2 q = fma2(dy, fma2(cz, dy, t1), t0);
             const bool pa = live[2 * p] && !(q.x < sx.w);       // live and alpha >= 1/255
             const bool pb = live[2 * p + 1] && !(q.y < sx.w);
-            if (!(pa || pb)) continue;
+            if (!__any_sync(0xffffffffu, pa || pb)) continue;   // no pixel of the warp blends
             const float4 so = s_o[k];
             float2 g;
             g.x = pa ? ex2_approx(q.x) : 0.f;
@@ -181,11 +183,11 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
             last[2 * p + 1] = bb ? pos : last[2 * p + 1];
             blended += (uint32_t)ba + (uint32_t)bb;
           }
-          if ((k & 7) == 7) {              // every eighth splat: leave once all pixels stopped
+          if ((k & 7) == 7) {     // every eighth splat: the warp leaves once all its pixels stopped
             bool any_live = false;
 #pragma unroll
             for (int j = 0; j < PIX; ++j) any_live = any_live || live[j];
-            if (!any_live) {
+            if (!__any_sync(0xffffffffu, any_live)) {
               done = true;
               break;
             }
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
           bool any_live = false;
 #pragma unroll
           for (int j = 0; j < PIX; ++j) any_live = any_live || live[j];
-          done = !any_live;
+          done = !__any_sync(0xffffffffu, any_live);
         }
       }
     }
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         s_co[k] = co;
       }
       __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
       for (int k = cnt - 1; k >= 0; --k) {
         const uint32_t pos = bstart - rg.x + (uint32_t)k + 1u;
         const float4 sx = s_x[k];
@@ -369,21 +371,29 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
         const float2 t0 = dup2(__fmul_rn(__fmul_rn(sx.y, dx), dx));
         const float2 t1 = dup2(__fmul_rn(sx.z, dx));
         const float2 nmy = make_float2(sy.x, sy.y), cz = make_float2(sy.z, sy.w);
-        // this thread's sums over its pixels (pairwise): colour gradient (negated), and the
-        // moments E0 = sum e, E1 = sum e dy, E2 = sum e dy^2 of e = G dL/dalpha (unclamped)
-        float2 nR0 = dup2(0.f), nR1 = dup2(0.f), nR2 = dup2(0.f);
-        float2 E0 = dup2(0.f), E1 = dup2(0.f), E2 = dup2(0.f);
+        // which of this thread's pixels blend the splat; a warp none of whose pixels does
+        // skips it (one vote), the others take every pair, non-blending pixels with G = 0
+        float2 dyv[NP], qv[NP];
+        bool pav[NP], pbv[NP];
         bool any = false;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-          const float2 dy = add2(FY[p], nmy);
-          const float2 q = fma2(dy, fma2(cz, dy, t1), t0);
-          const bool pa = pos <= last[2 * p] && !(q.x < sx.w);      // alpha >= 1/255
-          const bool pb = pos <= last[2 * p + 1] && !(q.y < sx.w);
-          if (!(pa || pb)) continue;
-          any = true;
-          const float4 so = s_o[k];
-          const float4 sc = s_c[k];
+          dyv[p] = add2(FY[p], nmy);
+          qv[p] = fma2(dyv[p], fma2(cz, dyv[p], t1), t0);
+          pav[p] = pos <= last[2 * p] && !(qv[p].x < sx.w);      // alpha >= 1/255
+          pbv[p] = pos <= last[2 * p + 1] && !(qv[p].y < sx.w);
+          any = any || pav[p] || pbv[p];
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        const float4 so = s_o[k];
+        const float4 sc = s_c[k];
+        // this thread's sums over its pixels (pairwise): colour gradient (negated), and the
+        // moments E0 = sum e, E1 = sum e dy, E2 = sum e dy^2 of e = G dL/dalpha (unclamped)
+        float2 nR0, nR1, nR2, E0, E1, E2;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const float2 dy = dyv[p], q = qv[p];
+          const bool pa = pav[p], pb = pbv[p];
           float2 g;                                   // G = 2^q' (0: pixel not blended)
           g.x = pa ? ex2_approx(q.x) : 0.f;
           g.y = pb ? ex2_approx(q.y) : 0.f;
@@ -394,9 +404,6 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
                                           pb ? rcp_approx(oma.y) : 1.f);
           T[p] = mul2(T[p], ioma);                                 // T in front of this splat
           const float2 nw = mul2(na, T[p]);                        // -alpha T
-          nR0 = fma2(nw, G0[p], nR0);
-          nR1 = fma2(nw, G1[p], nR1);
-          nR2 = fma2(nw, G2[p], nR2);
           const float2 gc = fma2(G2[p], make_float2(sc.z, sc.w),
                                  fma2(G1[p], make_float2(sc.x, sc.y),
                                       mul2(G0[p], make_float2(so.z, so.w))));
@@ -406,11 +413,23 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
                                         nog.y > -kAlphaMax ? g.y : 0.f);
           const float2 e = mul2(ge, dal);
           const float2 ed = mul2(e, dy);
-          E0 = add2(E0, e);
-          E1 = add2(E1, ed);
-          E2 = fma2(ed, dy, E2);
+          if (p == 0) {
+            nR0 = mul2(nw, G0[p]);
+            nR1 = mul2(nw, G1[p]);
+            nR2 = mul2(nw, G2[p]);
+            E0 = e;
+            E1 = ed;
+            E2 = mul2(ed, dy);
+          } else {
+            nR0 = fma2(nw, G0[p], nR0);
+            nR1 = fma2(nw, G1[p], nR1);
+            nR2 = fma2(nw, G2[p], nR2);
+            E0 = add2(E0, e);
+            E1 = add2(E1, ed);
+            E2 = fma2(ed, dy, E2);
+          }
         }
-        if (__any_sync(0xffffffffu, any)) {
+        {
           // dL/dq = -o/2 e; q = a dx^2 + 2 b dx dy + c dy^2, dq/du = -2 (a dx + b dy), ...
           const float4 co = s_co[k];
           const float hq = -0.5f * co.w;
