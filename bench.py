@@ -69,7 +69,7 @@ def measured_traffic(kernel: str):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="flod", choices=["flod", "reference"])
     ap.add_argument("--small", action="store_true", help="300k-Gaussian level (smoke runs)")
@@ -106,7 +106,7 @@ def clock_sampler(dev_index: int):
          "clocks_event_reasons.sw_power_cap")
     try:
         p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
-                              "--format=csv,noheader,nounits", "-lms", "200"],
+                              "--format=csv,noheader,nounits", "-lms", "50"],
                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
     except OSError:
         return None
@@ -225,7 +225,12 @@ def run_reference(a):
     g = make_level(a.small, a.scale)
     g["s_opt"] = adjust_chain_numpy(g["s_opt"], level_counts(a.small, a.scale))
     cam = synth.level_camera()
-    ost = OracleStep(g, cam, synth.LEVEL_SMIN[-1], slice_n=20_000, tiles=3)
+    # each step times a bounded sample, smaller for long runs so that the whole run stays
+    # within a few minutes (about 60 samples' worth of the 20,000-Gaussian slice)
+    n_samples = max(a.steps + a.warmup, 1)
+    ost = OracleStep(g, cam, synth.LEVEL_SMIN[-1],
+                     slice_n=max(4_000, min(20_000, 20_000 * 60 // n_samples)),
+                     tiles=3 if n_samples <= 60 else 1)
     for _ in range(a.warmup):
         ost.step_seconds()
     secs = [ost.step_seconds() for _ in range(a.steps)]
