@@ -30,6 +30,7 @@ __device__ __forceinline__ BigUnits big_units(const Ws& ws) { return {ws.keys[1]
 // is also stored in slot order (in the unit sort's key buffer 0, free once the sort is done;
 // 0 past the visible units), so that the emission reads it without a gather.
 __global__ void __launch_bounds__(256) k_block_sums(Ws ws) {
+  pdl_entry();
   __shared__ uint32_t red[8];
   const uint32_t* order = ws.uvals[ws.plan[kPlanFinalUnits]];
   const uint32_t nvis = visible_units(ws);
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(256) k_block_sums(Ws ws) {
 // One CTA: exclusive scan of the block sums, pair total, partition count, counters reset.
 __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
                                                       unsigned long long* user_count) {
+  pdl_entry();
   __shared__ unsigned long long warp_tot[32];
   __shared__ uint32_t warp_sl[32];
   __shared__ unsigned long long carry_s;
@@ -199,6 +201,7 @@ __device__ __forceinline__ uint32_t block_excl_sum(uint32_t x, uint32_t* warp_to
 template <int MAXV>
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV> b, Ws ws,
                                               uint32_t nblocks) {
+  pdl_entry();
   __shared__ uint32_t s_pre[kScanBlock + 1];     // slot start positions (block-relative)
   __shared__ uint32_t s_row[kScanBlock + 1];     // first item of each slot
   __shared__ uint32_t s_unit[kScanBlock];
@@ -564,6 +567,7 @@ __device__ __forceinline__ bool small_unit_rows(const uint4& rc, uint32_t c, uin
 
 template <int MAXV>
 __global__ void __launch_bounds__(256, 4) k_emit_light(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  pdl_entry();
   constexpr int kRounds = kScanBlock / 256;   // rounds of 32 slots per warp
   __shared__ uint32_t warp_tot[8];
   __shared__ uint4 s_K[8][32];                 // row tables of the round's small units
@@ -619,7 +623,6 @@ __global__ void __launch_bounds__(256, 4) k_emit_light(const __grid_constant__ B
         u = unit[q];
         rr = rc[q];
       }
-    const uint32_t mode = rr.y >> 16;
     // small units: their row table, for the lanes that write their pairs
     bool small = false;
     if (c && c <= kSmallTiles) {
@@ -695,6 +698,7 @@ __global__ void __launch_bounds__(256, 4) k_emit_light(const __grid_constant__ B
 // their units' data at once, then the warp writes the units one after the other.
 template <int MAXV>
 __global__ void __launch_bounds__(256) k_emit_big(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  pdl_entry();
   constexpr uint32_t G = kBigPerWarp;
   const uint32_t n = ws.plan[kPlanBigUnits];
   const BigUnits L = big_units(ws);
@@ -739,6 +743,7 @@ __global__ void __launch_bounds__(256) k_emit_big(const __grid_constant__ Batch<
 // Tile ranges from the sorted tile keys: four consecutive keys per thread (one 16-byte load),
 // a range starts or ends where a key differs from its neighbour.
 __global__ void __launch_bounds__(256) k_ranges(Ws ws, uint32_t n_tiles) {
+  pdl_entry();
   const unsigned long long P0 = *ws.pair_count;
   const uint32_t P = (uint32_t)(P0 < ws.pair_capacity ? P0 : ws.pair_capacity);
   const uint32_t* keys = ws.keys[ws.plan[kPlanFinal]];
@@ -768,6 +773,7 @@ __global__ void __launch_bounds__(256) k_ranges(Ws ws, uint32_t n_tiles) {
 }
 
 __global__ void __launch_bounds__(256) k_queue_count(Ws ws, uint32_t n_tiles) {
+  pdl_entry();
   __shared__ uint32_t h[33];
   if (threadIdx.x < 33) h[threadIdx.x] = 0;
   __syncthreads();
@@ -781,6 +787,7 @@ __global__ void __launch_bounds__(256) k_queue_count(Ws ws, uint32_t n_tiles) {
 }
 
 __global__ void k_queue_offsets(Ws ws) {
+  pdl_entry();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
     for (int bkt = 32; bkt >= 0; --bkt) {
@@ -791,6 +798,7 @@ __global__ void k_queue_offsets(Ws ws) {
 }
 
 __global__ void __launch_bounds__(256) k_queue_fill(Ws ws, uint32_t n_tiles) {
+  pdl_entry();
   for (uint32_t t = blockIdx.x * 256u + threadIdx.x; t < n_tiles; t += gridDim.x * 256u) {
     const uint2 r = ws.ranges[t];
     const uint32_t n = r.y - r.x;
@@ -812,26 +820,26 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
   }
   if (nblocks) {
     if ((e = launch_unit_sort(ws, resident_small, resident_sort, st)) != cudaSuccess) return e;
-    k_block_sums<<<nblocks, 256, 0, st>>>(ws);
+    launch_k(k_block_sums, dim3(nblocks), dim3(256), 0, st, ws);
   }
-  k_scan_blocks<<<1, 1024, 0, st>>>(ws, nblocks, d_pair_count);
+  launch_k(k_scan_blocks, dim3(1), dim3(1024), 0, st, ws, nblocks, d_pair_count);
   if (nblocks) {
-    k_emit_light<MAXV><<<nblocks, 256, 0, st>>>(b, ws);
-    k_emit_big<MAXV><<<resident_small, 256, 0, st>>>(b, ws);
-    k_emit<MAXV><<<resident_small, 256, 0, st>>>(b, ws, nblocks);
+    launch_k(k_emit_light<MAXV>, dim3(nblocks), dim3(256), 0, st, b, ws);
+    launch_k(k_emit_big<MAXV>, dim3(resident_small), dim3(256), 0, st, b, ws);
+    launch_k(k_emit<MAXV>, dim3(resident_small), dim3(256), 0, st, b, ws, nblocks);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_pair_sort(ws, n_passes, tile_bits, resident_small, resident_sort, st)) !=
       cudaSuccess)
     return e;
-  k_ranges<<<resident_small, 256, 0, st>>>(ws, b.tiles);
+  launch_k(k_ranges, dim3(resident_small), dim3(256), 0, st, ws, b.tiles);
   if (build_queue && b.tiles) {
     if ((e = cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t) * kQueueHeader, st)) != cudaSuccess)
       return e;
     const uint32_t g = min((uint32_t)resident_small, (b.tiles + 255) / 256);
-    k_queue_count<<<g, 256, 0, st>>>(ws, b.tiles);
-    k_queue_offsets<<<1, 32, 0, st>>>(ws);
-    k_queue_fill<<<g, 256, 0, st>>>(ws, b.tiles);
+    launch_k(k_queue_count, dim3(g), dim3(256), 0, st, ws, b.tiles);
+    launch_k(k_queue_offsets, dim3(1), dim3(32), 0, st, ws);
+    launch_k(k_queue_fill, dim3(g), dim3(256), 0, st, ws, b.tiles);
   }
   return cudaGetLastError();
 }

@@ -311,6 +311,17 @@ __device__ __forceinline__ float splat_alpha(float qs, float o, float& g) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Programmatic dependent launch. Every kernel is launched so that it may be scheduled while
+// the previous kernel of its stream drains (launch_k). Its first statement waits for that
+// kernel to complete and its writes to be visible (before any global memory access, so the
+// order of the stream is kept), then lets the next kernel be scheduled.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------------------
 // Bulk (TMA) copies global -> shared memory completing on an mbarrier
 // ---------------------------------------------------------------------------------------
 constexpr uint32_t kBulkSpinLimit = 1u << 26;   // polls of a barrier before giving up

@@ -5,6 +5,24 @@
 
 namespace flod {
 
+// Launches a kernel (which starts with pdl_entry) with programmatic stream serialization:
+// it may be scheduled while the stream's previous kernel finishes.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // How the preprocess backward writes a set's gradients.
 enum GradMode : int { kGradAccumulate = 0, kGradAtomic = 1, kGradOverwrite = 2 };
 

@@ -161,6 +161,7 @@ struct PreStage {
 
 template <int MAXV>
 __global__ void __launch_bounds__(kStageN) k_preprocess(const __grid_constant__ Batch<MAXV> b, Ws ws) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char pre_smem[];
   PreStage& stg = *reinterpret_cast<PreStage*>(pre_smem);
   const uint32_t u = blockIdx.x * (uint32_t)kStageN + threadIdx.x;
@@ -346,6 +347,7 @@ __device__ __forceinline__ void zero_grads(const flod_grads& GR, uint32_t gi, in
 template <int MAXV>
 __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ Batch<MAXV> b,
                                                         Ws ws, GradTable gt) {
+  pdl_entry();
   const uint32_t u = blockIdx.x * 128u + threadIdx.x;
   if (u >= b.units) return;
   const int vi = view_of_unit(b, u);
@@ -532,7 +534,7 @@ cudaError_t launch_preprocess(const Batch<MAXV>& b, const Ws& ws, cudaStream_t s
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_preprocess<MAXV><<<(b.units + kStageN - 1) / kStageN, kStageN, sizeof(PreStage), st>>>(b, ws);
+  launch_k(k_preprocess<MAXV>, dim3((b.units + kStageN - 1) / kStageN), dim3(kStageN), sizeof(PreStage), st, b, ws);
   return cudaGetLastError();
 }
 
@@ -540,7 +542,7 @@ template <int MAXV>
 cudaError_t launch_preprocess_bwd(const Batch<MAXV>& b, const Ws& ws, const GradTable& gt,
                                   cudaStream_t st) {
   if (b.units == 0) return cudaSuccess;
-  k_preprocess_bwd<MAXV><<<(b.units + 127) / 128, 128, 0, st>>>(b, ws, gt);
+  launch_k(k_preprocess_bwd<MAXV>, dim3((b.units + 127) / 128), dim3(128), 0, st, b, ws, gt);
   return cudaGetLastError();
 }
 

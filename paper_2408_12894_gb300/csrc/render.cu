@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_fwd(const __grid_constant_
                                                           Ws ws, float* __restrict__ out_rgb,
                                                           float* __restrict__ out_T,
                                                           uint32_t* __restrict__ out_nc) {
+  pdl_entry();
   static_assert(PIX % 2 == 0, "pixels are walked in pairs");
   constexpr int NP = PIX / 2;
   __shared__ float4 s_x[256];     // (mean x, a', 2b', q'_min)
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
                                                           Ws ws, const float* __restrict__ dL,
                                                           const float* __restrict__ fwd_T,
                                                           const uint32_t* __restrict__ fwd_nc) {
+  pdl_entry();
   static_assert(PIX % 2 == 0, "pixels are walked in pairs");
   constexpr int NP = PIX / 2;
   // per staged Gaussian: the scalars of its column terms, and the operands the pixel pairs
@@ -476,9 +478,9 @@ static cudaError_t fwd_launch(const Batch<MAXV>& b, const Ws& ws, float* out_rgb
     static int cached = 0;
     if (!cached) cached = resident_ctas((const void*)k_render_fwd<MAXV, PIX, true>, thr, resident);
     const uint32_t grid = min((uint32_t)cached, b.tiles);
-    k_render_fwd<MAXV, PIX, true><<<grid, thr, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
+    launch_k(k_render_fwd<MAXV, PIX, true>, dim3(grid), dim3(thr), 0, st, b, ws, out_rgb, out_T, out_nc);
   } else {
-    k_render_fwd<MAXV, PIX, false><<<b.tiles, thr, 0, st>>>(b, ws, out_rgb, out_T, out_nc);
+    launch_k(k_render_fwd<MAXV, PIX, false>, dim3(b.tiles), dim3(thr), 0, st, b, ws, out_rgb, out_T, out_nc);
   }
   return cudaGetLastError();
 }
@@ -494,9 +496,9 @@ static cudaError_t bwd_launch(const Batch<MAXV>& b, const Ws& ws, const float* d
     static int cached = 0;
     if (!cached) cached = resident_ctas((const void*)k_render_bwd<MAXV, PIX, true>, thr, resident);
     const uint32_t grid = min((uint32_t)cached, b.tiles);
-    k_render_bwd<MAXV, PIX, true><<<grid, thr, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
+    launch_k(k_render_bwd<MAXV, PIX, true>, dim3(grid), dim3(thr), 0, st, b, ws, dL, fwd_T, fwd_nc);
   } else {
-    k_render_bwd<MAXV, PIX, false><<<b.tiles, thr, 0, st>>>(b, ws, dL, fwd_T, fwd_nc);
+    launch_k(k_render_bwd<MAXV, PIX, false>, dim3(b.tiles), dim3(thr), 0, st, b, ws, dL, fwd_T, fwd_nc);
   }
   return cudaGetLastError();
 }

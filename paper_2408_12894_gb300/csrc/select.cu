@@ -45,6 +45,7 @@ __device__ __forceinline__ int level_of_block(const SelP& s, uint32_t blk) {
 
 __global__ void __launch_bounds__(kSelThreads) k_sel_count(const __grid_constant__ SelP s,
                                                            uint32_t* counts) {
+  pdl_entry();
   __shared__ uint32_t red[kSelThreads / 32];
   const int lv = level_of_block(s, blockIdx.x);
   const uint32_t i0 = blockIdx.x * (uint32_t)kSelBlock - s.start[lv];
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_count(const __grid_constant
 
 __global__ void __launch_bounds__(1024) k_sel_scan(uint32_t* counts, uint32_t nblocks,
                                                    uint32_t* d_count) {
+  pdl_entry();
   __shared__ uint32_t wt[32];
   __shared__ uint32_t carry_s;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(1024) k_sel_scan(uint32_t* counts, uint32_t nb
 __global__ void __launch_bounds__(kSelThreads) k_sel_write(const __grid_constant__ SelP s,
                                                            const uint32_t* offsets, uint32_t* out,
                                                            uint32_t cap) {
+  pdl_entry();
   __shared__ uint32_t wcnt[kSelThreads / 32];
   __shared__ uint32_t base_s;
   const int lv = level_of_block(s, blockIdx.x);
@@ -155,9 +158,9 @@ cudaError_t launch_select(const SetP* levels, int n_levels, const float* lo, con
   if (n_blocks == 0) {
     return cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
   }
-  k_sel_count<<<n_blocks, kSelThreads, 0, st>>>(s, scratch);
-  k_sel_scan<<<1, 1024, 0, st>>>(scratch, n_blocks, d_count);
-  k_sel_write<<<n_blocks, kSelThreads, 0, st>>>(s, scratch, out, cap);
+  launch_k(k_sel_count, dim3(n_blocks), dim3(kSelThreads), 0, st, s, scratch);
+  launch_k(k_sel_scan, dim3(1), dim3(1024), 0, st, scratch, n_blocks, d_count);
+  launch_k(k_sel_write, dim3(n_blocks), dim3(kSelThreads), 0, st, s, scratch, out, cap);
   return cudaGetLastError();
 }
 
@@ -169,6 +172,7 @@ uint32_t select_blocks(const int* ns, int n_levels) {
 
 // Eq. 5 in float32 with the library exp/log (full precision).
 __global__ void k_adjust_scale(float* s_opt, int64_t n, float s_cur, float s_next) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     s_opt[i] = logf(expf(s_opt[i]) + (s_cur - s_next));
@@ -179,7 +183,7 @@ cudaError_t launch_adjust_scale(float* s_opt, int64_t n, float s_cur, float s_ne
   if (n == 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  k_adjust_scale<<<(unsigned)blocks, 256, 0, st>>>(s_opt, n, s_cur, s_next);
+  launch_k(k_adjust_scale, dim3((unsigned)blocks), dim3(256), 0, st, s_opt, n, s_cur, s_next);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,7 @@ __device__ __forceinline__ const uint32_t* src_keys(const Stage& s, int src) {
 // are positive, so the bits order like the values, and the difference keeps that order with
 // fewer significant bits: digits above them are skipped), value = unit index.
 __global__ void __launch_bounds__(256) k_vis_count(Ws ws) {
+  pdl_entry();
   __shared__ uint32_t red[3][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t i4 = blockIdx.x * 256u + threadIdx.x;
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(256) k_vis_count(Ws ws) {
 }
 
 __global__ void __launch_bounds__(1024) k_vis_scan(Ws ws, Stage st, uint32_t nblocks) {
+  pdl_entry();
   __shared__ uint32_t warp_tot[32], warp_lo[32], warp_hi[32];
   __shared__ uint32_t s_carry, s_lo, s_hi;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(1024) k_vis_scan(Ws ws, Stage st, uint32_t nbl
 }
 
 __global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st) {
+  pdl_entry();
   __shared__ uint32_t red[8];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t u0 = blockIdx.x * 1024u + 4u * tid;
@@ -185,6 +188,7 @@ __global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st) {
 
 // Phase 1: digit histogram of every partition, stored digit-major.
 __global__ void __launch_bounds__(256) k_count(Ws ws, Stage st, int digit) {
+  pdl_entry();
   __shared__ uint32_t h[kRadixBins];
   if (!digit_live(ws, st, digit)) return;
   const int slot = st.slot0 + digit;
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(256) k_count(Ws ws, Stage st, int digit) {
 // in place and its total; the last CTA to finish writes the digit bases and the pass plan.
 constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) k_scan(Ws ws, Stage st, int digit, int last) {
+  pdl_entry();
   __shared__ uint32_t warp_tot[kScanThreads / 32];
   __shared__ uint32_t s_carry;
   __shared__ int s_last;
@@ -327,6 +332,7 @@ struct SortSmem {
 // unrolls (one instantiation per width 1..9).
 template <int W>
 __global__ void __launch_bounds__(kSortThreads, 2) k_pass(Ws ws, Stage st, int digit) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
   const int slot = st.slot0 + digit;
@@ -500,9 +506,9 @@ static cudaError_t run_passes(const Ws& ws, const Stage& s, int n_digits, int re
     const int width = (int)((s.widths >> (8 * p)) & 0xffu);
     if (width < 1 || width > 9) return cudaErrorInvalidValue;
     const uint32_t nbins = 1u << width;
-    k_count<<<resident_small, 256, 0, st>>>(ws, s, p);
-    k_scan<<<nbins, kScanThreads, 0, st>>>(ws, s, p, p + 1 == n_digits ? 1 : 0);
-    kPassFns[width]<<<resident_sort, kSortThreads, sizeof(SortSmem), st>>>(ws, s, p);
+    launch_k(k_count, dim3(resident_small), dim3(256), 0, st, ws, s, p);
+    launch_k(k_scan, dim3(nbins), dim3(kScanThreads), 0, st, ws, s, p, p + 1 == n_digits ? 1 : 0);
+    launch_k(kPassFns[width], dim3(resident_sort), dim3(kSortThreads), sizeof(SortSmem), st, ws, s, p);
   }
   return cudaGetLastError();
 }
@@ -511,9 +517,9 @@ static cudaError_t run_passes(const Ws& ws, const Stage& s, int n_digits, int re
 cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st) {
   const Stage s = unit_stage(ws);
   const uint32_t nblocks = ws.units / kScanBlock;
-  k_vis_count<<<nblocks, 256, 0, st>>>(ws);
-  k_vis_scan<<<1, 1024, 0, st>>>(ws, s, nblocks);
-  k_unit_keys<<<nblocks, 256, 0, st>>>(ws, s);
+  launch_k(k_vis_count, dim3(nblocks), dim3(256), 0, st, ws);
+  launch_k(k_vis_scan, dim3(1), dim3(1024), 0, st, ws, s, nblocks);
+  launch_k(k_unit_keys, dim3(nblocks), dim3(256), 0, st, ws, s);
   return run_passes(ws, s, 4, resident_small, resident_sort, st);
 }
 
