@@ -341,7 +341,7 @@ flod_status flod_preprocess(const flod_gaussians* sets, int n_sets, const flod_v
   if (s != FLOD_OK) return s;
   const Ws w = ws_ptrs(ws, P);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(w.status, 0, 4, st) != cudaSuccess) return FLOD_ERR_CUDA;
+  if (launch_clear_status(w.status, st) != cudaSuccess) return FLOD_ERR_CUDA;
   return with_batch(sets, n_sets, views, n_views, cfg, P,
                     [&](const auto& B) { return launch_preprocess(B, w, st); });
 }
@@ -420,7 +420,7 @@ flod_status flod_blend_bwd(const flod_gaussians* sets, int n_sets, const flod_vi
   if (s != FLOD_OK) return s;
   const Ws w = ws_ptrs(ws, P);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (P.L.units && cudaMemsetAsync(w.grad2d, 0, 36 * P.L.units, st) != cudaSuccess)
+  if (P.L.units && launch_zero16(w.grad2d, 36 * P.L.units, dev->res_small, st) != cudaSuccess)
     return FLOD_ERR_CUDA;
   const bool pers = cfg->persistent != 0;
   return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {

@@ -814,12 +814,13 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
                            cudaStream_t st) {
   const uint32_t nblocks = b.units / kScanBlock;
   cudaError_t e;
-  if (b.tiles) {
+  if (b.tiles && !nblocks) {   // with units, the unit sort's first kernel clears them
     e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * b.tiles, st);
     if (e != cudaSuccess) return e;
   }
   if (nblocks) {
-    if ((e = launch_unit_sort(ws, resident_small, resident_sort, st)) != cudaSuccess) return e;
+    if ((e = launch_unit_sort(ws, b.tiles, resident_small, resident_sort, st)) != cudaSuccess)
+      return e;
     launch_k(k_block_sums, dim3(nblocks), dim3(256), 0, st, ws);
   }
   launch_k(k_scan_blocks, dim3(1), dim3(1024), 0, st, ws, nblocks, d_pair_count);

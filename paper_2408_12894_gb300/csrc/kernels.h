@@ -46,7 +46,9 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
                            cudaStream_t st);
 
 // sort.cu
-cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st);
+// launch_unit_sort also clears the n_tiles tile ranges (when there are units)
+cudaError_t launch_unit_sort(const Ws& ws, uint32_t n_tiles, int resident_small, int resident_sort,
+                             cudaStream_t st);
 cudaError_t launch_pair_sort(const Ws& ws, int n_digits, int tile_bits, int resident_small,
                              int resident_sort, cudaStream_t st);
 int sort_kernel_smem_bytes();
@@ -61,6 +63,10 @@ template <int MAXV>
 cudaError_t launch_render_bwd(const Batch<MAXV>& b, const Ws& ws, const float* dL,
                               const float* fwd_T, const uint32_t* fwd_nc, int resident,
                               bool persistent, cudaStream_t st);
+
+// render.cu: helpers in stream order
+cudaError_t launch_zero16(void* p, size_t bytes, int grid, cudaStream_t st);   // 16-B aligned
+cudaError_t launch_clear_status(uint32_t* status, cudaStream_t st);
 
 // select.cu
 cudaError_t launch_select(const SetP* levels, int n_levels, const float* thresh_lo,

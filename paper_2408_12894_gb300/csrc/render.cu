@@ -456,6 +456,29 @@ __global__ void __launch_bounds__(256 / PIX) k_render_bwd(const __grid_constant_
   add_evals(ws.plan + kPlanEvalBwd, evals);
 }
 
+// Zero-fill of n 16-byte words, in stream order (the previous kernel may still read them).
+__global__ void __launch_bounds__(256) k_zero16(uint4* __restrict__ p, size_t n) {
+  pdl_entry();
+  for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256)
+    p[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// The device status word cleared, in stream order.
+__global__ void k_clear_status(uint32_t* status) {
+  pdl_entry();
+  *status = 0u;
+}
+
+cudaError_t launch_zero16(void* p, size_t bytes, int grid, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if (bytes % 16 || reinterpret_cast<uintptr_t>(p) % 16) return cudaErrorInvalidValue;
+  return launch_k(k_zero16, dim3(grid), dim3(256), 0, st, reinterpret_cast<uint4*>(p), bytes / 16);
+}
+
+cudaError_t launch_clear_status(uint32_t* status, cudaStream_t st) {
+  return launch_k(k_clear_status, dim3(1), dim3(1), 0, st, status);
+}
+
 // ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------

@@ -62,8 +62,11 @@ __device__ __forceinline__ const uint32_t* src_keys(const Stage& s, int src) {
 // order (k_unit_keys): key = float bits of the view-space depth minus the smallest (depths
 // are positive, so the bits order like the values, and the difference keeps that order with
 // fewer significant bits: digits above them are skipped), value = unit index.
-__global__ void __launch_bounds__(256) k_vis_count(Ws ws) {
+__global__ void __launch_bounds__(256) k_vis_count(Ws ws, uint32_t n_tiles) {
   pdl_entry();
+  // the tile ranges of this frame start empty (k_ranges sets those of tiles with pairs)
+  for (uint32_t t = blockIdx.x * 256u + threadIdx.x; t < n_tiles; t += gridDim.x * 256u)
+    ws.ranges[t] = make_uint2(0u, 0u);
   __shared__ uint32_t red[3][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t i4 = blockIdx.x * 256u + threadIdx.x;
@@ -514,10 +517,11 @@ static cudaError_t run_passes(const Ws& ws, const Stage& s, int n_digits, int re
 }
 
 // Stage "units": depth digits (32 bits -> 4 passes of 8 bits) of the units with tiles.
-cudaError_t launch_unit_sort(const Ws& ws, int resident_small, int resident_sort, cudaStream_t st) {
+cudaError_t launch_unit_sort(const Ws& ws, uint32_t n_tiles, int resident_small, int resident_sort,
+                             cudaStream_t st) {
   const Stage s = unit_stage(ws);
   const uint32_t nblocks = ws.units / kScanBlock;
-  launch_k(k_vis_count, dim3(nblocks), dim3(256), 0, st, ws);
+  launch_k(k_vis_count, dim3(nblocks), dim3(256), 0, st, ws, n_tiles);
   launch_k(k_vis_scan, dim3(1), dim3(1024), 0, st, ws, s, nblocks);
   launch_k(k_unit_keys, dim3(nblocks), dim3(256), 0, st, ws, s);
   return run_passes(ws, s, 4, resident_small, resident_sort, st);
