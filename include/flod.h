@@ -160,7 +160,7 @@ typedef struct {
   uint64_t pair_capacity;
 } flod_ws_layout;
 
-/* Fill *cfg with the defaults: 16x16 tiles, batch 256, dilation 0.3, z_near 0.2, black
+/* Fill *cfg with the defaults: 16x16 tiles, batch 128, dilation 0.3, z_near 0.2, black
  * background, opacity-aware extent, one CTA per tile. */
 void flod_default_config(flod_raster_config *cfg);
 

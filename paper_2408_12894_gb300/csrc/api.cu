@@ -299,7 +299,7 @@ void flod_default_config(flod_raster_config* c) {
   if (!c) return;
   c->tile_w = 16;
   c->tile_h = 16;
-  c->batch = 256;
+  c->batch = 128;
   c->dilation = 0.3f;
   c->z_near = 0.2f;
   c->bg[0] = c->bg[1] = c->bg[2] = 0.f;

@@ -47,7 +47,7 @@ def test_host_side_checks_without_a_device(libpath):
     from paper_2408_12894_gb300 import flod
     import ctypes as C
     cfg = flod.default_config()
-    assert (cfg.tile_w, cfg.tile_h, cfg.batch) == (16, 16, 256)
+    assert (cfg.tile_w, cfg.tile_h, cfg.batch) == (16, 16, 128)
     assert abs(cfg.dilation - 0.3) < 1e-7 and abs(cfg.z_near - 0.2) < 1e-7
     # a fake set/view description: the size query is pure host arithmetic
     g = flod.Gaussians()

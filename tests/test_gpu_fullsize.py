@@ -1,5 +1,5 @@
 """Parity at the full benchmark sizes, in the launch configuration bench.py times (16x16
-tiles, batch 256, one CTA per tile): sampled pixels against the oracle's per-pixel render
+tiles, batch 128, one CTA per tile): sampled pixels against the oracle's per-pixel render
 over every Gaussian, sampled Gaussians' gradients against the oracle's exact per-footprint
 gradient, and invariants that hold at any size."""
 import numpy as np
