@@ -97,7 +97,8 @@ typedef struct {
 
 typedef struct {
   int tile_w, tile_h; /* 8x8, 16x16 or 32x8 pixels */
-  int batch;          /* Gaussians staged per shared-memory batch: 32, 64, 128 or 256 */
+  int batch;          /* Gaussians staged per shared-memory batch: 32, 64, 128 or 256 (the
+                         blending kernels stage at most 128) */
   float dilation;     /* px^2 added to the 2D covariance diagonal (default 0.3) */
   float z_near;       /* cull t_z <= z_near (default 0.2) */
   float bg[3];        /* background colour (default black) */
