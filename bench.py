@@ -421,11 +421,12 @@ def run_flod(a):
     achieved = d_flop / (d_ms * 1e-3) / 1e12
     n_tiles = int(rast.layout.tiles)
     n_passes = (max(1, math.ceil(math.log2(max(n_tiles, 2)))) + 8) // 9   # 9-bit tile digits
-    # preprocess 1; bin_sort: visible counts, their scan, unit keys, 4 depth passes of 3
-    # kernels (count, scan, scatter; a pass above the keys' significant bits exits at once),
-    # block sums, scan, light and sliced emission, n_passes tile passes of 3, ranges;
-    # render_fwd 1; blend_bwd 1; preprocess_bwd 1 (memsets not counted)
-    launches_per_step = 1 + (3 + 12 + 4 + 3 * n_passes + 1) + 1 + 1 + 1
+    # preprocess 2 (status clear, preprocess); bin_sort: visible counts, their scan, unit
+    # keys, 4 depth passes of 3 kernels (count, scan, scatter; a pass above the keys'
+    # significant bits exits at once), block sums, scan, light, big-unit and sliced emission,
+    # n_passes tile passes of 3, ranges; render_fwd 1; blend_bwd 2 (2D-gradient zero-fill,
+    # blend); preprocess_bwd 1
+    launches_per_step = 2 + (3 + 12 + 2 + 3 + 3 * n_passes + 1) + 1 + 2 + 1
 
     if rank == 0:
         line = {

@@ -12,7 +12,7 @@
 namespace flod {
 
 constexpr uint32_t kLightPairs = 16 * kEmitSlice;   // blocks up to this many pairs: k_emit_light
-constexpr uint32_t kBigPerWarp = 2;    // k_emit_big: units per warp, fetched together
+constexpr uint32_t kBigPerGroup = 1;   // k_emit_big: units per half-warp and step
 constexpr uint32_t kSmallTiles = 32;   // light emission, one pair per lane: units of at most
                                        //   this many tiles, rows from their tile record
 
@@ -458,9 +458,9 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<MAXV
 //     binary search over the units' first numbers (shuffles) and its row from the row
 //     starts, and writes keys and values of 32 consecutive positions of a unit run at once;
 //   - the other units (more tiles, rows recomputed from the ellipse, or a record that does
-//     not add up) are listed for k_emit_big, where one warp writes each: rows 32 at a time
-//     (one per lane, their columns from the record or recomputed), then each row's tiles one
-//     per lane. A CTA's run time then no longer depends on how many of them its slots hold.
+//     not add up) are listed for k_emit_big, where half a warp writes each: rows 16 at a time
+//     (one per lane, their columns from the record or recomputed), then the pairs one per
+//     lane. A CTA's run time then no longer depends on how many of them its slots hold.
 // Heavier blocks are left to the sliced k_emit.
 template <int MAXV>
 __device__ __forceinline__ bool rec_row_tiles(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
@@ -483,17 +483,20 @@ __device__ __forceinline__ bool rec_row_tiles(const Batch<MAXV>& b, const Ws& ws
   return c > 0;
 }
 
-// The whole warp writes the n_all pairs of unit u (tile record rc; centre xy and extent ext,
-// (m, h, rx, ry) or (0, 0, r, r), for rows recomputed) from position p0 on: rows 32 at a
-// time, one per lane (first tile and count, from the record or recomputed), then their pairs
-// one per lane.
-template <int MAXV>
-__device__ __forceinline__ void emit_unit_warp(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
-                                               const uint4& rc, float2 xy, float4 ext,
-                                               unsigned long long p0, uint32_t n_all,
-                                               uint32_t* keys, uint32_t* vals,
-                                               unsigned long long cap) {
-  const int lane = threadIdx.x & 31;
+// A group of GW lanes (the whole warp, or one half of it) writes the n_all pairs of unit u
+// (tile record rc; centre xy and extent ext, (m, h, rx, ry) or (0, 0, r, r), for rows
+// recomputed) from position p0 on: rows GW at a time, one per lane (first tile and count,
+// from the record or recomputed), then their pairs one per lane. The group's lanes take the
+// same path; the shuffles involve only them.
+template <int MAXV, int GW>
+__device__ __forceinline__ void emit_unit_group(const Batch<MAXV>& b, const Ws& ws, uint32_t u,
+                                                const uint4& rc, float2 xy, float4 ext,
+                                                unsigned long long p0, uint32_t n_all,
+                                                uint32_t* keys, uint32_t* vals,
+                                                unsigned long long cap) {
+  static_assert(GW == 16 || GW == 32, "a warp or half a warp");
+  const int lane = threadIdx.x & (GW - 1);
+  const uint32_t mask = GW == 32 ? 0xffffffffu : 0xffffu << (threadIdx.x & 16);
   const ViewP& V = b.views[view_of_unit(b, u)];
   const uint32_t row_base = V.tile_off, tiles_x = V.tiles_x;
   UnitTiles t;
@@ -502,30 +505,30 @@ __device__ __forceinline__ void emit_unit_warp(const Batch<MAXV>& b, const Ws& w
                b.cfg.extent_rule == 2, t);
   const uint32_t nrows = rc.y & 0xffffu;
   uint32_t done = 0;
-  for (uint32_t r0 = 0; r0 < nrows; r0 += 32) {
-    // rows r0..r0+31, one per lane: their first tile and tile count
+  for (uint32_t r0 = 0; r0 < nrows; r0 += GW) {
+    // rows r0..r0+GW-1, one per lane: their first tile and tile count
     const uint32_t r = r0 + lane;
     uint32_t rn = 0, rt0 = 0;
     if (r < nrows && !rec_row_tiles(b, ws, u, rc, t, r, row_base, tiles_x, rn, rt0)) rn = 0;
     uint32_t incl = rn;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    for (int o = 1; o < GW; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(mask, incl, o, GW);
       if (lane >= o) incl += y;
     }
     const uint32_t excl = incl - rn;                      // the row's first pair (chunk-relative)
-    const uint32_t chunk = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t chunk = __shfl_sync(mask, incl, GW - 1, GW);
     // the chunk's pairs, one per lane: the row holding pair q is the last row whose first
     // pair is <= q (a row without tiles shares its first pair with the next one)
-    for (uint32_t q0 = 0; q0 < chunk; q0 += 32) {
+    for (uint32_t q0 = 0; q0 < chunk; q0 += GW) {
       const uint32_t q = q0 + lane;
       int v = 0;
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t ev = __shfl_sync(0xffffffffu, excl, v + step);
+      for (int step = GW / 2; step > 0; step >>= 1) {
+        const uint32_t ev = __shfl_sync(mask, excl, v + step, GW);
         if (ev <= q) v += step;
       }
-      const uint32_t tile = __shfl_sync(0xffffffffu, rt0, v) + (q - __shfl_sync(0xffffffffu, excl, v));
+      const uint32_t tile = __shfl_sync(mask, rt0, v, GW) + (q - __shfl_sync(mask, excl, v, GW));
       if (q < chunk && done + q < n_all) {
         const unsigned long long p = p0 + done + q;
         if (p < cap) {
@@ -694,26 +697,29 @@ __global__ void __launch_bounds__(256, 4) k_emit_light(const __grid_constant__ B
 }
 
 // The units the light emission listed (more than kSmallTiles tiles, rows recomputed, or a
-// record that does not add up): each warp takes kBigPerWarp entries, its first lanes fetch
-// their units' data at once, then the warp writes the units one after the other.
+// record that does not add up): each half-warp takes kBigPerGroup entries, its first lanes
+// fetch their units' data at once, then it writes the units one after the other (the two
+// halves of a warp side by side).
 template <int MAXV>
 __global__ void __launch_bounds__(256) k_emit_big(const __grid_constant__ Batch<MAXV> b, Ws ws) {
   pdl_entry();
-  constexpr uint32_t G = kBigPerWarp;
+  constexpr uint32_t G = kBigPerGroup;
+  constexpr int GW = 16;   // lanes per group: two units of a warp are written side by side
   const uint32_t n = ws.plan[kPlanBigUnits];
   const BigUnits L = big_units(ws);
-  const int lane = threadIdx.x & 31;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const int gl = threadIdx.x & (GW - 1);
+  const uint32_t mask = 0xffffu << (threadIdx.x & 16);
+  const uint32_t ng = (gridDim.x * blockDim.x) / GW;
   const unsigned long long cap = ws.pair_capacity;
   const bool rows = b.cfg.extent_rule == 2;
-  for (uint32_t e0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; e0 < n; e0 += nw * G) {
-    // lanes 0..G-1 fetch one unit's data each, all requests in flight together
-    const uint32_t e = e0 + (uint32_t)lane;
+  for (uint32_t e0 = ((blockIdx.x * blockDim.x + threadIdx.x) / GW) * G; e0 < n; e0 += ng * G) {
+    // the group's lanes 0..G-1 fetch one unit's data each, all requests in flight together
+    const uint32_t e = e0 + (uint32_t)gl;
     uint32_t u = 0, pos = 0, c = 0;
     uint4 rc = make_uint4(0u, 0u, 0u, 0u);
     float2 xy = make_float2(0.f, 0.f);
     float4 ext = make_float4(0.f, 0.f, 0.f, 0.f);
-    if ((uint32_t)lane < G && e < n) {
+    if ((uint32_t)gl < G && e < n) {
       u = L.unit[e];
       pos = L.pos[e];
       c = ws.tiles_touched[u];
@@ -728,14 +734,14 @@ __global__ void __launch_bounds__(256) k_emit_big(const __grid_constant__ Batch<
     }
     const int m = (int)min(G, n - e0);
     for (int k = 0; k < m; ++k) {
-      const uint4 rk = make_uint4(__shfl_sync(0xffffffffu, rc.x, k), __shfl_sync(0xffffffffu, rc.y, k),
-                                  __shfl_sync(0xffffffffu, rc.z, k), __shfl_sync(0xffffffffu, rc.w, k));
-      const float2 xk = make_float2(__shfl_sync(0xffffffffu, xy.x, k), __shfl_sync(0xffffffffu, xy.y, k));
-      const float4 ek = make_float4(__shfl_sync(0xffffffffu, ext.x, k), __shfl_sync(0xffffffffu, ext.y, k),
-                                    __shfl_sync(0xffffffffu, ext.z, k), __shfl_sync(0xffffffffu, ext.w, k));
-      emit_unit_warp(b, ws, __shfl_sync(0xffffffffu, u, k), rk, xk, ek,
-                     __shfl_sync(0xffffffffu, pos, k), __shfl_sync(0xffffffffu, c, k), ws.keys[0],
-                     ws.vals[0], cap);
+      const uint4 rk = make_uint4(__shfl_sync(mask, rc.x, k, GW), __shfl_sync(mask, rc.y, k, GW),
+                                  __shfl_sync(mask, rc.z, k, GW), __shfl_sync(mask, rc.w, k, GW));
+      const float2 xk = make_float2(__shfl_sync(mask, xy.x, k, GW), __shfl_sync(mask, xy.y, k, GW));
+      const float4 ek = make_float4(__shfl_sync(mask, ext.x, k, GW), __shfl_sync(mask, ext.y, k, GW),
+                                    __shfl_sync(mask, ext.z, k, GW), __shfl_sync(mask, ext.w, k, GW));
+      emit_unit_group<MAXV, GW>(b, ws, __shfl_sync(mask, u, k, GW), rk, xk, ek,
+                                __shfl_sync(mask, pos, k, GW), __shfl_sync(mask, c, k, GW),
+                                ws.keys[0], ws.vals[0], cap);
     }
   }
 }
