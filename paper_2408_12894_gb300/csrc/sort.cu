@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) k_unit_keys(Ws ws, Stage st) {
 // Phase 1: digit histogram of every partition, stored digit-major.
 __global__ void __launch_bounds__(256) k_count(Ws ws, Stage st, int digit) {
   pdl_entry();
-  __shared__ uint32_t h[kRadixBins];
+  __shared__ uint32_t h[8][kRadixBins];   // one histogram per warp (fewer colliding atomics)
   if (!digit_live(ws, st, digit)) return;
   const int slot = st.slot0 + digit;
   const uint32_t* __restrict__ kin = src_keys(st, (int)ws.plan[kPlanSrc + slot]);
@@ -202,8 +202,9 @@ __global__ void __launch_bounds__(256) k_count(Ws ws, Stage st, int digit) {
   const uint32_t width = (st.widths >> (8 * digit)) & 0xffu;
   const uint32_t dmask = (1u << width) - 1u, nbins = 1u << width;
   const int tid = threadIdx.x;
+  uint32_t* hw = h[tid >> 5];
   for (uint32_t part = blockIdx.x; part < nparts; part += gridDim.x) {
-    for (uint32_t d = tid; d < nbins; d += 256) h[d] = 0;
+    for (uint32_t d = tid; d < 8 * nbins; d += 256) h[d / nbins][d % nbins] = 0;
     __syncthreads();
     const uint32_t base = part * (uint32_t)kSortPart;
 #pragma unroll
@@ -211,17 +212,22 @@ __global__ void __launch_bounds__(256) k_count(Ws ws, Stage st, int digit) {
       const uint32_t i = base + 4u * (r * 256u + tid);
       if (i + 3 < P) {
         const uint4 v = reinterpret_cast<const uint4*>(kin)[i >> 2];
-        atomicAdd(&h[(v.x >> shift) & dmask], 1u);
-        atomicAdd(&h[(v.y >> shift) & dmask], 1u);
-        atomicAdd(&h[(v.z >> shift) & dmask], 1u);
-        atomicAdd(&h[(v.w >> shift) & dmask], 1u);
+        atomicAdd(&hw[(v.x >> shift) & dmask], 1u);
+        atomicAdd(&hw[(v.y >> shift) & dmask], 1u);
+        atomicAdd(&hw[(v.z >> shift) & dmask], 1u);
+        atomicAdd(&hw[(v.w >> shift) & dmask], 1u);
       } else {
         for (uint32_t j = 0; j < 4; ++j)
-          if (i + j < P) atomicAdd(&h[(kin[i + j] >> shift) & dmask], 1u);
+          if (i + j < P) atomicAdd(&hw[(kin[i + j] >> shift) & dmask], 1u);
       }
     }
     __syncthreads();
-    for (uint32_t d = tid; d < nbins; d += 256) ws.counts[(size_t)d * ws.max_parts + part] = h[d];
+    for (uint32_t d = tid; d < nbins; d += 256) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) c += h[w][d];
+      ws.counts[(size_t)d * ws.max_parts + part] = c;
+    }
     __syncthreads();
   }
 }
