@@ -173,18 +173,6 @@ __device__ __forceinline__ bool pixel_rect(float u, float v, float rx, float ry,
 // of a (non-negative) pixel coordinate is a shift.
 __device__ __forceinline__ int tile_shift(int t) { return __ffs(t) - 1; }
 
-__device__ __forceinline__ bool tile_rect(float u, float v, float r, int W, int H, int tw,
-                                          int th, int& tx0, int& tx1, int& ty0, int& ty1) {
-  int px0, px1, py0, py1;
-  if (!pixel_rect(u, v, r, r, W, H, px0, px1, py0, py1)) return false;
-  const int lw = tile_shift(tw), lh = tile_shift(th);
-  tx0 = px0 >> lw;
-  tx1 = px1 >> lw;
-  ty0 = py0 >> lh;
-  ty1 = py1 >> lh;
-  return true;
-}
-
 // ---------------------------------------------------------------------------------------
 // Tile sets of a unit ("segments": one run of tile columns per tile row)
 // ---------------------------------------------------------------------------------------
