@@ -59,8 +59,8 @@ typedef enum {
 
 /* Device status bits (flod_read_status). */
 #define FLOD_DEV_CAPACITY 0x1u /* pairs exceeded pair_capacity: pairs beyond it dropped */
-#define FLOD_DEV_TIMEOUT 0x2u  /* a bounded device-side wait gave up (reserved: no kernel of
-                                  this version waits on another CTA) */
+#define FLOD_DEV_TIMEOUT 0x2u  /* a bounded device-side wait gave up: the preprocess's wait for
+                                  its bulk copies (no kernel waits on another CTA) */
 #define FLOD_DEV_TILESET 0x4u  /* emission listed another tile count than tiles_touched
                                   (only with inconsistent per-unit inputs in the workspace) */
 
