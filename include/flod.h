@@ -146,9 +146,12 @@ typedef struct {
   size_t tiles_touched; /* uint32 [units], 0 when culled */
   size_t block_sums;    /* uint64 [units/1024 + 1] exclusive pair offsets per 1024 units */
   size_t slices;        /* uint32 [units/1024 + 1] exclusive count of 4096-pair emission slices */
-  size_t ukeys[2];      /* uint32 [units] x 2: depth keys of the unit-stage sort */
+  size_t ukeys[2];      /* uint32 [units] x 2: depth keys of the unit-stage sort; after it,
+                           ukeys[0] holds the tile count of every depth-sorted slot */
   size_t uvals[2];      /* uint32 [units] x 2: units in depth order (plan[45] = result buffer) */
-  size_t keys[2];       /* uint32 [pair_capacity] x 2: tile ids of the pairs (keys[0] = emitted) */
+  size_t keys[2];       /* uint32 [pair_capacity] x 2: tile ids of the pairs (keys[0] = emitted;
+                           during emission keys[1], vals[1] list the units written by whole
+                           half-warps: first position, unit) */
   size_t vals[2];       /* uint32 [pair_capacity] x 2: units of the pairs */
   size_t hist;          /* radix-sort digit histograms */
   size_t counts;        /* uint32 [512][partitions]: radix sort, per-partition digit counts */
