@@ -150,8 +150,9 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Ws ws, uint32_t nblocks,
 //   2. counts the tile rows of the slots that overlap the slice and scans them: each
 //      (slot, tile row) is one work item;
 //   3. evaluates the items, split evenly over the threads (consecutive items per thread, at
-//      most kEmitPerThread per round): the row's tile columns (UnitTiles/unit_row, the rule preprocess counted with), a block scan of their
-//      counts for the row's first position, and, for a row that overlaps the slice, a
+//      most kEmitPerThread per round): the row's tile columns (UnitTiles/unit_row, the rule
+//      preprocess counted with), a block scan of their counts for the row's first
+//      position, and, for a row that overlaps the slice, a
 //      "segment": its first tile id (minus its first slice position) and its unit, with the
 //      segment's id marked at that position;
 //   4. fills every position with the id of the last mark at or before it (a block scan);
