@@ -151,13 +151,35 @@ def clock_summary(s):
 # CPU oracle timing (the reference arm and the cpu_baseline key)
 # ---------------------------------------------------------------------------------------
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 class OracleStep:
     """Times the FP64 oracle on a bounded sample of one training step and scales it to the
     full step: preprocess forward+backward and binning on a slice of the Gaussians (scaled by
-    N / slice) plus blending forward+backward on a sample of tiles (scaled by tiles / sample).
-    The tile lists come from an untimed FP64 preprocess of the whole level."""
+    N / slice) plus blending forward+backward on a stratified sample of tiles. The tiles are
+    ordered by pair count and cut into `tiles` strata of equal size; the middle tile of each
+    stratum is timed and stands for its stratum. The tile lists come from an untimed FP64
+    preprocess of the whole level. The sample depends only on the workload, so every arm and
+    every run times the same work."""
 
-    def __init__(self, g, cam, s_min, slice_n=40_000, tiles=6, seed=0):
+    def __init__(self, g, cam, s_min, slice_n=20_000, tiles=64):
         import numpy as np
         import torch
         from oracle import raster as R
@@ -172,13 +194,26 @@ class OracleStep:
         self.lists = R.tile_lists(pre, cam, self.cfg)
         ranges = self.lists[2]
         counts = ranges[:, 1] - ranges[:, 0]
-        rng = np.random.default_rng(seed)
-        nz = np.nonzero(counts)[0]
-        self.sample = rng.choice(nz, size=min(tiles, nz.size), replace=False)
+        order = np.argsort(counts, kind="stable")
+        strata = np.array_split(order, min(tiles, order.size))
+        self.sample = np.array([st[st.size // 2] for st in strata])
+        self.weight = np.array([st.size for st in strata], dtype=np.float64)
+        self.sample_pairs = counts[self.sample]
         self.n_tiles = ranges.shape[0]
+        rng = np.random.default_rng(11)
         self.grad_out = rng.normal(0, 1e-3, (3, cam["height"], cam["width"]))
 
-    def step_seconds(self) -> float:
+    def step_seconds(self, threads=None) -> float:
+        R, np, torch = self.R, self.np, self.torch
+        prev = torch.get_num_threads()
+        if threads:
+            torch.set_num_threads(threads)
+        try:
+            return self._step()
+        finally:
+            torch.set_num_threads(prev)
+
+    def _step(self) -> float:
         R, np, torch = self.R, self.np, self.torch
         sub = {k: (v[:self.slice_n] if k != "sh_degree" else v) for k, v in self.g.items()}
         t0 = time.perf_counter()
@@ -193,26 +228,40 @@ class OracleStep:
         keys, vals, ranges, tx, ty = self.lists
         leaves = {n: self.pre[n].detach().clone().requires_grad_(True) for n in self.pre}
         bg = torch.zeros(3, dtype=torch.float64)
-        t0 = time.perf_counter()
-        for tile in self.sample:
+        t_tiles = 0.0
+        for tile, w in zip(self.sample, self.weight):
+            t0 = time.perf_counter()
             s, e = ranges[tile]
-            gi = torch.as_tensor(vals[s:e].astype(np.int64))
-            x0, y0 = (tile % tx) * 16, (tile // tx) * 16
-            xs = np.arange(x0, min(x0 + 16, self.cam["width"]))
-            ys = np.arange(y0, min(y0 + 16, self.cam["height"]))
-            gx, gy = np.meshgrid(xs, ys)
-            pix = torch.as_tensor(np.stack([gx.ravel() + 0.5, gy.ravel() + 0.5], 1))
-            a = R.alpha_raw(pix, leaves["mean2d"][gi], leaves["conic"][gi], leaves["opacity"][gi])
-            col, _, _ = R.blend(a, leaves["rgb"][gi], bg)
-            go = torch.as_tensor(self.grad_out[:, y0:y0 + len(ys), x0:x0 + len(xs)].reshape(3, -1).T)
-            (col * go).sum().backward()
-        t_tiles = time.perf_counter() - t0
-        return t_slice * self.n / self.slice_n + t_tiles * self.n_tiles / max(len(self.sample), 1)
+            if e > s:
+                gi = torch.as_tensor(vals[s:e].astype(np.int64))
+                x0, y0, x1, y1 = R.tile_pixels(int(tile), tx, self.cam, self.cfg)
+                gx, gy = np.meshgrid(np.arange(x0, x1), np.arange(y0, y1))
+                pix = torch.as_tensor(np.stack([gx.ravel() + 0.5, gy.ravel() + 0.5], 1))
+                a = R.alpha_raw(pix, leaves["mean2d"][gi], leaves["conic"][gi], leaves["opacity"][gi])
+                col, _, _ = R.blend(a, leaves["rgb"][gi], bg)
+                go = torch.as_tensor(self.grad_out[:, y0:y1, x0:x1].reshape(3, -1).T)
+                (col * go).sum().backward()
+            t_tiles += (time.perf_counter() - t0) * w
+        return t_slice * self.n / self.slice_n + t_tiles
 
     def describe(self) -> str:
+        np = self.np
         return (f"preprocess fwd+bwd and binning of {self.slice_n} of {self.n} Gaussians "
                 f"(x{self.n / self.slice_n:.0f}) + blend fwd+bwd of {len(self.sample)} of "
-                f"{self.n_tiles} 16x16 tiles (x{self.n_tiles / max(len(self.sample), 1):.0f})")
+                f"{self.n_tiles} 16x16 tiles, one per equal-size stratum of the tiles ordered by "
+                f"pair count (pairs {int(self.sample_pairs.min())}..{int(self.sample_pairs.max())}, "
+                f"median {int(np.median(self.sample_pairs))}), each standing for its stratum")
+
+
+def cpu_baseline_line(ost, value_all=None):
+    """The cpu_baseline object: the oracle sample on every host core and on one."""
+    import torch
+    cores = os.cpu_count() or 1
+    t_all = ost.step_seconds(threads=cores) if value_all is None else 1.0 / value_all
+    t_one = ost.step_seconds(threads=1)
+    return {"value": 1.0 / t_all, "unit": "it/s", "cores": cores, "kind": "oracle",
+            "value_1_thread": 1.0 / t_one, "cpu_model": cpu_model(),
+            "torch_threads_default": torch.get_num_threads(), "sample": ost.describe()}
 
 
 def run_reference(a):
@@ -225,15 +274,12 @@ def run_reference(a):
     g = make_level(a.small, a.scale)
     g["s_opt"] = adjust_chain_numpy(g["s_opt"], level_counts(a.small, a.scale))
     cam = synth.level_camera()
-    # each step times a bounded sample, smaller for long runs so that the whole run stays
-    # within a few minutes (about 60 samples' worth of the 20,000-Gaussian slice)
-    n_samples = max(a.steps + a.warmup, 1)
-    ost = OracleStep(g, cam, synth.LEVEL_SMIN[-1],
-                     slice_n=max(4_000, min(20_000, 20_000 * 60 // n_samples)),
-                     tiles=3 if n_samples <= 60 else 1)
+    # each step times the same bounded sample as the main arm's cpu_baseline, on every core
+    ost = OracleStep(g, cam, synth.LEVEL_SMIN[-1])
+    cores = os.cpu_count() or 1
     for _ in range(a.warmup):
-        ost.step_seconds()
-    secs = [ost.step_seconds() for _ in range(a.steps)]
+        ost.step_seconds(threads=cores)
+    secs = [ost.step_seconds(threads=cores) for _ in range(a.steps)]
     mean = sum(secs) / len(secs)
     v = 1.0 / mean
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "it/s", "n_gpus": world,
@@ -241,8 +287,8 @@ def run_reference(a):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "gaussians": g["means"].shape[0],
                                             "resolution": "1920x1080", "sh_degree": 3},
-            "cpu_baseline": {"value": v, "unit": "it/s", "cores": torch.get_num_threads(),
-                             "kind": "oracle", "sample": ost.describe()},
+            "cpu_baseline": {"value": v, "unit": "it/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(), "sample": ost.describe()},
             "e2e": {"value": v, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

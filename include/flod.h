@@ -22,8 +22,9 @@
  *   except a per-device cache of occupancy figures.
  * - Calls enqueue work on `stream` and return without waiting. Argument checks are done on
  *   the host before anything is enqueued; on a check failure nothing is enqueued and the
- *   status says why. Errors found on the device (pair capacity exceeded, a bounded spin
- *   that ran out) set bits of the workspace status word, read with flod_read_status().
+ *   status says why. Errors found on the device (pair capacity exceeded, inconsistent
+ *   per-unit tile counts) set bits of the workspace status word, read with
+ *   flod_read_status().
  *   No call aborts, traps or prints.
  * - Cameras: world->camera [R|t] row-major 3x4 (OpenCV axes: x right, y down, z forward),
  *   pinhole u = fx*x/z + cx, v = fy*y/z + cy; pixel (i, j) samples at (i+0.5, j+0.5).
@@ -59,8 +60,9 @@ typedef enum {
 
 /* Device status bits (flod_read_status). */
 #define FLOD_DEV_CAPACITY 0x1u /* pairs exceeded pair_capacity: pairs beyond it dropped */
-#define FLOD_DEV_TIMEOUT 0x2u  /* a bounded device-side wait gave up: the preprocess's wait for
-                                  its bulk copies (no kernel waits on another CTA) */
+#define FLOD_DEV_TIMEOUT 0x2u  /* reserved for a bounded device-side wait that gave up; no
+                                  kernel of this library spins on a flag or barrier, so none
+                                  sets it */
 #define FLOD_DEV_TILESET 0x4u  /* emission listed another tile count than tiles_touched
                                   (only with inconsistent per-unit inputs in the workspace) */
 
@@ -110,10 +112,14 @@ typedef struct {
 } flod_raster_config;
 
 /* Gradient outputs of one set, same shapes as the parameters (quats and, at SH degree 3,
- * sh 16-byte aligned). Accumulated with += unless `overwrite` is 1: then every gradient of
- * the set is written once (zeros for Gaussians that touch no tile), which needs no zeroed
- * buffers; overwrite requires that exactly one view renders the set, as a whole set (no
- * selection list), else the call returns FLOD_ERR_INVALID_ARG. */
+ * sh 16-byte aligned). `overwrite` selects how they are written:
+ *   0  accumulated with += into the caller's values;
+ *   1  every gradient of the set is written once (zeros for Gaussians that touch no tile),
+ *      which needs no zeroed buffers; requires that exactly one view renders the set, as a
+ *      whole set (no selection list), else the call returns FLOD_ERR_INVALID_ARG;
+ *   2  the library zero-fills the set's buffers (one kernel in the call's stream, before the
+ *      gradients are added), then accumulates as with 0: any views, no caller fill needed.
+ * Other values return FLOD_ERR_INVALID_ARG. */
 typedef struct {
   float *means, *quats, *s_opt, *opacity_logit, *sh;
   int overwrite;
@@ -205,6 +211,27 @@ flod_status flod_preprocess(const flod_gaussians *sets, int n_sets, const flod_v
 flod_status flod_bin_sort(const flod_gaussians *sets, int n_sets, const flod_view *views,
                           int n_views, const flod_raster_config *cfg, void *ws, size_t ws_bytes,
                           uint64_t pair_capacity, uint64_t *d_pair_count, flod_stream stream);
+
+/* flod_bin_sort in parts, for callers that time them separately: phase FLOD_BIN_ALL is
+ * flod_bin_sort itself; phases 1..4, called in order with the same arguments, enqueue
+ * exactly the same kernels:
+ *   FLOD_BIN_PHASE_DEPTH    the depth order of the units with tiles (their compaction and
+ *                           the depth-digit passes; also clears the tile ranges);
+ *   FLOD_BIN_PHASE_EMIT     per-block pair offsets, their scan (pair total to *d_pair_count
+ *                           and the workspace) and the emission of the pairs in depth order;
+ *   FLOD_BIN_PHASE_TILES    the tile-digit passes over the pairs;
+ *   FLOD_BIN_PHASE_RANGES   the tile ranges (and, with cfg->persistent, the largest-first
+ *                           tile order).
+ * Any other phase returns FLOD_ERR_INVALID_ARG. */
+#define FLOD_BIN_ALL 0
+#define FLOD_BIN_PHASE_DEPTH 1
+#define FLOD_BIN_PHASE_EMIT 2
+#define FLOD_BIN_PHASE_TILES 3
+#define FLOD_BIN_PHASE_RANGES 4
+flod_status flod_bin_sort_phase(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                                int n_views, const flod_raster_config *cfg, void *ws,
+                                size_t ws_bytes, uint64_t pair_capacity, uint64_t *d_pair_count,
+                                int phase, flod_stream stream);
 
 /* Front-to-back blending per pixel of every view. Outputs (device, planar per view, views
  * concatenated at their pixel offsets): out_rgb [3][H][W] per view, out_T [H][W] final

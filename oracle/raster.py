@@ -208,6 +208,34 @@ def tile_lists(pre: dict, cam: dict, cfg: Config):
     return keys, vals, tile_ranges(keys, tiles_x * tiles_y), tiles_x, tiles_y
 
 
+def tile_pixels(tile: int, tiles_x: int, cam: dict, cfg: Config):
+    """Pixel bounds (x0, y0, x1, y1), end exclusive, of one tile of a camera."""
+    tx, ty = tile % tiles_x, tile // tiles_x
+    x0, y0 = tx * cfg.tile_w, ty * cfg.tile_h
+    return x0, y0, min(x0 + cfg.tile_w, cam["width"]), min(y0 + cfg.tile_h, cam["height"])
+
+
+def render_tiles(pre: dict, cam: dict, cfg: Config, lists, tiles):
+    """The tiled render of the listed tiles only: for each tile, (colour [3,h,w], T_final
+    [h,w], n_contrib [h,w]) of its pixels, each pixel blending its tile's Gaussians in
+    sorted-key order (the same blend as ``render_tiled``)."""
+    keys, vals, ranges, tiles_x, tiles_y = lists
+    bg = torch.as_tensor(np.asarray(cfg.bg, dtype=np.float64))
+    out = {}
+    with torch.no_grad():
+        for tile in tiles:
+            x0, y0, x1, y1 = tile_pixels(int(tile), tiles_x, cam, cfg)
+            s, e = ranges[tile]
+            g = torch.as_tensor(vals[s:e].astype(np.int64))
+            pix = _pixel_centres(np.arange(x0, x1), np.arange(y0, y1))
+            a = alpha_raw(pix, pre["mean2d"][g], pre["conic"][g], pre["opacity"][g])
+            col, tf, lst = blend(a, pre["rgb"][g], bg)
+            h, w = y1 - y0, x1 - x0
+            out[int(tile)] = (col.numpy().T.reshape(3, h, w), tf.numpy().reshape(h, w),
+                              lst.reshape(h, w))
+    return out
+
+
 def render_tiled(pre: dict, cam: dict, cfg: Config, lists=None, grad_out=None):
     """Tile by tile: each pixel blends its tile's Gaussians in sorted-key order.
 

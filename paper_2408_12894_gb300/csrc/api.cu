@@ -346,11 +346,13 @@ flod_status flod_preprocess(const flod_gaussians* sets, int n_sets, const flod_v
                     [&](const auto& B) { return launch_preprocess(B, w, st); });
 }
 
-flod_status flod_bin_sort(const flod_gaussians* sets, int n_sets, const flod_view* views,
-                          int n_views, const flod_raster_config* cfg, void* ws, size_t ws_bytes,
-                          uint64_t pair_capacity, uint64_t* d_pair_count, flod_stream stream) {
+flod_status flod_bin_sort_phase(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                                int n_views, const flod_raster_config* cfg, void* ws,
+                                size_t ws_bytes, uint64_t pair_capacity, uint64_t* d_pair_count,
+                                int phase, flod_stream stream) {
   static thread_local Plan P;
   DevInfo* dev = nullptr;
+  if (phase < FLOD_BIN_ALL || phase > FLOD_BIN_PHASE_RANGES) return FLOD_ERR_INVALID_ARG;
   flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
   if (s != FLOD_OK) return s;
   const Ws w = ws_ptrs(ws, P);
@@ -359,8 +361,15 @@ flod_status flod_bin_sort(const flod_gaussians* sets, int n_sets, const flod_vie
   return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {
     return launch_binning(B, w, n_passes, P.tile_bits, dev->res_sort, dev->res_small,
                           reinterpret_cast<unsigned long long*>(d_pair_count),
-                          cfg->persistent != 0, st);
+                          cfg->persistent != 0, phase, st);
   });
+}
+
+flod_status flod_bin_sort(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                          int n_views, const flod_raster_config* cfg, void* ws, size_t ws_bytes,
+                          uint64_t pair_capacity, uint64_t* d_pair_count, flod_stream stream) {
+  return flod_bin_sort_phase(sets, n_sets, views, n_views, cfg, ws, ws_bytes, pair_capacity,
+                             d_pair_count, FLOD_BIN_ALL, stream);
 }
 
 flod_status flod_render_fwd(const flod_gaussians* sets, int n_sets, const flod_view* views,
@@ -382,7 +391,8 @@ flod_status flod_render_fwd(const flod_gaussians* sets, int n_sets, const flod_v
 
 namespace {
 // Per set: atomics when several units may hold one Gaussian (several views, or a selection
-// list beside other views), plain read-modify-write otherwise, plain stores on request.
+// list beside other views), plain read-modify-write otherwise, plain stores on request
+// (overwrite 1); overwrite 2 zero-fills the set's buffers in the stream first.
 bool grad_table(const flod_view* views, int n_views, int n_sets, const flod_grads* grads,
                 GradTable& gt) {
   memset(&gt, 0, sizeof(gt));
@@ -398,11 +408,13 @@ bool grad_table(const flod_view* views, int n_views, int n_sets, const flod_grad
     if (reinterpret_cast<uintptr_t>(grads[k].quats) & 15u) return false;
     if (reinterpret_cast<uintptr_t>(grads[k].sh) & 15u) return false;
     const bool shared = (direct[k] + n_sel) > 1;
-    if (grads[k].overwrite) {
+    if (grads[k].overwrite < 0 || grads[k].overwrite > 2) return false;
+    if (grads[k].overwrite == 1) {
       if (direct[k] != 1 || n_sel != 0) return false;
       gt.mode[k] = kGradOverwrite;
     } else {
       gt.mode[k] = shared ? kGradAtomic : kGradAccumulate;
+      gt.zero[k] = grads[k].overwrite == 2;
     }
   }
   return true;
@@ -441,8 +453,10 @@ flod_status flod_preprocess_bwd(const flod_gaussians* sets, int n_sets, const fl
   if (!grad_table(views, n_views, n_sets, grads, gt)) return FLOD_ERR_INVALID_ARG;
   const Ws w = ws_ptrs(ws, P);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  return with_batch(sets, n_sets, views, n_views, cfg, P,
-                    [&](const auto& B) { return launch_preprocess_bwd(B, w, gt, st); });
+  return with_batch(sets, n_sets, views, n_views, cfg, P, [&](const auto& B) {
+    const cudaError_t e = launch_zero_grads(B, gt, dev->res_small, st);
+    return e != cudaSuccess ? e : launch_preprocess_bwd(B, w, gt, st);
+  });
 }
 
 flod_status flod_render_bwd(const flod_gaussians* sets, int n_sets, const flod_view* views,

@@ -818,28 +818,34 @@ template <int MAXV>
 cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int tile_bits,
                            int resident_sort,
                            int resident_small, unsigned long long* d_pair_count, bool build_queue,
-                           cudaStream_t st) {
+                           int phase, cudaStream_t st) {
   const uint32_t nblocks = b.units / kScanBlock;
   cudaError_t e;
-  if (b.tiles && !nblocks) {   // with units, the unit sort's first kernel clears them
-    e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * b.tiles, st);
-    if (e != cudaSuccess) return e;
-  }
-  if (nblocks) {
-    if ((e = launch_unit_sort(ws, b.tiles, resident_small, resident_sort, st)) != cudaSuccess)
+  if (phase == 0 || phase == 1) {   // depth order of the units with tiles
+    if (b.tiles && !nblocks) {   // with units, the unit sort's first kernel clears them
+      e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * b.tiles, st);
+      if (e != cudaSuccess) return e;
+    }
+    if (nblocks &&
+        (e = launch_unit_sort(ws, b.tiles, resident_small, resident_sort, st)) != cudaSuccess)
       return e;
-    launch_k(k_block_sums, dim3(nblocks), dim3(256), 0, st, ws);
   }
-  launch_k(k_scan_blocks, dim3(1), dim3(1024), 0, st, ws, nblocks, d_pair_count);
-  if (nblocks) {
-    launch_k(k_emit_light<MAXV>, dim3(nblocks), dim3(256), 0, st, b, ws);
-    launch_k(k_emit_big<MAXV>, dim3(resident_small), dim3(256), 0, st, b, ws);
-    launch_k(k_emit<MAXV>, dim3(resident_small), dim3(256), 0, st, b, ws, nblocks);
+  if (phase == 0 || phase == 2) {   // pair offsets and key emission
+    if (nblocks) launch_k(k_block_sums, dim3(nblocks), dim3(256), 0, st, ws);
+    launch_k(k_scan_blocks, dim3(1), dim3(1024), 0, st, ws, nblocks, d_pair_count);
+    if (nblocks) {
+      launch_k(k_emit_light<MAXV>, dim3(nblocks), dim3(256), 0, st, b, ws);
+      launch_k(k_emit_big<MAXV>, dim3(resident_small), dim3(256), 0, st, b, ws);
+      launch_k(k_emit<MAXV>, dim3(resident_small), dim3(256), 0, st, b, ws, nblocks);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_pair_sort(ws, n_passes, tile_bits, resident_small, resident_sort, st)) !=
-      cudaSuccess)
-    return e;
+  if (phase == 0 || phase == 3) {   // tile digits over the pairs
+    if ((e = launch_pair_sort(ws, n_passes, tile_bits, resident_small, resident_sort, st)) !=
+        cudaSuccess)
+      return e;
+  }
+  if (phase != 0 && phase != 4) return cudaGetLastError();
   launch_k(k_ranges, dim3(resident_small), dim3(256), 0, st, ws, b.tiles);
   if (build_queue && b.tiles) {
     if ((e = cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t) * kQueueHeader, st)) != cudaSuccess)
@@ -853,8 +859,8 @@ cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int
 }
 
 template cudaError_t launch_binning<kMaxViewsSmall>(const BatchS&, const Ws&, int, int, int, int,
-                                                    unsigned long long*, bool, cudaStream_t);
+                                                    unsigned long long*, bool, int, cudaStream_t);
 template cudaError_t launch_binning<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, int, int, int, int,
-                                                    unsigned long long*, bool, cudaStream_t);
+                                                    unsigned long long*, bool, int, cudaStream_t);
 
 }  // namespace flod

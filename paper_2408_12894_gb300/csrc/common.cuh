@@ -47,7 +47,7 @@ struct SetP {
   const float* sh;
   int n, deg;
   float s_min;
-  int bulk_ok;   // every array 16-byte aligned: chunks of 256 Gaussians can be bulk-copied
+  int bulk_ok;   // every array 16-byte aligned: a CTA's chunk can be staged by cp.async
 };
 
 struct CfgP {
@@ -310,43 +310,26 @@ __device__ __forceinline__ void pdl_entry() {
 }
 
 // ---------------------------------------------------------------------------------------
-// Bulk (TMA) copies global -> shared memory completing on an mbarrier
+// Asynchronous copies global -> shared memory (cp.async, 16 bytes per request). The
+// requests of a CTA are spread over its threads and complete with one wait_all per thread
+// followed by a barrier: no copy can still be writing into a CTA's shared memory once its
+// threads have passed that barrier, so no exit path leaves a copy in flight.
 // ---------------------------------------------------------------------------------------
-constexpr uint32_t kBulkSpinLimit = 1u << 26;   // polls of a barrier before giving up
-
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// One arrival expected per phase; the fence makes the initialisation visible to the copies.
-__device__ __forceinline__ void bulk_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+// dst, src 16-byte aligned, bytes a multiple of 16; every thread of the CTA takes part.
+__device__ __forceinline__ void async_copy(void* dst, const void* src, uint32_t bytes) {
+  const char* s = static_cast<const char*>(src);
+  const uint32_t d = smem_addr(dst);
+  for (uint32_t o = threadIdx.x * 16u; o < bytes; o += blockDim.x * 16u)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + o), "l"(s + o) : "memory");
 }
 
-// Arrive on the barrier announcing the bytes the copies of this phase bring.
-__device__ __forceinline__ void bulk_expect(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-// dst, src 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-
-// Waits for the barrier's phase of the given parity to complete; false if the bound ran out.
-__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kBulkSpinLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.b32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-    if (done) return true;
-  }
-  return false;
+// Waits for every cp.async this thread issued (the caller then synchronises the CTA).
+__device__ __forceinline__ void async_copy_wait() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {

@@ -29,6 +29,7 @@ enum GradMode : int { kGradAccumulate = 0, kGradAtomic = 1, kGradOverwrite = 2 }
 struct GradTable {
   flod_grads g[FLOD_MAX_SETS];
   int mode[FLOD_MAX_SETS];   // GradMode: RMW (one unit per Gaussian), atomics, or store
+  int zero[FLOD_MAX_SETS];   // 1: the set's buffers are zero-filled first (flod_grads.overwrite 2)
 };
 
 // preprocess.cu
@@ -37,13 +38,17 @@ cudaError_t launch_preprocess(const Batch<MAXV>& b, const Ws& ws, cudaStream_t s
 template <int MAXV>
 cudaError_t launch_preprocess_bwd(const Batch<MAXV>& b, const Ws& ws, const GradTable& gt,
                                   cudaStream_t st);
+// zero-fills the gradient buffers of the sets with gt.zero set (one launch, in stream order)
+template <int MAXV>
+cudaError_t launch_zero_grads(const Batch<MAXV>& b, const GradTable& gt, int grid, cudaStream_t st);
 
-// binning.cu: block sums -> scan -> emit -> (sort) -> ranges
+// binning.cu: unit sort -> block sums -> scan -> emit -> pair sort -> ranges. phase 0 runs
+// everything; phases 1..4 one part each (FLOD_BIN_PHASE_*), in that order
 template <int MAXV>
 cudaError_t launch_binning(const Batch<MAXV>& b, const Ws& ws, int n_passes, int tile_bits,
                            int resident_sort,
                            int resident_small, unsigned long long* d_pair_count, bool build_queue,
-                           cudaStream_t st);
+                           int phase, cudaStream_t st);
 
 // sort.cu
 // launch_unit_sort also clears the n_tiles tile ranges (when there are units)

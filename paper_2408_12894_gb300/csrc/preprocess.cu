@@ -1,11 +1,11 @@
 // Per-(view, Gaussian) preprocess and its backward.
 //
-// Forward (one thread per unit; a CTA's 128 Gaussians of one set are first bulk-copied into
-// shared memory by TMA when they form a whole aligned chunk): Eq. 4 constrained scale
-// s = exp(s_opt) + s_min (Sec. 4.1),
-// Eq. 1 covariance through M = R diag(s) (Sigma = M M^T, Sec. 3), the local-affine
-// projection of Eq. 2 (Sigma' = (J W M)(J W M)^T + dilation I), conic, opacity, the
-// opacity-aware extent, the tile set (rectangle, or ellipse rows) and the SH colour.
+// Forward (one thread per unit; a CTA's 128 Gaussians of one set are first copied into
+// shared memory by asynchronous 16-byte copies when they form a whole aligned chunk):
+// Eq. 4 constrained scale s = exp(s_opt) + s_min (Sec. 4.1), Eq. 1 covariance through
+// M = R diag(s) (Sigma = M M^T, Sec. 3), the local-affine projection of Eq. 2
+// (Sigma' = (J W M)(J W M)^T + dilation I), conic, opacity, the opacity-aware extent, the
+// tile set (rectangle, or ellipse rows) and the SH colour.
 //
 // Backward (one thread per unit): the chain rule of the same steps, from the per-unit
 // gradient of (u, v, conic, opacity, rgb) that the blending backward accumulated, to the
@@ -146,9 +146,10 @@ __device__ __forceinline__ void sh_colour(const SetP& S, uint32_t gi, const View
   }
 }
 
-// Bulk (TMA) staging of a CTA's kStageN consecutive Gaussians: one thread arms an mbarrier with
-// the byte count and issues one cp.async.bulk per parameter array; every thread then waits
-// on the barrier (bounded) and reads its Gaussian from shared memory.
+// Staging of a CTA's kStageN consecutive Gaussians: every thread issues its share of 16-byte
+// cp.async requests for each parameter array (SH, means, rotations, scales, opacity logits),
+// waits for its own requests and meets the others at a barrier; then each thread reads its
+// Gaussian from shared memory. Nothing waits on a spin loop, and no copy outlives the barrier.
 constexpr int kStageN = 128;
 struct PreStage {
   float sh[kStageN * 48];
@@ -156,7 +157,6 @@ struct PreStage {
   float4 quats[kStageN];
   float s_opt[kStageN * 3];
   float logit[kStageN];
-  unsigned long long bar;
 };
 
 template <int MAXV>
@@ -167,29 +167,21 @@ __global__ void __launch_bounds__(kStageN) k_preprocess(const __grid_constant__ 
   const uint32_t u = blockIdx.x * (uint32_t)kStageN + threadIdx.x;
   const bool in_range = u < b.units;   // always true (units are padded to 1024); kept for safety
   const ViewP& V = b.views[view_of_unit(b, in_range ? u : 0u)];
-  // a whole chunk of one set (no selection, all kStageN Gaussians present): bulk-copy it
+  // a whole chunk of one set (no selection, all kStageN Gaussians present): stage it (the
+  // condition is the same for every thread of the CTA, whose units lie in one view)
   const uint32_t local0 = blockIdx.x * (uint32_t)kStageN - V.unit_off;
   const SetP& S0 = b.sets[V.sel ? 0 : V.set];
   const bool staged = !V.sel && S0.bulk_ok && local0 + kStageN <= V.cap &&
                       local0 + kStageN <= (uint32_t)S0.n;
   if (staged) {
-    const uint32_t bar = smem_addr(&stg.bar);
     const int K = (S0.deg + 1) * (S0.deg + 1);
-    const uint32_t shb = kStageN * 12u * (uint32_t)K;   // 3 K floats per Gaussian
-    if (threadIdx.x == 0) {
-      bulk_init(bar);
-      bulk_expect(bar, shb + kStageN * (12u + 16u + 12u + 4u));
-      bulk_load(stg.sh, S0.sh + 3ull * K * local0, shb, bar);
-      bulk_load(stg.means, S0.means + 3ull * local0, kStageN * 12u, bar);
-      bulk_load(stg.quats, S0.quats + 4ull * local0, kStageN * 16u, bar);
-      bulk_load(stg.s_opt, S0.s_opt + 3ull * local0, kStageN * 12u, bar);
-      bulk_load(stg.logit, S0.logit + local0, kStageN * 4u, bar);
-    }
+    async_copy(stg.sh, S0.sh + 3ull * K * local0, kStageN * 12u * (uint32_t)K);
+    async_copy(stg.means, S0.means + 3ull * local0, kStageN * 12u);
+    async_copy(stg.quats, S0.quats + 4ull * local0, kStageN * 16u);
+    async_copy(stg.s_opt, S0.s_opt + 3ull * local0, kStageN * 12u);
+    async_copy(stg.logit, S0.logit + local0, kStageN * 4u);
+    async_copy_wait();
     __syncthreads();
-    if (!bulk_wait(bar, 0)) {
-      set_status(ws.status, FLOD_DEV_TIMEOUT);
-      if (!bulk_wait(bar, 0)) return;   // copies still in flight: leave the shared memory alone
-    }
   }
   int si = 0;
   uint32_t gi = 0;
@@ -521,9 +513,55 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
   }
 }
 
+// Zero-fill of the gradient buffers of the sets marked in gt.zero: blockIdx.y picks one
+// (set, parameter) buffer, the CTAs of that row stride over it (16-byte stores where the
+// buffer allows them).
+struct ZeroSegs {
+  float* p[5 * FLOD_MAX_SETS];
+  uint64_t n[5 * FLOD_MAX_SETS];
+};
+
+__global__ void __launch_bounds__(256) k_zero_grads(const __grid_constant__ ZeroSegs z) {
+  pdl_entry();
+  float* p = z.p[blockIdx.y];
+  const uint64_t n = z.n[blockIdx.y];
+  const uint64_t stride = (uint64_t)gridDim.x * 256u;
+  uint64_t i = (uint64_t)blockIdx.x * 256u + threadIdx.x;
+  if (!(reinterpret_cast<uintptr_t>(p) & 15u)) {
+    float4* q = reinterpret_cast<float4*>(p);
+    for (uint64_t k = i; k < n / 4; k += stride) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint64_t k = n / 4 * 4 + i; k < n; k += stride) p[k] = 0.f;
+  } else {
+    for (uint64_t k = i; k < n; k += stride) p[k] = 0.f;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
+template <int MAXV>
+cudaError_t launch_zero_grads(const Batch<MAXV>& b, const GradTable& gt, int grid, cudaStream_t st) {
+  ZeroSegs z;
+  int ns = 0;
+  for (int s = 0; s < b.n_sets; ++s) {
+    if (!gt.zero[s] || b.sets[s].n == 0) continue;
+    const uint64_t n = (uint64_t)b.sets[s].n;
+    const uint64_t K = (uint64_t)(b.sets[s].deg + 1) * (b.sets[s].deg + 1);
+    const flod_grads& g = gt.g[s];
+    float* ptr[5] = {g.means, g.quats, g.s_opt, g.opacity_logit, g.sh};
+    const uint64_t cnt[5] = {3 * n, 4 * n, 3 * n, n, 3 * K * n};
+    for (int f = 0; f < 5; ++f) {
+      if (!ptr[f]) continue;
+      z.p[ns] = ptr[f];
+      z.n[ns] = cnt[f];
+      ++ns;
+    }
+  }
+  if (!ns) return cudaSuccess;
+  launch_k(k_zero_grads, dim3((unsigned)max(1, grid / ns), (unsigned)ns), dim3(256), 0, st, z);
+  return cudaGetLastError();
+}
+
 template <int MAXV>
 cudaError_t launch_preprocess(const Batch<MAXV>& b, const Ws& ws, cudaStream_t st) {
   if (b.units == 0) return cudaSuccess;
@@ -548,6 +586,8 @@ cudaError_t launch_preprocess_bwd(const Batch<MAXV>& b, const Ws& ws, const Grad
 
 template cudaError_t launch_preprocess<kMaxViewsSmall>(const BatchS&, const Ws&, cudaStream_t);
 template cudaError_t launch_preprocess<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, cudaStream_t);
+template cudaError_t launch_zero_grads<kMaxViewsSmall>(const BatchS&, const GradTable&, int, cudaStream_t);
+template cudaError_t launch_zero_grads<FLOD_MAX_VIEWS>(const BatchL&, const GradTable&, int, cudaStream_t);
 template cudaError_t launch_preprocess_bwd<kMaxViewsSmall>(const BatchS&, const Ws&, const GradTable&, cudaStream_t);
 template cudaError_t launch_preprocess_bwd<FLOD_MAX_VIEWS>(const BatchL&, const Ws&, const GradTable&, cudaStream_t);
 

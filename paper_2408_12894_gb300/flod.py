@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
         L.flod_workspace_layout.argtypes = [P, I, P, I, U64, P, P, P, P, P]
         L.flod_preprocess.argtypes = [P, I, P, I, P, P, SZ, U64, P]
         L.flod_bin_sort.argtypes = [P, I, P, I, P, P, SZ, U64, P, P]
+        L.flod_bin_sort_phase.argtypes = [P, I, P, I, P, P, SZ, U64, P, I, P]
         L.flod_render_fwd.argtypes = [P, I, P, I, P, P, SZ, U64, P, P, P, P]
         L.flod_render_bwd.argtypes = [P, I, P, I, P, P, SZ, U64, P, P, P, P, P]
         L.flod_blend_bwd.argtypes = [P, I, P, I, P, P, SZ, U64, P, P, P, P]
@@ -109,6 +110,7 @@ def lib() -> C.CDLL:
         L.flod_status_string.argtypes = [I]
         L.flod_status_string.restype = C.c_char_p
         for name in ("flod_workspace_layout", "flod_preprocess", "flod_bin_sort",
+                     "flod_bin_sort_phase",
                      "flod_render_fwd", "flod_render_bwd", "flod_blend_bwd",
                      "flod_preprocess_bwd", "flod_select_levels", "flod_select_levels_noalloc",
                      "flod_adjust_scale", "flod_read_status"):
@@ -234,6 +236,17 @@ def flod_bin_sort(sets, views, cfg, ws: torch.Tensor, pair_capacity: int, d_pair
            "flod_bin_sort")
 
 
+#: flod_bin_sort_phase phases, in call order
+BIN_PHASE_DEPTH, BIN_PHASE_EMIT, BIN_PHASE_TILES, BIN_PHASE_RANGES = 1, 2, 3, 4
+
+
+def flod_bin_sort_phase(sets, views, cfg, ws: torch.Tensor, pair_capacity: int, phase: int,
+                        d_pair_count=None, stream=None):
+    _check(lib().flod_bin_sort_phase(sets, len(sets), views, len(views), C.byref(cfg),
+                                     ws.data_ptr(), ws.numel(), pair_capacity, _ptr(d_pair_count),
+                                     phase, _stream(stream)), "flod_bin_sort_phase")
+
+
 def flod_render_fwd(sets, views, cfg, ws, pair_capacity, out_rgb, out_T, out_nc, stream=None):
     _check(lib().flod_render_fwd(sets, len(sets), views, len(views), C.byref(cfg), ws.data_ptr(),
                                  ws.numel(), pair_capacity, out_rgb.data_ptr(), out_T.data_ptr(),
@@ -259,10 +272,19 @@ def flod_preprocess_bwd(sets, views, cfg, ws, pair_capacity, grads, stream=None)
                                      _stream(stream)), "flod_preprocess_bwd")
 
 
-def grads_struct(grads, overwrite: bool = False):
+#: flod_grads.overwrite values
+GRAD_ACCUMULATE, GRAD_OVERWRITE, GRAD_ZERO_FIRST = 0, 1, 2
+
+
+def grads_struct(grads, overwrite=False):
     """grads: per set, a sequence of 5 tensors (or None) in GaussianSet.FIELDS order.
-    overwrite: write the gradients instead of adding to them (see flod_grads)."""
-    return _array(Grads, [Grads(*[_ptr(t) for t in gr], int(overwrite)) for gr in grads])
+    overwrite: one flod_grads.overwrite value for every set, or a sequence with one per set
+    (0 / False: add to the buffers; 1 / True: write every gradient of a set rendered by one
+    view; 2: the library zero-fills the buffers first, then adds)."""
+    modes = list(overwrite) if isinstance(overwrite, (list, tuple)) else [overwrite] * len(grads)
+    if len(modes) != len(grads):
+        raise FlodError("grads_struct: one overwrite value per set")
+    return _array(Grads, [Grads(*[_ptr(t) for t in gr], int(m)) for gr, m in zip(grads, modes)])
 
 
 def flod_select_scratch_size(levels) -> int:
@@ -340,6 +362,7 @@ class Rasterizer:
         dev = self.sets[0].means.device
         self.pair_count = torch.zeros(1, dtype=torch.int64, device=dev)
         self.npix = npix
+        self.generation = 0     # workspace rewrites so far (preprocess, bin_sort calls)
         _, self.unit_off, self.tile_off, self.pix_off = flod_workspace_layout(
             self.c_sets, self.c_views, self.pair_capacity, self.cfg)
 
@@ -362,19 +385,27 @@ class Rasterizer:
                 torch.empty(self.npix, dtype=torch.int32, device=dev))
 
     def preprocess(self, stream=None):
+        self.generation += 1
         flod_preprocess(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity, stream)
 
     def bin_sort(self, stream=None):
+        self.generation += 1
         flod_bin_sort(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity,
                       self.pair_count, stream)
+
+    def bin_sort_phase(self, phase: int, stream=None):
+        """One part of bin_sort (BIN_PHASE_*); the four in order equal bin_sort."""
+        self.generation += 1
+        flod_bin_sort_phase(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity,
+                            phase, self.pair_count, stream)
 
     def render_fwd(self, out_rgb, out_T, out_nc, stream=None):
         flod_render_fwd(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity, out_rgb,
                         out_T, out_nc, stream)
 
-    def render_bwd(self, dL, out_T, out_nc, grads, stream=None):
+    def render_bwd(self, dL, out_T, out_nc, grads, stream=None, overwrite=False):
         flod_render_bwd(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity, dL, out_T,
-                        out_nc, grads_struct(grads), stream)
+                        out_nc, grads_struct(grads, overwrite), stream)
 
     def blend_bwd(self, dL, out_T, out_nc, stream=None):
         flod_blend_bwd(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity, dL, out_T,
@@ -396,21 +427,37 @@ class Rasterizer:
         p = int(self.pair_count.item())
         if p <= self.pair_capacity:
             return True
-        self.pair_capacity = min(MAX_PAIRS, int(p * 1.25) + 1024)
         if p > MAX_PAIRS:
             raise FlodError(f"{p} pairs exceed the library maximum {MAX_PAIRS}")
+        self.pair_capacity = min(MAX_PAIRS, int(p * 1.25) + 1024)
         self._alloc()
         return False
 
     def forward(self, stream=None):
+        """preprocess -> bin_sort (regrowing the pair capacity if needed) -> render_fwd."""
         out = self.new_outputs()
         for _ in range(3):
             self.preprocess(stream)
             self.bin_sort(stream)
             if self.ensure_capacity():
                 break
+        else:
+            raise FlodError("pair capacity did not converge in three attempts")
         self.render_fwd(*out, stream)
         return out
+
+    def grad_modes(self):
+        """Per set, the cheapest legal flod_grads.overwrite value for a backward into fresh
+        (uninitialised) buffers: 1 where exactly one view renders the set as a whole set and
+        no view uses a selection list, else 2 (zero-filled by the library first)."""
+        direct = [0] * len(self.sets)
+        n_sel = 0
+        for v in self.views:
+            if v.sel:
+                n_sel += 1
+            else:
+                direct[v.set] += 1
+        return [GRAD_OVERWRITE if d == 1 and n_sel == 0 else GRAD_ZERO_FIRST for d in direct]
 
     def region(self, name: str, dtype, count: int, index: int | None = None) -> torch.Tensor:
         """A typed view of a workspace region (for tests and diagnostics)."""
@@ -440,6 +487,9 @@ class _Rasterize(torch.autograd.Function):
     def forward(ctx, rast: Rasterizer, *params):
         rgb, T, nc = rast.forward()
         ctx.rast = rast
+        # the backward re-walks the workspace this forward sorted: remember which one
+        ctx.generation = rast.generation
+        ctx.ws_ptr = rast.ws.data_ptr()
         ctx.save_for_backward(T, nc)
         ctx.mark_non_differentiable(T, nc)
         return rgb, T, nc
@@ -447,9 +497,14 @@ class _Rasterize(torch.autograd.Function):
     @staticmethod
     def backward(ctx, d_rgb, d_T, d_nc):
         rast = ctx.rast
+        if rast.generation != ctx.generation or rast.ws.data_ptr() != ctx.ws_ptr:
+            raise FlodError("rasterize backward: the Rasterizer ran another forward (or regrew "
+                            "its workspace) after this one; its sorted pairs are gone. Use one "
+                            "Rasterizer per differentiated render.")
         T, nc = ctx.saved_tensors
-        grads = [[torch.zeros_like(getattr(s, f)) for f in GaussianSet.FIELDS] for s in rast.sets]
-        rast.render_bwd(d_rgb.contiguous(), T, nc, grads)
+        # fresh buffers, written (or zero-filled) by the library itself: no torch fill kernels
+        grads = [[torch.empty_like(getattr(s, f)) for f in GaussianSet.FIELDS] for s in rast.sets]
+        rast.render_bwd(d_rgb.contiguous(), T, nc, grads, overwrite=rast.grad_modes())
         flat = [g for per_set in grads for g in per_set]
         return (None, *flat)
 

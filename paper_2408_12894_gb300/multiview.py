@@ -68,9 +68,11 @@ class BatchedStep:
         self.dL = dL
         self.graph = None
         if backward:
-            self.grads = [[torch.zeros_like(getattr(s, f)) for f in flod.GaussianSet.FIELDS]
+            self.grads = [[torch.empty_like(getattr(s, f)) for f in flod.GaussianSet.FIELDS]
                           for s in self.sets]
-            self.grads_c = flod.grads_struct(self.grads)
+            # the library writes (mode 1) or zero-fills then accumulates (mode 2) every set's
+            # gradients inside the step: no fill kernels of its own are needed here
+            self.grads_c = flod.grads_struct(self.grads, self.rast.grad_modes())
 
     def set_camera(self, i: int, cam: dict):
         """Move job i's camera (and, for a selective job, its selection origin). A captured
@@ -99,9 +101,6 @@ class BatchedStep:
         r.bin_sort(stream)
         r.render_fwd(*self.out, stream)
         if self.backward:
-            for per_set in self.grads:
-                for t in per_set:
-                    t.zero_()
             r.blend_bwd(self.dL, self.out[1], self.out[2], stream)
             r.preprocess_bwd(self.grads_c, stream)
 

@@ -16,7 +16,10 @@ from paper_2408_12894_gb300 import flod, synth
 IMG_MAX_ABS = 2e-4      # per pixel and channel, on >= 99.9% of pixels
 IMG_FRAC = 0.999
 IMG_MEAN_ABS = 1e-5     # per channel
-GRAD_REL = 1e-3         # ||g_gpu - g_ref|| / ||g_ref|| per parameter tensor
+GRAD_REL = 1e-3         # ||g_gpu - g_ref|| / ||g_ref|| per parameter tensor, and per entry
+GRAD_FLOOR = 1e-6       # elementwise: |d| <= GRAD_REL |g_ref| + GRAD_FLOOR max |g_ref|
+DECISION_MARGIN = 2e-4  # relative distance of a blending decision to its threshold below
+                        # which float32 and float64 may decide differently
 
 
 def rasterizer(sets_np, cams, s_mins, view_sets=None, cfg=None, pair_capacity=None):
@@ -222,3 +225,134 @@ def inject_units(rast, view: int, f: dict):
 def clear_units(rast):
     U = rast.layout.units
     rast.region("tiles_touched", torch.int32, U).zero_()
+
+
+def assert_grad_close(got: dict, ref: dict, what: str = ""):
+    """Both bars of the gradient parity: per parameter tensor, relative L2 error <= GRAD_REL,
+    and per entry |g - g_ref| <= GRAD_REL |g_ref| + GRAD_FLOOR max|g_ref| (max over the
+    compared entries of that tensor)."""
+    for k in ref:
+        a = np.asarray(got[k], dtype=np.float64).reshape(-1)
+        b = np.asarray(ref[k], dtype=np.float64).reshape(-1)
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            assert np.all(a == 0), f"{what} {k}: nonzero gradient where the oracle's is zero"
+            continue
+        rel = np.linalg.norm(a - b) / nb
+        assert rel <= GRAD_REL, f"{what} {k}: relative L2 error {rel:.2e}"
+        bound = GRAD_REL * np.abs(b) + GRAD_FLOOR * np.abs(b).max()
+        bad = np.nonzero(np.abs(a - b) > bound)[0]
+        assert bad.size == 0, (f"{what} {k}: {bad.size} of {b.size} entries off, worst "
+                               f"|d|={np.abs(a - b)[bad].max():.3e} at |g_ref|={np.abs(b)[bad[0]]:.3e}")
+
+
+def blend_decision_margin(pix_xy, mean2d, conic, opacity):
+    """FP64 relative distance of every discrete blending decision of each pixel to its
+    threshold: alpha against 1/255 for each Gaussian up to the one that stops the pixel, and
+    T (1 - alpha) against 1e-4 for each blended one. A pixel whose smallest margin is below
+    DECISION_MARGIN may blend another set of Gaussians in float32; elsewhere n_contrib has
+    one right answer. Inputs are torch float64 (pixel centres [P,2], the tile's Gaussians
+    in list order)."""
+    with torch.no_grad():
+        a_raw = R.alpha_raw(pix_xy, mean2d, conic, opacity).numpy()
+    if a_raw.shape[1] == 0:
+        return np.full(a_raw.shape[0], np.inf)
+    a = np.minimum(a_raw, R.ALPHA_MAX)
+    kept = a >= R.ALPHA_MIN
+    m_skip = np.where(a_raw < R.ALPHA_MAX, np.abs(a_raw / R.ALPHA_MIN - 1.0), np.inf)
+    t_after = np.cumprod(1.0 - np.where(kept, a, 0.0), axis=1)
+    m_stop = np.where(kept, np.abs(t_after / R.T_MIN - 1.0), np.inf)
+    live = t_after >= R.T_MIN
+    K = a.shape[1]
+    stop = np.where(live.all(axis=1), K - 1, np.argmin(live, axis=1))
+    upto = np.arange(K)[None, :] <= stop[:, None]
+    m = np.where(upto, np.minimum(m_skip, m_stop), np.inf)
+    return m.min(axis=1)
+
+
+def tile_sample(ranges_tile, tiles_x, tiles_y, n, rng):
+    """About n tiles of one view: stratified over the pair-count distribution (empty to
+    heaviest) plus the four corners and a ragged last row / column tile."""
+    counts = ranges_tile[:, 1] - ranges_tile[:, 0]
+    order = np.argsort(counts, kind="stable")
+    k = max(n - 6, 1)
+    picks = set(int(order[int(q)]) for q in np.linspace(0, order.size - 1, k))
+    picks |= {0, tiles_x - 1, tiles_x * (tiles_y - 1), tiles_x * tiles_y - 1,
+              (tiles_y - 1) * tiles_x + tiles_x // 2, (tiles_y // 2) * tiles_x + tiles_x - 1}
+    extra = rng.choice(tiles_x * tiles_y, size=2, replace=False)
+    picks |= set(int(t) for t in extra)
+    return sorted(picks)
+
+
+def compare_tiles(img, T, nc, ref_tiles, pre, lists, cam, ocfg, gpu_lists=None):
+    """GPU outputs ([3,H,W], [H,W], [H,W] numpy) against the oracle's render of the sampled
+    tiles (R.render_tiles). n_contrib is a 1-based position in a tile's list: with
+    ``gpu_lists`` = (the GPU's sorted Gaussian indices, its [tiles, 2] ranges) of this view,
+    each side's position is turned into the Gaussian it names and those are compared (the two
+    lists may differ by Gaussians at the edge of their tile sets, which no pixel blends);
+    without it the lists are the same and positions are compared. Returns (per-pixel max abs
+    error over channels, per-channel abs errors, T abs errors, last blended Gaussian equal
+    where the decisions are unambiguous, fraction of pixels with an ambiguous decision)."""
+    keys, vals, ranges, tx, ty = lists
+    pix_err, ch_err, t_err, nc_ok, amb = [], [], [], [], []
+    for t, (col, tf, last) in ref_tiles.items():
+        x0, y0, x1, y1 = R.tile_pixels(t, tx, cam, ocfg)
+        d = np.abs(img[:, y0:y1, x0:x1].astype(np.float64) - col).reshape(3, -1)
+        pix_err.append(d.max(axis=0))
+        ch_err.append(d)
+        t_err.append(np.abs(T[y0:y1, x0:x1].astype(np.float64) - tf).reshape(-1))
+        s, e = ranges[t]
+        g = torch.as_tensor(vals[s:e].astype(np.int64))
+        gx, gy = np.meshgrid(np.arange(x0, x1), np.arange(y0, y1))
+        pix = torch.as_tensor(np.stack([gx.ravel() + 0.5, gy.ravel() + 0.5], 1).astype(np.float64))
+        m = blend_decision_margin(pix, pre["mean2d"].detach()[g], pre["conic"].detach()[g],
+                                  pre["opacity"].detach()[g])
+        clear = m > DECISION_MARGIN
+        got = nc[y0:y1, x0:x1].reshape(-1).astype(np.int64)
+        want = last.reshape(-1).astype(np.int64)
+        if gpu_lists is not None:
+            gv, gr = gpu_lists
+            gs, ge = (int(x) for x in gr[t])
+            got = np.where(got > 0, np.asarray(gv[gs:ge], np.int64)[np.maximum(got - 1, 0)]
+                           if ge > gs else -1, -1)
+            want = np.where(want > 0, vals[s:e].astype(np.int64)[np.maximum(want - 1, 0)]
+                            if e > s else -1, -1)
+        nc_ok.append(np.where(clear, got == want, True))
+        amb.append(~clear)
+    return (np.concatenate(pix_err), np.concatenate(ch_err, axis=1), np.concatenate(t_err),
+            np.concatenate(nc_ok), float(np.concatenate(amb).mean()))
+
+
+def assert_tiles_close(img, T, nc, ref_tiles, pre, lists, cam, ocfg, what="", gpu_lists=None):
+    """The image bar on the sampled tiles' pixels (>= 99.9% within 2e-4, mean abs <= 1e-5
+    per channel), T within 2e-4 on >= 99.9% of them, and the last blended Gaussian equal
+    wherever the blending decisions are unambiguous (ambiguous pixels: under 5%)."""
+    pe, ce, te, ncok, amb = compare_tiles(img, T, nc, ref_tiles, pre, lists, cam, ocfg, gpu_lists)
+    frac = float((pe <= IMG_MAX_ABS).mean())
+    assert frac >= IMG_FRAC, f"{what}: only {frac:.5f} of {pe.size} pixels within {IMG_MAX_ABS}"
+    mean = ce.mean(axis=1)
+    assert np.all(mean <= IMG_MEAN_ABS), f"{what}: mean abs error per channel {mean}"
+    tfrac = float((te <= IMG_MAX_ABS).mean())
+    assert tfrac >= IMG_FRAC, f"{what}: T within {IMG_MAX_ABS} on only {tfrac:.5f}"
+    assert amb < 0.05, f"{what}: {amb:.4f} of pixels have an ambiguous blending decision"
+    assert ncok.all(), f"{what}: last blended Gaussian differs on {int((~ncok).sum())} pixels"
+    return pe.size
+
+
+def gpu_view_lists(rast, view: int):
+    """The GPU's sorted Gaussian indices of one view (unit offset of the view removed; a
+    selective view's indices are positions in its selection list) and the view's [tiles, 2]
+    ranges into them. Only the view's slice of the pair list is read back (a view's pairs are
+    contiguous: tile ids are global, views in order)."""
+    torch.cuda.synchronize()
+    fin = int(rast.region("plan", torch.int32, 64)[63].item())
+    t0, t1 = rast.tile_off[view], rast.tile_off[view + 1]
+    rg = rast.region("ranges", torch.int32, 2 * rast.layout.tiles).view(-1, 2)[t0:t1]
+    rg = rg.cpu().numpy().astype(np.int64)
+    full = rg[:, 1] > rg[:, 0]
+    lo = int(rg[full, 0].min()) if full.any() else 0
+    hi = int(rg[full, 1].max()) if full.any() else 0
+    vals = rast.region("vals", torch.int32, rast.pair_capacity, fin)[lo:hi]
+    vals = vals.cpu().numpy().astype(np.int64)
+    rg = np.where(full[:, None], rg - lo, 0)
+    return vals - rast.unit_off[view], rg

@@ -95,6 +95,15 @@ def test_batched_gradients_equal_sum_of_per_view():
                 assert torch.linalg.norm(a).item() == 0
                 continue
             assert torch.linalg.norm(a - b).item() <= 1e-4 * nb
+        # elementwise: two float32 summation orders of the same terms (atomics in the batch,
+        # one view at a time here), so entries that are sums of cancelling terms may differ
+        # by a few float32 roundings of the largest terms; the oracle parity of the batched
+        # gradient itself is in test_gpu_backward (persistent launch) and in the full-size
+        # batch tests
+        for a, b in zip(a_set, b_set):
+            d = (a - b).abs()
+            bound = 1e-3 * b.abs() + 1e-5 * b.abs().max()
+            assert bool((d <= bound).all()), float((d - bound).max())
 
 
 def test_graph_replay_matches_eager():

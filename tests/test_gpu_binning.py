@@ -30,12 +30,17 @@ def _oracle_lists(rast, fs, cams, ocfg):
     return k, v, R.tile_ranges(k, rast.layout.tiles)
 
 
-def _run(rast, fs, cams):
+def _run(rast, fs, cams, phased=False):
     ocfg = oracle_cfg(rast.cfg)
     clear_units(rast)
     for i, f in enumerate(fs):
         inject_units(rast, i, f)
-    rast.bin_sort()
+    if phased:   # the four parts of flod_bin_sort_phase, in order
+        for ph in (flod.BIN_PHASE_DEPTH, flod.BIN_PHASE_EMIT, flod.BIN_PHASE_TILES,
+                   flod.BIN_PHASE_RANGES):
+            rast.bin_sort_phase(ph)
+    else:
+        rast.bin_sort()
     keys, vals, ranges, P, status = sorted_pairs(rast)
     k, v, rg = _oracle_lists(rast, fs, cams, ocfg)
     assert status == 0, status
@@ -60,13 +65,14 @@ def test_binning_single_view(tile, rule):
     assert P > 0
 
 
-def test_binning_batched_views_ragged_sizes():
+@pytest.mark.parametrize("phased", [False, True])
+def test_binning_batched_views_ragged_sizes(phased):
     g = synth.gaussian_set(2, 5003, k=16, radius=5.0, sh_degree=0, s_mean=-2.5)
     cams = [synth.camera((15.0 * np.cos(a), 1.0, 15.0 * np.sin(a)), w, h)
             for a, (w, h) in zip((0.0, 1.3, 2.9, 4.4), ((333, 201), (128, 128), (97, 250), (640, 360)))]
-    cfg = flod.default_config()
+    cfg = flod.default_config(persistent=1 if phased else 0)
     rast = rasterizer([g], cams, [0.0], cfg=cfg)
-    _run(rast, _scene_units(g, 0.0, cams, cfg), cams)
+    _run(rast, _scene_units(g, 0.0, cams, cfg), cams, phased)
 
 
 @pytest.mark.parametrize("rule", [2, 0])

@@ -1,12 +1,22 @@
 """Parity at the full benchmark sizes, in the launch configuration bench.py times (16x16
-tiles, batch 128, one CTA per tile): sampled pixels against the oracle's per-pixel render
-over every Gaussian, sampled Gaussians' gradients against the oracle's exact per-footprint
-gradient, and invariants that hold at any size."""
+tiles, batch 128, one CTA per tile):
+
+* whole sampled tiles (stratified by pair count, ragged edges included) against the oracle's
+  tiled render, itself pinned equal to the per-pixel definition: >= 99.9% of the pixels
+  within 2e-4, mean abs <= 1e-5 per channel, T likewise, and the last blended Gaussian of
+  every pixel whose blending decisions are unambiguous;
+* sampled Gaussians' full parameter gradients against the oracle's exact per-footprint
+  gradient, per tensor (relative L2 1e-3) and per entry;
+* the kernel's own tile lists cover every pixel where a sampled unit's opacity reaches 1/255
+  (FP64 brute force) and list no tile the support misses;
+* invariants that hold at any size.
+"""
 import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import GRAD_REL, IMG_MAX_ABS, rasterizer
+from gpu_helpers import (DECISION_MARGIN, assert_grad_close, assert_tiles_close, gpu_view_lists,
+                         rasterizer, sorted_pairs, tile_sample)
 from oracle import gaussians as OG
 from oracle import raster as R
 from paper_2408_12894_gb300 import flod, synth
@@ -42,6 +52,9 @@ def _invariants(rast, rgb, T, nc):
     same = tiles[1:] == tiles[:-1]
     depth = rast.region("depth", torch.float32, U)[vals]
     assert bool((depth[1:][same] >= depth[:-1][same]).all())
+    # per unit, its pairs' count equals its tile count
+    per_unit = torch.bincount(vals, minlength=U)
+    assert torch.equal(per_unit, tt)
     rg = rast.region("ranges", torch.int32, 2 * rast.layout.tiles).view(-1, 2).to(torch.int64)
     nz = rg[rg[:, 1] > rg[:, 0]]
     assert int(nz[0, 0]) == 0 and int(nz[-1, 1]) == P and bool((nz[1:, 0] == nz[:-1, 1]).all())
@@ -49,35 +62,16 @@ def _invariants(rast, rgb, T, nc):
     assert bool(torch.isfinite(rgb).all())
 
 
-def _pixels_vs_oracle(g, s_min, cam, img, n=48, seed=0):
-    rng = np.random.default_rng(seed)
-    pix = np.stack([rng.integers(0, cam["width"], n), rng.integers(0, cam["height"], n)], 1)
-    with torch.no_grad():
-        pre = R.preprocess(R.params(g), g["sh_degree"], s_min, cam, R.Config())
-        errs = []
-        for k in range(0, n, 4):
-            col, _ = R.render_brute(pre, cam, R.Config(), pixels=pix[k:k + 4])
-            want = col.numpy()
-            got = img[:, pix[k:k + 4, 1], pix[k:k + 4, 0]].T
-            errs.append(np.abs(got - want).max(axis=1))
-    errs = np.concatenate(errs)
-    assert (errs <= IMG_MAX_ABS).mean() >= 1 - 1.5 / n, errs
-    assert errs.mean() <= 2e-5, errs.mean()
-    return pre
+def _grad_check(g, s_min, cam, dL_img, got, pre, lists, sample, what):
+    ref = R.sampled_gradients(g, g["sh_degree"], s_min, cam, R.Config(), dL_img, sample,
+                              lists=lists, pre=pre)
+    assert_grad_close({k: got[k][sample] for k in ref}, ref, what)
 
 
-def _sampled_grad_check(g, s_min, cam, dL_img, got, pre, sample):
-    ref = R.sampled_gradients(g, g["sh_degree"], s_min, cam, R.Config(), dL_img, sample, pre=pre)
-    for k in ref:
-        a = got[k][sample].reshape(len(sample), -1).astype(np.float64)
-        b = ref[k].reshape(len(sample), -1)
-        scale = np.abs(b).max() + 1e-30
-        for i in range(len(sample)):
-            err = np.linalg.norm(a[i] - b[i])
-            assert err <= GRAD_REL * np.linalg.norm(b[i]) + 1e-5 * scale, (k, sample[i], err)
-
-
-def test_level5_3M_1080p():
+@pytest.fixture(scope="module")
+def level5_run():
+    """One GPU forward + backward of level 5 (3M Gaussians, 1920x1080) and the oracle's FP64
+    preprocess and tile lists of the same camera."""
     g = _level5()
     cam = synth.level_camera()
     s_min = synth.LEVEL_SMIN[-1]
@@ -88,14 +82,85 @@ def test_level5_3M_1080p():
     dL = synth.upstream_gradient(11, [cam])
     (rgb * torch.as_tensor(dL, device="cuda")).sum().backward()
     _invariants(rast, rgb, T, nc)
-    img = rgb.detach().view(3, 1080, 1920).cpu().numpy()
-    pre = _pixels_vs_oracle(g, s_min, cam, img)
-    got = {f: getattr(rast.sets[0], f).grad.cpu().numpy() for f in flod.GaussianSet.FIELDS}
+    out = {"img": rgb.detach().view(3, 1080, 1920).cpu().numpy(),
+           "T": T.view(1080, 1920).cpu().numpy(), "nc": nc.view(1080, 1920).cpu().numpy(),
+           "grads": {f: getattr(rast.sets[0], f).grad.cpu().numpy() for f in flod.GaussianSet.FIELDS}}
+    out["gpu_lists"] = gpu_view_lists(rast, 0)
+    keys, vals, ranges, _, _ = sorted_pairs(rast)
+    out["gpu_pairs"] = (keys >> np.uint64(32)).astype(np.int64), vals.astype(np.int64)
+    with torch.no_grad():
+        pre = R.preprocess(R.params(g), 3, s_min, cam, R.Config())
+    lists = R.tile_lists(pre, cam, R.Config())
+    del rast, rgb, T, nc
+    torch.cuda.empty_cache()
+    return g, cam, s_min, dL, pre, lists, out
+
+
+def test_level5_3M_1080p_tiles(level5_run):
+    g, cam, s_min, dL, pre, lists, out = level5_run
+    rng = np.random.default_rng(0)
+    tiles = tile_sample(lists[2], lists[3], lists[4], 40, rng)
+    ref = R.render_tiles(pre, cam, R.Config(), lists, tiles)
+    n = assert_tiles_close(out["img"], out["T"], out["nc"], ref, pre, lists, cam, R.Config(),
+                           "level 5, 3M, 1080p", out["gpu_lists"])
+    assert n >= 30 * 256
+
+
+def test_level5_3M_1080p_gradients(level5_run):
+    g, cam, s_min, dL, pre, lists, out = level5_run
     vis = np.nonzero(pre["tiles_touched"] > 0)[0]
     rng = np.random.default_rng(1)
     # a few of each size class: carried level-1 Gaussians (largest) to fresh level-5 ones
     sample = np.concatenate([rng.choice(vis[vis < 20_000], 3), rng.choice(vis[vis >= 1_000_000], 5)])
-    _sampled_grad_check(g, s_min, cam, dL.reshape(3, 1080, 1920), got, pre, sample)
+    _grad_check(g, s_min, cam, dL.reshape(3, 1080, 1920), out["grads"], pre, lists, sample,
+                "level 5 sampled Gaussians")
+
+
+def test_level5_3M_1080p_tile_lists_cover_the_support(level5_run):
+    """Every pixel where a sampled unit's FP64 opacity o G reaches 1/255 lies in a tile the
+    kernel listed for it (pixels within a relative DECISION_MARGIN of the threshold are left
+    out), and every listed tile holds a pixel where o G >= 0.99 / 255 (the support is widened
+    by a relative 2^-10 of tau in the kernel)."""
+    g, cam, s_min, dL, pre, lists, out = level5_run
+    tiles_k, vals_k = out["gpu_pairs"]
+    tt = pre["tiles_touched"]
+    vis = np.nonzero(tt > 0)[0]
+    rng = np.random.default_rng(3)
+    big = vis[np.argsort(tt[vis])[-12:]]
+    sample = np.unique(np.concatenate([rng.choice(vis, 600, replace=False), big]))
+    mask = np.isin(vals_k, sample)
+    listed = {}
+    for u, t in zip(vals_k[mask], tiles_k[mask]):
+        listed.setdefault(int(u), set()).add(int(t))
+    W, H, T = cam["width"], cam["height"], 16
+    tx = -(-W // T)
+    mean2d = pre["mean2d"].detach().numpy()
+    conic = pre["conic"].detach().numpy()
+    op = pre["opacity"].detach().numpy()
+    checked = 0
+    for u in sample:
+        a, b, c = conic[u]
+        o = op[u]
+        # bounding box of o exp(-q/2) >= 1/255: |dx| <= sqrt(tau A), A = c / det (conic inverse)
+        tau = 2.0 * np.log(255.0 * o)
+        det = a * c - b * b
+        rx, ry = np.sqrt(max(tau, 0) * c / det) + 1, np.sqrt(max(tau, 0) * a / det) + 1
+        x0, x1 = max(int(mean2d[u, 0] - rx), 0), min(int(mean2d[u, 0] + rx) + 1, W)
+        y0, y1 = max(int(mean2d[u, 1] - ry), 0), min(int(mean2d[u, 1] + ry) + 1, H)
+        got = listed.get(int(u), set())
+        if x0 >= x1 or y0 >= y1:
+            continue
+        gx, gy = np.meshgrid(np.arange(x0, x1), np.arange(y0, y1))
+        dx, dy = gx + 0.5 - mean2d[u, 0], gy + 0.5 - mean2d[u, 1]
+        val = o * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))
+        inside = val * 255.0 >= 1.0 + DECISION_MARGIN
+        need = set(((gy[inside] // T) * tx + gx[inside] // T).tolist())
+        assert need <= got, f"unit {u}: tiles {sorted(need - got)[:8]} missing"
+        near = val * 255.0 >= 0.99
+        have = set(((gy[near] // T) * tx + gx[near] // T).tolist())
+        assert got <= have, f"unit {u}: listed tiles {sorted(got - have)[:8]} miss the support"
+        checked += 1
+    assert checked >= 500
 
 
 def test_multiview_500k_720p_eight_views():
@@ -108,24 +173,30 @@ def test_multiview_500k_720p_eight_views():
     (rgb * torch.as_tensor(dL, device="cuda")).sum().backward()
     _invariants(rast, rgb, T, nc)
     imgs = flod.image_views(rgb.detach(), rast.views, 3)
+    Ts = flod.image_views(T, rast.views, 1)
+    ncs = flod.image_views(nc, rast.views, 1)
     got = {f: getattr(rast.sets[0], f).grad.cpu().numpy() for f in flod.GaussianSet.FIELDS}
     rng = np.random.default_rng(2)
-    pres = []
+    per_view = {}
     for v in (0, 5):
-        pres.append(_pixels_vs_oracle(g, 0.0, cams[v], imgs[v].cpu().numpy(), n=24, seed=v))
+        c = cams[v]
+        with torch.no_grad():
+            pre = R.preprocess(R.params(g), 3, 0.0, c, R.Config())
+        lists = R.tile_lists(pre, c, R.Config())
+        tiles = tile_sample(lists[2], lists[3], lists[4], 24, rng)
+        ref = R.render_tiles(pre, c, R.Config(), lists, tiles)
+        assert_tiles_close(imgs[v].cpu().numpy(), Ts[v][0].cpu().numpy(), ncs[v][0].cpu().numpy(),
+                           ref, pre, lists, c, R.Config(), f"500k view {v}", gpu_view_lists(rast, v))
+        per_view[v] = pre
     # gradients sum over all eight views: per-view exact footprint gradients, summed
-    vis = np.nonzero(pres[0]["tiles_touched"] > 0)[0]
+    vis = np.nonzero(per_view[0]["tiles_touched"] > 0)[0]
     sample = rng.choice(vis, 6, replace=False)
     ref = None
     off = 0
     for c in cams:
         n = 3 * c["width"] * c["height"]
-        r = R.sampled_gradients(g, 3, 0.0, c, R.Config(), dL[off:off + n].reshape(3, c["height"], c["width"]), sample)
+        r = R.sampled_gradients(g, 3, 0.0, c, R.Config(),
+                                dL[off:off + n].reshape(3, c["height"], c["width"]), sample)
         off += n
         ref = r if ref is None else {k: ref[k] + r[k] for k in ref}
-    for k in ref:
-        a = got[k][sample].reshape(len(sample), -1).astype(np.float64)
-        b = ref[k].reshape(len(sample), -1)
-        scale = np.abs(b).max() + 1e-30
-        for i in range(len(sample)):
-            assert np.linalg.norm(a[i] - b[i]) <= GRAD_REL * np.linalg.norm(b[i]) + 1e-5 * scale, (k, i)
+    assert_grad_close({k: got[k][sample] for k in ref}, ref, "500k eight views")

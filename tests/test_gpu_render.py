@@ -4,8 +4,9 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import (assert_image_close, clear_units, image_compare, inject_units,
-                         oracle_cfg, oracle_pre, oracle_units_f32, rasterizer)
+from gpu_helpers import (DECISION_MARGIN, IMG_FRAC, IMG_MAX_ABS, assert_image_close,
+                         assert_tiles_close, blend_decision_margin, clear_units, gpu_view_lists,
+                         inject_units, oracle_cfg, oracle_pre, oracle_units_f32, rasterizer)
 from oracle import raster as R
 from paper_2408_12894_gb300 import flod, synth
 
@@ -46,27 +47,53 @@ def _stage_render(g, cam, cfg, s_min=0.0):
              "rgb": torch.as_tensor(f["rgb"].astype(np.float64))}
     img, tf, last = R.render_tiled(o_pre, cam, ocfg, lists=(k, v, rg, tx, ty))
     H, W = cam["height"], cam["width"]
+    clear = _unambiguous(o_pre, (k, v, rg, tx, ty), cam, ocfg)
     return (rgb.view(3, H, W).cpu().numpy(), T.view(H, W).cpu().numpy(),
-            nc.view(H, W).cpu().numpy(), img, tf, last)
+            nc.view(H, W).cpu().numpy(), img, tf, last, clear)
+
+
+def _unambiguous(pre, lists, cam, ocfg):
+    """[H, W] mask of the pixels whose blending decisions lie clear of their thresholds
+    (n_contrib then has one right answer in any precision)."""
+    keys, vals, ranges, tx, ty = lists
+    H, W = cam["height"], cam["width"]
+    clear = np.ones((H, W), dtype=bool)
+    for t in range(tx * ty):
+        x0, y0, x1, y1 = R.tile_pixels(t, tx, cam, ocfg)
+        s, e = ranges[t]
+        g = torch.as_tensor(vals[s:e].astype(np.int64))
+        gx, gy = np.meshgrid(np.arange(x0, x1), np.arange(y0, y1))
+        pix = torch.as_tensor(np.stack([gx.ravel() + 0.5, gy.ravel() + 0.5], 1).astype(np.float64))
+        m = blend_decision_margin(pix, pre["mean2d"].detach()[g], pre["conic"].detach()[g],
+                                  pre["opacity"].detach()[g])
+        clear[y0:y1, x0:x1] = (m > DECISION_MARGIN).reshape(y1 - y0, x1 - x0)
+    return clear
+
+
+def _assert_nc(gnc, onc, clear):
+    assert (~clear).mean() < 0.05, f"{(~clear).mean():.4f} of pixels ambiguous"
+    bad = clear & (gnc != onc)
+    assert not bad.any(), f"n_contrib differs on {int(bad.sum())} unambiguous pixels"
 
 
 @pytest.mark.parametrize("tile,batch", [((16, 16), 256), ((8, 8), 32), ((32, 8), 64), ((16, 16), 128)])
 def test_render_stage_matches_oracle(tile, batch):
     g, cams = synth.scene_single_forward()
     cfg = flod.default_config(tile_w=tile[0], tile_h=tile[1], batch=batch)
-    gi, gT, gnc, oi, oT, onc = _stage_render(g, cams[0], cfg)
+    gi, gT, gnc, oi, oT, onc, clear = _stage_render(g, cams[0], cfg)
     assert_image_close(gi, oi)
     np.testing.assert_allclose(gT, oT, atol=2e-4)
-    assert (gnc == onc).mean() >= 0.999
+    _assert_nc(gnc, onc, clear)
 
 
 def test_render_stage_dense_sh3_background():
     g = synth.gaussian_set(4, 20000, k=8, radius=1.0, sh_degree=3, s_mean=-3.0)
     cam = synth.camera((0.4, -0.3, -3.0), 200, 150)
     cfg = flod.default_config(bg=(0.2, 0.5, 0.9))
-    gi, gT, gnc, oi, oT, onc = _stage_render(g, cam, cfg)
+    gi, gT, gnc, oi, oT, onc, clear = _stage_render(g, cam, cfg)
     assert_image_close(gi, oi)
-    assert (gnc == onc).mean() >= 0.999
+    np.testing.assert_allclose(gT, oT, atol=2e-4)
+    _assert_nc(gnc, onc, clear)
     assert (oT < 1e-3).mean() > 0.05          # early termination is exercised
 
 
@@ -75,9 +102,20 @@ def test_render_end_to_end_single_forward_scene():
     rast = rasterizer([g], cams, [0.0])
     rgb, T, nc = rast.forward()
     torch.cuda.synchronize()
-    img, tf, _ = R.render(g, 0, 0.0, cams[0], R.Config())
+    ocfg = R.Config()
+    pre = oracle_pre(g, 0.0, cams[0], ocfg)
+    lists = R.tile_lists(pre, cams[0], ocfg)
+    img, tf, last = R.render_tiled(pre, cams[0], ocfg, lists=lists)
     assert_image_close(rgb.view(3, 128, 128).cpu().numpy(), img)
-    np.testing.assert_allclose(T.view(128, 128).cpu().numpy(), tf, atol=2e-3)
+    # T like an image channel; n_contrib names a position in each side's own tile list (the
+    # lists may differ by Gaussians at the edge of their tile sets): the Gaussian it names is
+    # compared, wherever the decisions are unambiguous
+    tiles = list(range(lists[3] * lists[4]))
+    ref = R.render_tiles(pre, cams[0], ocfg, lists, tiles)
+    n = assert_tiles_close(rgb.view(3, 128, 128).cpu().numpy(), T.view(128, 128).cpu().numpy(),
+                           nc.view(128, 128).cpu().numpy(), ref, pre, lists, cams[0], ocfg,
+                           "single forward", gpu_view_lists(rast, 0))
+    assert n == 128 * 128
     assert flod.flod_read_status(rast.ws) == 0
 
 
