@@ -18,9 +18,12 @@ Modules and the passages they follow:
                      (Sec. 3, text after Eq. 2), the tiled and the brute-force per-pixel
                      renders, and the gradient (autograd of the written-out forward).
 * ``select``      -- Eq. 6 (selective Gaussian set) and Eq. 7 (distance thresholds).
+* ``loss``        -- the training loss of every level, L1 + D-SSIM (Sec. 5.1.4, the Loss
+                     step of Algorithm 1), and its gradient.
+* ``adam``        -- the Adam step of Algorithm 1 over one Gaussian set.
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py`` against
 closed forms, library routines, brute force, finite differences or values the paper
 prints; none is "parity unpinned".
 """
-from . import gaussians, projection, raster, select, sh  # noqa: F401
+from . import adam, gaussians, loss, projection, raster, select, sh  # noqa: F401
