@@ -3,16 +3,22 @@
 
 Workload (the headline configuration): the finest level of the 5-level scene -- 3,000,000
 Gaussians (64 clusters, radius 20, SH degree 3, level-by-level initialised with Eq. 5 from
-levels 1..4), one 1920x1080 pinhole camera at distance 40, upstream image gradient
-N(0, 1e-3). A step is one training iteration of that level: preprocess, binning + radix
-sort, forward blending, blending backward, preprocess backward (gradients to means, s_opt,
-quaternions, opacity logits and SH). The forward-only frame rate is reported beside it.
+levels 1..4), one 1920x1080 pinhole camera at distance 40. A step is one training iteration
+of that level (the loop body of Algorithm 1): preprocess (Eq. 4, Eq. 1, projection, SH),
+binning + radix sort, forward blending, the L1 + D-SSIM loss against the target image and
+its gradient, the blending backward, and the preprocess backward fused with the Adam step
+of every parameter. The target is the level rendered with its DC colours perturbed
+(seed 12). The forward-only frame rate and the rasterizer-only forward+backward rate (a
+synthetic upstream gradient, no loss, no optimiser) are reported beside it.
 
-``value`` = fwd+bwd iterations per second over all ranks (inputs resident in HBM; the 708 MB
-parameter set and the per-step buffers exceed the 129 MB L2, so no flush is needed).
-``e2e`` = the same through the Python API with the step's input (the upstream image
-gradient) copied from pinned host memory and the rendered image read back, every step; the
-copies run on a second stream, double-buffered, overlapped with the neighbouring steps.
+``value`` = training iterations per second over all ranks (inputs resident in HBM; the
+708 MB parameter set and the 1.4 GB of Adam moments exceed the 129 MB L2, so no flush is
+needed). Each timed loop starts from the initial parameters and zero moments.
+``e2e`` = the same iterations through the Python API with the step's input (the target
+image) copied from pinned host memory and the step's result (the loss) read back, every
+step; the copies run on a second stream, double-buffered.
+``rooflines`` = every stage's achieved fraction of its bound, from CUDA-event times of a
+pass with events at every stage boundary and the algorithmic work of each stage.
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same step.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under torchrun each rank
@@ -34,9 +40,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "1080p frames/s fwd & fwd+bwd it/s (3M Gaussians), batched vs per-view"
-WORKLOAD = "FLoD 5-level scene, level 5 (3M Gaussians, SH3), 1920x1080, fwd+bwd per level"
-# peak of plain float32 ALU work: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz
-ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+WORKLOAD = ("FLoD 5-level scene, level 5 (3M Gaussians, SH3), 1920x1080, one training iteration "
+            "per step (render, L1 + D-SSIM loss, backward, Adam)")
 # FP32 operations (an FFMA counts 2) of the blending kernels: per evaluated (pixel, Gaussian)
 # pair -- the offset, q and its threshold test, with the per-column terms shared by the
 # thread's pixels -- and on top for each pair the forward blended (alpha, transmittance,
@@ -44,6 +49,24 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # reduction is overhead, not counted.
 FLOP_FWD_EVAL, FLOP_FWD_BLEND = 8, 13
 FLOP_BWD_EVAL, FLOP_BWD_BLEND = 7, 31
+# FP32 operations of the loss per pixel and channel: the separable 11-tap window (22 FMA) on
+# the five moment maps and on the three gradient maps, plus the SSIM value, its three
+# derivatives, the L1 term and the combination (about 40)
+FLOP_LOSS_PX = 2 * 22 * (5 + 3) + 40
+
+
+def hbm_peak():
+    """(GB/s, source): the driver's measured copy bandwidth, else the recipe's fallback."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, a copy kernel)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (an earlier GB300 copy measurement)"
+
+
+def alu_peak_tflops(sms: int, mhz: float) -> float:
+    """Plain float32 peak: SMs x 128 FP32 lanes x 2 (FMA) x SM clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
 def measured_traffic(kernel: str):
@@ -172,8 +195,9 @@ def cpu_model() -> str:
 
 class OracleStep:
     """Times the FP64 oracle on a bounded sample of one training step and scales it to the
-    full step: preprocess forward+backward and binning on a slice of the Gaussians (scaled by
-    N / slice) plus blending forward+backward on a stratified sample of tiles. The tiles are
+    full step: preprocess forward+backward, binning and Adam on a slice of the Gaussians
+    (scaled by N / slice), the loss and its gradient on a crop (scaled by the image area),
+    plus blending forward+backward on a stratified sample of tiles. The tiles are
     ordered by pair count and cut into `tiles` strata of equal size; the middle tile of each
     stratum is timed and stands for its stratum. The tile lists come from an untimed FP64
     preprocess of the whole level. The sample depends only on the workload, so every arm and
@@ -202,6 +226,10 @@ class OracleStep:
         self.n_tiles = ranges.shape[0]
         rng = np.random.default_rng(11)
         self.grad_out = rng.normal(0, 1e-3, (3, cam["height"], cam["width"]))
+        # the loss on a 256 x 256 crop (scaled by the image area) and Adam on the slice
+        self.crop = (rng.random((3, 256, 256)), rng.random((3, 256, 256)))
+        self.adam_grads = {k: rng.normal(size=np.shape(g[k][:self.slice_n]))
+                           for k in ("means", "quats", "s_opt", "opacity_logit", "sh")}
 
     def step_seconds(self, threads=None) -> float:
         R, np, torch = self.R, self.np, self.torch
@@ -242,12 +270,26 @@ class OracleStep:
                 go = torch.as_tensor(self.grad_out[:, y0:y1, x0:x1].reshape(3, -1).T)
                 (col * go).sum().backward()
             t_tiles += (time.perf_counter() - t0) * w
-        return t_slice * self.n / self.slice_n + t_tiles
+        from oracle import adam as AD
+        from oracle import loss as LS
+        t0 = time.perf_counter()
+        LS.loss_and_grad(*self.crop)
+        t_loss = (time.perf_counter() - t0) * self.cam["width"] * self.cam["height"] / (256 * 256)
+        par = {k: np.asarray(sub[k], dtype=np.float64) for k in self.adam_grads}
+        zero = {k: np.zeros_like(v) for k, v in par.items()}
+        lrs = {"means": 3.2e-3, "quats": 1e-3, "s_opt": 5e-3, "opacity_logit": 5e-2,
+               "sh_dc": 2.5e-3, "sh_rest": 1.25e-4}
+        t0 = time.perf_counter()
+        AD.adam_set(par, self.adam_grads, zero, zero, 1, lrs)
+        t_adam = (time.perf_counter() - t0) * self.n / self.slice_n
+        return t_slice * self.n / self.slice_n + t_tiles + t_loss + t_adam
 
     def describe(self) -> str:
         np = self.np
-        return (f"preprocess fwd+bwd and binning of {self.slice_n} of {self.n} Gaussians "
-                f"(x{self.n / self.slice_n:.0f}) + blend fwd+bwd of {len(self.sample)} of "
+        return (f"preprocess fwd+bwd, binning and Adam of {self.slice_n} of {self.n} Gaussians "
+                f"(x{self.n / self.slice_n:.0f}) + the loss and its gradient on a 256x256 crop "
+                f"(x{self.cam['width'] * self.cam['height'] / 65536:.1f}) + blend fwd+bwd of "
+                f"{len(self.sample)} of "
                 f"{self.n_tiles} 16x16 tiles, one per equal-size stratum of the tiles ordered by "
                 f"pair count (pairs {int(self.sample_pairs.min())}..{int(self.sample_pairs.max())}, "
                 f"median {int(np.median(self.sample_pairs))}), each standing for its stratum")
@@ -310,6 +352,70 @@ def adjust_chain_numpy(s_opt, counts):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 
+def stage_work(n, n_vis, pairs, tiles, depth_passes, tile_passes, deg, evals, pixels):
+    """Algorithmic work of each stage of one training iteration: (bound, amount, unit).
+    Bytes are the minimum DRAM traffic of the stage's definition, FLOPs its arithmetic
+    (FLOP_* above); n Gaussians (one unit each), n_vis of them with tiles, `pairs` (unit,
+    tile) pairs, `tiles` tiles, the sort passes that moved keys, SH degree deg."""
+    par = 12 + 16 + 12 + 4 + 12 * (deg + 1) ** 2          # 236 B of parameters at SH3
+    fwd_ev, bwd_ev, blended = evals
+    return {
+        # parameters in; xy, depth, conic, colour, radius, ellipse, tile record, count out
+        "preprocess": ("hbm", n * (par + 84), "B"),
+        # tile counts of all units; compaction (depth in, key + index out) and per pass
+        # 4 B counted + 16 B scattered per visible unit
+        "depth_sort": ("hbm", 4 * n + 12 * n_vis + 20 * n_vis * depth_passes, "B"),
+        # per visible unit its count, slot count, unit id and tile record; 8 B per pair out
+        "emission": ("hbm", 36 * n_vis + 8 * pairs, "B"),
+        # per pass: 4 B counted + 16 B scattered per pair
+        "tile_sort": ("hbm", 20 * pairs * tile_passes, "B"),
+        # one tile id per pair in, one range per tile out
+        "ranges": ("hbm", 4 * pairs + 8 * tiles, "B"),
+        "render_fwd": ("alu", fwd_ev * FLOP_FWD_EVAL + blended * FLOP_FWD_BLEND, "FLOP"),
+        "loss": ("alu", 3 * pixels * FLOP_LOSS_PX, "FLOP"),
+        "blend_bwd": ("alu", bwd_ev * FLOP_BWD_EVAL + blended * FLOP_BWD_BLEND, "FLOP"),
+        # parameters, both Adam moments in and out, and the tile count of every Gaussian;
+        # the 2D gradient record and colour of the visible ones
+        "bwd_adam": ("hbm", n * (6 * par + 4) + n_vis * (36 + 16), "B"),
+    }
+
+
+def rooflines(stage_ms, work, hbm_gbs, alu_tflops):
+    out = {}
+    for k, (bound, amount, unit) in work.items():
+        ms = stage_ms.get(k)
+        if not ms:
+            continue
+        if bound == "hbm":
+            ach = amount / (ms * 1e-3) / 1e9
+            out[k] = {"bound": "hbm", "ms": round(ms, 4), "work": int(amount), "achieved": ach,
+                      "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs}
+        else:
+            ach = amount / (ms * 1e-3) / 1e12
+            out[k] = {"bound": "alu", "ms": round(ms, 4), "work": int(amount), "achieved": ach,
+                      "peak": alu_tflops, "unit": "TFLOP/s", "frac": ach / alu_tflops}
+    return out
+
+
+def dc_perturbed_target(gs, view, seed=12, sigma=0.2):
+    """The target image: the level rendered with its DC colours perturbed (untimed data)."""
+    import numpy as np
+    import torch
+    from paper_2408_12894_gb300 import flod
+    rng = np.random.default_rng(seed)
+    sh = gs.sh.clone()
+    noise = rng.normal(0.0, sigma, (gs.n, 3)).astype(np.float32)
+    sh[:, 0, :] += torch.as_tensor(noise, device=sh.device)
+    tg = flod.GaussianSet(gs.means, gs.quats, gs.s_opt, gs.opacity_logit, sh, gs.sh_degree, gs.s_min)
+    r = flod.Rasterizer([tg], [view])
+    rgb, _, _ = r.forward()
+    torch.cuda.synchronize()
+    out = rgb.clone()
+    del r, sh, tg
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_flod(a):
     import numpy as np
     import torch
@@ -320,7 +426,7 @@ def run_flod(a):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_2408_12894_gb300 import _build, flod, synth
+    from paper_2408_12894_gb300 import _build, flod, synth, train
     _build.build()
     counts = level_counts(a.small, a.scale)
     g = make_level(a.small, a.scale)
@@ -329,61 +435,39 @@ def run_flod(a):
         flod.flod_adjust_scale(gs.s_opt[:counts[l]], synth.LEVEL_SMIN[l], synth.LEVEL_SMIN[l + 1])
     cam = synth.level_camera()
     view = flod.view_struct(cam)
+    H, W = cam["height"], cam["width"]
+    st = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(local)
+
+    def barrier():
+        replicas.barrier()
+
+    # ---------------- rasterizer alone: forward frames, and forward + backward with a
+    # synthetic upstream gradient (no loss, no optimiser)
     rast = flod.Rasterizer([gs], [view])
     rgb, T, nc = rast.forward()                    # sizes the pair capacity once
     torch.cuda.synchronize()
     pairs = int(rast.pair_count.item())
     rast.pair_capacity = int(pairs * 1.2) + 4096
     rast._alloc()
-    H, W = cam["height"], cam["width"]
-    dL_host = torch.as_tensor(synth.upstream_gradient(11, [cam])).pin_memory()
-    dL = dL_host.to("cuda")
-    grads = [[torch.zeros_like(getattr(gs, f)) for f in flod.GaussianSet.FIELDS]]
-    # one view renders the level: the backward writes every gradient (no zero-fill needed)
-    grads_c = flod.grads_struct(grads, overwrite=True)
-    st = torch.cuda.current_stream()
+    dL = torch.as_tensor(synth.upstream_gradient(11, [cam]), device="cuda")
+    grads = [[torch.empty_like(getattr(gs, f)) for f in flod.GaussianSet.FIELDS]]
+    grads_c = flod.grads_struct(grads, overwrite=True)   # one view: every gradient written
 
     def fwd():
         rast.preprocess()
         rast.bin_sort()
         rast.render_fwd(rgb, T, nc)
 
-    def step(ev=None, ev_blend=None):
-        # ev: events at every stage boundary; ev_blend: only around the two blending stages
-        if ev:
-            ev[0].record(st)
-        rast.preprocess()
-        if ev:
-            ev[1].record(st)
-        rast.bin_sort()
-        if ev:
-            ev[2].record(st)
-        if ev_blend:
-            ev_blend[0].record(st)
-        rast.render_fwd(rgb, T, nc)
-        if ev:
-            ev[3].record(st)
-            ev[4].record(st)
-        if ev_blend:
-            ev_blend[1].record(st)
+    def raster_step():
+        fwd()
         rast.blend_bwd(dL, T, nc)
-        if ev:
-            ev[5].record(st)
-        if ev_blend:
-            ev_blend[2].record(st)
         rast.preprocess_bwd(grads_c)
-        if ev:
-            ev[6].record(st)
 
     for _ in range(max(a.warmup, 3)):
-        step()
+        raster_step()
     torch.cuda.synchronize()
     assert flod.flod_read_status(rast.ws) == 0, "device status error"
-
-    def barrier():
-        replicas.barrier()
-
-    # ---- forward frames
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
@@ -392,48 +476,116 @@ def run_flod(a):
     e1.record(st)
     barrier()
     fwd_ms = e0.elapsed_time(e1) / a.steps
+    e0.record(st)
+    for _ in range(a.steps):
+        raster_step()
+    e1.record(st)
+    barrier()
+    raster_ms = e0.elapsed_time(e1) / a.steps
+    del rast, grads, grads_c, rgb, T, nc, dL
+    torch.cuda.empty_cache()
 
-    # ---- fwd+bwd training steps (the headline): K steps between two events; inside, events
-    # only around the two blending stages (the roofline kernels, timed live here)
+    # ---------------- the training iteration
+    target = dc_perturbed_target(gs, view)
+    init = {f: getattr(gs, f).clone() for f in flod.GaussianSet.FIELDS}
+    ts = train.TrainStep([gs], [view], target, lrs=train.default_lrs(extent=20.0))
+    assert ts.fused, "one view renders the level: the fused backward + Adam applies"
+    pairs = ts.size_capacity(headroom=1.5)
+    r = ts.rast
+    rgb, T, nc = ts.out
+
+    def reset():
+        """Initial parameters, zero moments, step counter 0 (untimed, between loops)."""
+        for f in flod.GaussianSet.FIELDS:
+            getattr(gs, f).copy_(init[f])
+        for t in ts.m[0] + ts.v[0]:
+            t.zero_()
+        ts.d_step.zero_()
+
+    def iteration(ev=None, ev_k=None):
+        # ev: events at every stage boundary; ev_k: around the dominant kernels only
+        def rec(i):
+            if ev:
+                ev[i].record(st)
+        rec(0)
+        r.preprocess()
+        rec(1)
+        for ph in (flod.BIN_PHASE_DEPTH, flod.BIN_PHASE_EMIT, flod.BIN_PHASE_TILES,
+                   flod.BIN_PHASE_RANGES):
+            r.bin_sort_phase(ph)
+            rec(1 + ph)
+        r.render_fwd(rgb, T, nc)
+        rec(6)
+        flod.flod_loss(rgb, ts.target, ts.sizes, ts.dL, ts.scratch, ts.loss, ts.lam)
+        rec(7)
+        if ev_k:
+            ev_k[0].record(st)
+        r.blend_bwd(ts.dL, T, nc)
+        rec(8)
+        if ev_k:
+            ev_k[1].record(st)
+        r.preprocess_bwd_adam(ts.states_c, ts.acfg)
+        rec(9)
+        if ev_k:
+            ev_k[2].record(st)
+
+    for _ in range(max(a.warmup, 3)):
+        iteration()
+    torch.cuda.synchronize()
+    assert flod.flod_read_status(r.ws) == 0, "device status error"
+
+    # ---- stage times (events at every boundary) and the blending evaluation counts
+    reset()
+    ev_before = r.eval_counts()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(a.steps)]
+    for i in range(a.steps):
+        iteration(evs[i])
+    torch.cuda.synchronize()
+    ev_after = r.eval_counts()
+    names = ["preprocess", "depth_sort", "emission", "tile_sort", "ranges", "render_fwd",
+             "loss", "blend_bwd", "bwd_adam"]
+    stage_ms = {n: sum(evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(a.steps)) / a.steps
+                for j, n in enumerate(names)}
+    step_ms = [evs[i][0].elapsed_time(evs[i][9]) for i in range(a.steps)]
+    plan = r.region("plan", torch.int32, 64).cpu().numpy()
+    n_vis = int(r.region("plan", torch.int64, 32)[8].item())
+    pairs_now = int(r.pair_count.item())
+    evals = tuple((ev_after[k] - ev_before[k]) / a.steps for k in range(3))
+
+    # ---- the headline: K iterations between two events; inside, events only around the
+    # blending backward and the fused backward + Adam (the dominant kernels, timed live)
+    reset()
     clk = clock_sampler(local)
-    ev_before = rast.eval_counts()
-    evb = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(a.steps)]
+    evk = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(a.steps)]
     h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     t_wall = time.perf_counter()
     h0.record(st)
     for i in range(a.steps):
-        step(ev_blend=evb[i])
+        iteration(ev_k=evk[i])
     h1.record(st)
     barrier()
     t_wall = time.perf_counter() - t_wall
     clocks = clock_summary(clk)
-    ev_after = rast.eval_counts()
     ms = h0.elapsed_time(h1) / a.steps
-    blend_ms = {"render_fwd": sum(e[0].elapsed_time(e[1]) for e in evb) / a.steps,
-                "blend_bwd": sum(e[1].elapsed_time(e[2]) for e in evb) / a.steps}
-    # ---- the same steps again with events at every stage boundary (stage times and the
-    # per-step spread; not the headline)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(a.steps)]
-    for i in range(a.steps):
-        step(evs[i])
-    torch.cuda.synchronize()
-    step_ms = [evs[i][0].elapsed_time(evs[i][6]) for i in range(a.steps)]
-    names = ["preprocess", "bin_sort", "render_fwd", "(none)", "blend_bwd", "preprocess_bwd"]
-    stage_ms = {n: sum(evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(a.steps)) / a.steps
-                for j, n in enumerate(names) if n != "(none)"}
-    ms, fwd_ms = replicas.max_over_ranks([ms, fwd_ms], device="cuda")
+    live_ms = {"blend_bwd": sum(e[0].elapsed_time(e[1]) for e in evk) / a.steps,
+               "bwd_adam": sum(e[1].elapsed_time(e[2]) for e in evk) / a.steps}
+    loss_end = float(ts.loss[0].item())
+    status = flod.flod_read_status(r.ws)
+    assert status == 0, f"device status {status} during the timed iterations"
+    ms, fwd_ms, raster_ms = replicas.max_over_ranks([ms, fwd_ms, raster_ms], device="cuda")
 
-    # ---- end to end: upstream gradient in from pinned host memory, image back, every step.
-    # The copies run on a second stream, double-buffered: step i+1's gradient is copied in
-    # while step i computes, and step i's image is copied out while its backward runs.
+    # ---- end to end through TrainStep: the target image in from pinned host memory and
+    # the loss back, every step, on a second stream, double-buffered
+    reset()
     cs = torch.cuda.Stream()
-    dLs, rgbs = [dL, torch.empty_like(dL)], [rgb, torch.empty_like(rgb)]
-    img_hosts = [torch.empty(3 * H * W, dtype=torch.float32).pin_memory() for _ in range(2)]
-    ev_in = [torch.cuda.Event() for _ in range(2)]     # gradient j is on the device
-    ev_used = [torch.cuda.Event() for _ in range(2)]   # the backward that read gradient j ended
-    ev_img = [torch.cuda.Event() for _ in range(2)]    # image j is rendered
-    ev_out = [torch.cuda.Event() for _ in range(2)]    # image j is on the host
+    tgt_host = target.cpu().pin_memory()
+    tgts = [target, torch.empty_like(target)]
+    losses = [ts.loss, torch.zeros_like(ts.loss)]
+    loss_hosts = [torch.zeros(1, dtype=torch.float32).pin_memory() for _ in range(2)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]     # target j is on the device
+    ev_used = [torch.cuda.Event() for _ in range(2)]   # the loss that read target j ended
+    ev_out = [torch.cuda.Event() for _ in range(2)]    # loss j is on the host
 
     def e2e_step(i):
         j = i % 2
@@ -442,20 +594,16 @@ def run_flod(a):
             if i >= 1:
                 cs.wait_event(ev_used[1 - j])
             with torch.cuda.stream(cs):
-                dLs[1 - j].copy_(dL_host, non_blocking=True)
+                tgts[1 - j].copy_(tgt_host, non_blocking=True)
                 ev_in[1 - j].record(cs)
         if i >= 2:
             st.wait_event(ev_out[j])
-        rast.preprocess()
-        rast.bin_sort()
-        rast.render_fwd(rgbs[j], T, nc)
-        ev_img[j].record(st)
-        rast.blend_bwd(dLs[j], T, nc)
+        ts.target, ts.loss = tgts[j], losses[j]
+        ts.run()
         ev_used[j].record(st)
-        rast.preprocess_bwd(grads_c)
-        cs.wait_event(ev_img[j])
+        cs.wait_event(ev_used[j])
         with torch.cuda.stream(cs):
-            img_hosts[j].copy_(rgbs[j], non_blocking=True)
+            loss_hosts[j].copy_(losses[j], non_blocking=True)
             ev_out[j].record(cs)
 
     barrier()
@@ -463,7 +611,7 @@ def run_flod(a):
     e2e0.record(st)
     cs.wait_event(e2e0)
     with torch.cuda.stream(cs):
-        dLs[0].copy_(dL_host, non_blocking=True)
+        tgts[0].copy_(tgt_host, non_blocking=True)
         ev_in[0].record(cs)
     for i in range(a.steps):
         e2e_step(i)
@@ -472,49 +620,60 @@ def run_flod(a):
     barrier()
     e2e_ms = e2e0.elapsed_time(e2e1) / a.steps
     e2e_ms, = replicas.max_over_ranks([e2e_ms], device="cuda")
+    ts.target, ts.loss = target, losses[0]
 
-    fwd_evals = (ev_after[0] - ev_before[0]) / a.steps
-    bwd_evals = (ev_after[1] - ev_before[1]) / a.steps
-    blended = (ev_after[2] - ev_before[2]) / a.steps
-    kernels = {"render_fwd": (blend_ms["render_fwd"],
-                              fwd_evals * FLOP_FWD_EVAL + blended * FLOP_FWD_BLEND),
-               "blend_bwd": (blend_ms["blend_bwd"],
-                             bwd_evals * FLOP_BWD_EVAL + blended * FLOP_BWD_BLEND)}
-    dom = max(kernels, key=lambda k: kernels[k][0])
-    d_ms, d_flop = kernels[dom]
-    achieved = d_flop / (d_ms * 1e-3) / 1e12
-    n_tiles = int(rast.layout.tiles)
-    n_passes = (max(1, math.ceil(math.log2(max(n_tiles, 2)))) + 8) // 9   # 9-bit tile digits
-    # preprocess 2 (status clear, preprocess); bin_sort: visible counts, their scan, unit
-    # keys, 4 depth passes of 3 kernels (count, scan, scatter; a pass above the keys'
-    # significant bits exits at once), block sums, scan, light, big-unit and sliced emission,
-    # n_passes tile passes of 3, ranges; render_fwd 1; blend_bwd 2 (2D-gradient zero-fill,
-    # blend); preprocess_bwd 1
-    launches_per_step = 2 + (3 + 12 + 2 + 3 + 3 * n_passes + 1) + 1 + 2 + 1
+    # ---- rooflines
+    hbm, hbm_src = hbm_peak()
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    alu = alu_peak_tflops(props.multi_processor_count, mhz)
+    depth_passes = int(sum(plan[0:4]))
+    tile_passes = int(sum(plan[4:8]))
+    work = stage_work(gs.n, n_vis, pairs_now, int(r.layout.tiles), depth_passes, tile_passes,
+                      gs.sh_degree, evals, W * H)
+    roof = rooflines(stage_ms, work, hbm, alu)
+    live = rooflines(live_ms, {k: work[k] for k in live_ms}, hbm, alu)
+    dom = max(live, key=lambda k: live[k]["ms"])
+    d = live[dom]
+    traffic = measured_traffic({"blend_bwd": "k_render_bwd", "bwd_adam": "k_preprocess_bwd_adam"}[dom])
+    roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+                "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
+                "peak_source": hbm_src if d["bound"] == "hbm" else
+                f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (derived)"}
+    # launches per iteration: status clear + preprocess; depth sort (visible counts, scan,
+    # unit keys, 4 x (count, scan, scatter)); block sums, scan, light, big-unit and sliced
+    # emission; tile passes x (count, scan, scatter); ranges; render; 2 loss kernels;
+    # 2D-gradient zero-fill + blend backward; fused backward + Adam and the step tick
+    launches_per_step = 2 + (3 + 12) + 5 + 3 * max(1, (int(math.ceil(math.log2(max(int(r.layout.tiles), 2)))) + 8) // 9) + 1 + 1 + 2 + 2 + 2
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": world * 1e3 / ms, "unit": "it/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "data": "synthetic (seeded cluster scene; target = the level rendered with perturbed "
+                    "DC colours)",
             "config": {"workload": WORKLOAD, "gaussians": int(gs.n), "resolution": f"{W}x{H}",
                        "sh_degree": 3, "tile": "16x16", "pairs_per_step": pairs,
-                       "l2": "inputs larger than L2 (708 MB parameters, no flush)",
+                       "pairs_after_training_steps": pairs_now, "loss": "L1 + 0.2 D-SSIM",
+                       "optimizer": "Adam (3DGS learning rates, scene extent 20)",
+                       "l2": "inputs larger than L2 (708 MB parameters + 1.4 GB Adam moments, no flush)",
                        "parallelism": f"replicas x{world}"},
             "fwd_fps": world * 1e3 / fwd_ms, "fwd_ms": fwd_ms,
+            "raster_fwd_bwd_it_s": world * 1e3 / raster_ms, "raster_fwd_bwd_ms": raster_ms,
             "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "step_ms_median": statistics.median(step_ms),
             "wall_ms_per_step": 1e3 * t_wall / a.steps,
-            "evals_per_step": {"fwd": fwd_evals, "bwd": bwd_evals, "blended": blended},
-            "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved,
-                         "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / ALU_PEAK_TFLOPS,
-                         "traffic": measured_traffic("k_render_bwd") if dom == "blend_bwd" else None,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+            "loss_after_steps": loss_end,
+            "evals_per_step": {"fwd": evals[0], "bwd": evals[1], "blended": evals[2]},
+            "sort_passes": {"depth": depth_passes, "tile": tile_passes},
+            "visible_units": n_vis,
+            "roofline": roofline,
+            "rooflines": roof,
+            "device": {"name": props.name, "sms": props.multi_processor_count,
+                       "alu_peak_tflops": alu, "alu_peak_clock_mhz": mhz, "hbm_peak_gbs": hbm},
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": "it/s",
-                    "h2d_bytes_per_step": int(dL.numel() * 4),
-                    "d2h_bytes_per_step": int(rgb.numel() * 4)},
+                    "h2d_bytes_per_step": int(target.numel() * 4),
+                    "d2h_bytes_per_step": 4},
             "gpu_launches": launches_per_step * a.steps,
             "clocks": clocks,
         }
@@ -525,12 +684,9 @@ def run_flod(a):
         if not a.no_cpu_baseline and world == 1:
             try:
                 g_np = dict(g)
-                g_np["s_opt"] = gs.s_opt.cpu().numpy()
+                g_np["s_opt"] = init["s_opt"].cpu().numpy()
                 ost = OracleStep(g_np, cam, synth.LEVEL_SMIN[-1])
-                sec = ost.step_seconds()
-                line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "it/s",
-                                        "cores": torch.get_num_threads(), "kind": "oracle",
-                                        "sample": ost.describe()}
+                line["cpu_baseline"] = cpu_baseline_line(ost)
             except Exception as ex:   # report, never hide
                 line["cpu_baseline"] = {"value": None, "unit": "it/s", "kind": "oracle",
                                         "error": repr(ex)}

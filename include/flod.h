@@ -270,6 +270,76 @@ flod_status flod_preprocess_bwd(const flod_gaussians *sets, int n_sets, const fl
                                 size_t ws_bytes, uint64_t pair_capacity, const flod_grads *grads,
                                 flod_stream stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Training step of a level (Algorithm 1: Loss, then Adam on the gradient)
+ * --------------------------------------------------------------------------------------- */
+
+/* The five parameter arrays of one set (device, float32, shapes of flod_gaussians). */
+typedef struct {
+  float *means, *quats, *s_opt, *opacity_logit, *sh;
+} flod_param_arrays;
+
+/* Scratch bytes of flod_loss for n_images images of the given sizes (host arrays). */
+size_t flod_loss_scratch_size(const int *widths, const int *heights, int n_images);
+
+/* The training loss of the level (Sec. 5.1.4: the backbone's "L1 and SSIM losses"; the Loss
+ * step of Algorithm 1) and its gradient, per image:
+ *   L = (1 - lambda) mean|I - I_hat| + lambda (1 - mean SSIM(I, I_hat)),
+ * means over the image's 3 channels and pixels; SSIM of Wang et al. with an 11 x 11 Gaussian
+ * window (sigma 1.5, normalised, zero outside the image), C1 = 0.01^2, C2 = 0.03^2.
+ * img, target: device, the planar layout of flod_render_fwd's out_rgb ([3][H][W] per image,
+ * images concatenated; widths / heights are host arrays of n_images <= FLOD_MAX_VIEWS
+ * entries). Writes dL/dimg (same layout; the gradient of each image's own loss, ready for
+ * flod_render_bwd) and, when d_loss is not NULL, each image's loss to d_loss[i] (device).
+ * scratch: device, flod_loss_scratch_size() bytes, 256-byte aligned, no initial contents. */
+flod_status flod_loss(const float *img, const float *target, const int *widths,
+                      const int *heights, int n_images, float lambda, float *d_loss,
+                      float *dL_dimg, void *scratch, size_t scratch_bytes, flod_stream stream);
+
+/* Adam hyper-parameters (Adam step of Algorithm 1). One learning rate per parameter group:
+ * means, rotations, s_opt, opacity logits, SH coefficient 0 (DC) and SH coefficients 1..K-1.
+ * beta1, beta2 and eps are doubles: 1 - beta and the bias corrections are formed from them in
+ * double before rounding (0.999 has no float32 representation close enough for 1 - beta2).
+ * d_step (device uint32) counts the steps taken: a call uses t = *d_step + 1 for the bias
+ * corrections and then increments it in the stream, so a captured CUDA graph replays
+ * successive steps; start it at 0. */
+typedef struct {
+  float lr_means, lr_quats, lr_s_opt, lr_opacity, lr_sh_dc, lr_sh_rest;
+  double beta1, beta2, eps;
+  uint32_t *d_step;
+} flod_adam_config;
+
+/* One Adam step of n_sets sets (one launch, one advance of the step counter), per entry:
+ *   m <- beta1 m + (1 - beta1) g,   v <- beta2 v + (1 - beta2) g^2,
+ *   p <- p - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+ * params (updated in place), grads, m, v: host arrays of n_sets entries of device arrays;
+ * set k has n[k] Gaussians at SH degree sh_degree[k] (host arrays); all five members
+ * non-NULL when n[k] > 0; m and v start at zero. Returns FLOD_ERR_INVALID_ARG on NULL
+ * arrays, n[k] < 0 or n_sets outside 1..FLOD_MAX_SETS. */
+flod_status flod_adam_step(const flod_param_arrays *params, const flod_param_arrays *grads,
+                           const flod_param_arrays *m, const flod_param_arrays *v, const int *n,
+                           const int *sh_degree, int n_sets, const flod_adam_config *cfg,
+                           flod_stream stream);
+
+/* Adam state of one set for flod_preprocess_bwd_adam: where the updated parameters go
+ * (`params`; may be the set's own arrays) and the moments m, v (same shapes). Every array of
+ * the three, and every parameter array of the set, must be 16-byte aligned. */
+typedef struct {
+  flod_param_arrays params, m, v;
+} flod_adam_state;
+
+/* flod_preprocess_bwd and flod_adam_step in one pass: the chain rule of each unit from the
+ * blending backward's 2D gradients to the parameters, each parameter gradient consumed at once
+ * by the Adam step of that entry (the gradient is never stored). Every set must be rendered
+ * by exactly one view, as a whole set (no selection list), so each Gaussian has one unit;
+ * Gaussians that touch no tile take the step with g = 0, as the standalone step would. states
+ * has n_sets entries. The step counter advances once per call. Else as flod_preprocess_bwd. */
+flod_status flod_preprocess_bwd_adam(const flod_gaussians *sets, int n_sets,
+                                     const flod_view *views, int n_views,
+                                     const flod_raster_config *cfg, void *ws, size_t ws_bytes,
+                                     uint64_t pair_capacity, const flod_adam_state *states,
+                                     const flod_adam_config *acfg, flod_stream stream);
+
 /* Eq. 6 with the thresholds of Eq. 7. levels[0..n_levels-1] are given coarse to fine.
  * d_thresh (host array of n_levels-1 floats, descending) gives d_proj of each level but the
  * last; if NULL, d_proj = s_min * focal / gamma (Eq. 7). The last level's band ends at 0 and

@@ -472,6 +472,143 @@ flod_status flod_render_bwd(const flod_gaussians* sets, int n_sets, const flod_v
                              stream);
 }
 
+namespace {
+bool all_set(const flod_param_arrays* a) {
+  return a && a->means && a->quats && a->s_opt && a->opacity_logit && a->sh;
+}
+bool aligned16(const void* p) { return !(reinterpret_cast<uintptr_t>(p) & 15u); }
+bool adam_cfg_ok(const flod_adam_config* c) {
+  return c && c->d_step && c->beta1 >= 0.0 && c->beta1 < 1.0 && c->beta2 >= 0.0 && c->beta2 < 1.0 &&
+         c->eps >= 0.0 && isfinite(c->lr_means) && isfinite(c->lr_quats) && isfinite(c->lr_s_opt) &&
+         isfinite(c->lr_opacity) && isfinite(c->lr_sh_dc) && isfinite(c->lr_sh_rest);
+}
+AdamHyper adam_hyper(const flod_adam_config* c) {
+  AdamHyper h;
+  h.lr[0] = c->lr_means;
+  h.lr[1] = c->lr_quats;
+  h.lr[2] = c->lr_s_opt;
+  h.lr[3] = c->lr_opacity;
+  h.lr[4] = c->lr_sh_dc;
+  h.lr[5] = c->lr_sh_rest;
+  h.beta1 = c->beta1;
+  h.beta2 = c->beta2;
+  h.b1 = (float)c->beta1;
+  h.b2 = (float)c->beta2;
+  h.omb1 = (float)(1.0 - c->beta1);
+  h.omb2 = (float)(1.0 - c->beta2);
+  h.eps = (float)c->eps;
+  h.d_step = c->d_step;
+  return h;
+}
+AdamArrays adam_arrays(const flod_param_arrays& in, const flod_param_arrays& out,
+                       const flod_param_arrays& m, const flod_param_arrays& v) {
+  AdamArrays a;
+  const float* pi[5] = {in.means, in.quats, in.s_opt, in.opacity_logit, in.sh};
+  float* po[5] = {out.means, out.quats, out.s_opt, out.opacity_logit, out.sh};
+  float* pm[5] = {m.means, m.quats, m.s_opt, m.opacity_logit, m.sh};
+  float* pv[5] = {v.means, v.quats, v.s_opt, v.opacity_logit, v.sh};
+  for (int f = 0; f < 5; ++f) {
+    a.in[f] = pi[f];
+    a.out[f] = po[f];
+    a.m[f] = pm[f];
+    a.v[f] = pv[f];
+  }
+  return a;
+}
+}  // namespace
+
+size_t flod_loss_scratch_size(const int* widths, const int* heights, int n_images) {
+  if (!widths || !heights || n_images < 1 || n_images > FLOD_MAX_VIEWS) return 0;
+  for (int i = 0; i < n_images; ++i)
+    if (widths[i] <= 0 || heights[i] <= 0 || widths[i] > 16384 || heights[i] > 16384) return 0;
+  return loss_scratch_bytes(widths, heights, n_images, nullptr, nullptr);
+}
+
+flod_status flod_loss(const float* img, const float* target, const int* widths, const int* heights,
+                      int n_images, float lambda, float* d_loss, float* dL_dimg, void* scratch,
+                      size_t scratch_bytes, flod_stream stream) {
+  const size_t need = flod_loss_scratch_size(widths, heights, n_images);
+  if (!need || !img || !target || !dL_dimg || !scratch || !(lambda >= 0.f && lambda <= 1.f))
+    return FLOD_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(scratch) & 255u) return FLOD_ERR_INVALID_ARG;
+  if (scratch_bytes < need) return FLOD_ERR_WORKSPACE;
+  DevInfo* dev = nullptr;
+  flod_status s = device_info(&dev);
+  if (s != FLOD_OK) return s;
+  return launch_loss(img, target, widths, heights, n_images, lambda, d_loss, dL_dimg, scratch,
+                     reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FLOD_OK
+             : FLOD_ERR_CUDA;
+}
+
+flod_status flod_adam_step(const flod_param_arrays* params, const flod_param_arrays* grads,
+                           const flod_param_arrays* m, const flod_param_arrays* v, const int* n,
+                           const int* sh_degree, int n_sets, const flod_adam_config* cfg,
+                           flod_stream stream) {
+  if (!params || !grads || !m || !v || !n || !sh_degree || n_sets < 1 || n_sets > FLOD_MAX_SETS ||
+      !adam_cfg_ok(cfg))
+    return FLOD_ERR_INVALID_ARG;
+  AdamArrays a[FLOD_MAX_SETS];
+  for (int k = 0; k < n_sets; ++k) {
+    if (n[k] < 0 || n[k] >= (1 << FLOD_SEL_SHIFT) || sh_degree[k] < 0 || sh_degree[k] > 3)
+      return FLOD_ERR_INVALID_ARG;
+    if (n[k] > 0 && (!all_set(&params[k]) || !all_set(&grads[k]) || !all_set(&m[k]) ||
+                     !all_set(&v[k])))
+      return FLOD_ERR_INVALID_ARG;
+    a[k] = adam_arrays(params[k], params[k], m[k], v[k]);
+  }
+  DevInfo* dev = nullptr;
+  flod_status s = device_info(&dev);
+  if (s != FLOD_OK) return s;
+  return launch_adam(a, grads, n, sh_degree, n_sets, adam_hyper(cfg), dev->res_small,
+                     reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FLOD_OK
+             : FLOD_ERR_CUDA;
+}
+
+flod_status flod_preprocess_bwd_adam(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                                     int n_views, const flod_raster_config* cfg, void* ws,
+                                     size_t ws_bytes, uint64_t pair_capacity,
+                                     const flod_adam_state* states, const flod_adam_config* acfg,
+                                     flod_stream stream) {
+  static thread_local Plan P;
+  DevInfo* dev = nullptr;
+  if (!states || !adam_cfg_ok(acfg)) return FLOD_ERR_INVALID_ARG;
+  flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
+  if (s != FLOD_OK) return s;
+  int direct[FLOD_MAX_SETS] = {0};
+  for (int v = 0; v < n_views; ++v) {
+    if (views[v].sel) return FLOD_ERR_INVALID_ARG;
+    ++direct[views[v].set];
+  }
+  static thread_local AdamTable at;
+  memset(&at, 0, sizeof(at));
+  for (int k = 0; k < n_sets; ++k) {
+    const flod_adam_state& S = states[k];
+    if (direct[k] != 1 || !all_set(&S.params) || !all_set(&S.m) || !all_set(&S.v))
+      return FLOD_ERR_INVALID_ARG;
+    // the Adam pass moves each CTA's chunk of every array with 16-byte accesses
+    const flod_param_arrays* arrs[3] = {&S.params, &S.m, &S.v};
+    for (const flod_param_arrays* a : arrs)
+      if (!aligned16(a->means) || !aligned16(a->quats) || !aligned16(a->s_opt) ||
+          !aligned16(a->opacity_logit) || !aligned16(a->sh))
+        return FLOD_ERR_INVALID_ARG;
+    if (!aligned16(sets[k].means) || !aligned16(sets[k].s_opt) ||
+        !aligned16(sets[k].opacity_logit) || !aligned16(sets[k].sh))
+      return FLOD_ERR_INVALID_ARG;
+    const flod_param_arrays in = {const_cast<float*>(sets[k].means), const_cast<float*>(sets[k].quats),
+                                  const_cast<float*>(sets[k].s_opt),
+                                  const_cast<float*>(sets[k].opacity_logit),
+                                  const_cast<float*>(sets[k].sh)};
+    at.a[k] = adam_arrays(in, S.params, S.m, S.v);
+  }
+  at.h = adam_hyper(acfg);
+  const Ws w = ws_ptrs(ws, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return with_batch(sets, n_sets, views, n_views, cfg, P,
+                    [&](const auto& B) { return launch_preprocess_bwd_adam(B, w, at, st); });
+}
+
 size_t flod_select_scratch_size(const flod_gaussians* levels, int n_levels) {
   if (!levels || n_levels < 1 || n_levels > FLOD_MAX_SETS) return 0;
   int ns[FLOD_MAX_SETS];

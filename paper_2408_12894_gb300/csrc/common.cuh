@@ -298,6 +298,13 @@ __device__ __forceinline__ float splat_alpha(float qs, float o, float& g) {
   return fminf(kAlphaMax, __fmul_rn(o, g));
 }
 
+// Pairs of float32 values in one instruction (sm_100 and later): where two results share an
+// operand, one packed instruction does the work of two scalar ones.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // ---------------------------------------------------------------------------------------
 // Programmatic dependent launch. Every kernel is launched so that it may be scheduled while
 // the previous kernel of its stream drains (launch_k). Its first statement waits for that

@@ -32,12 +32,97 @@ struct GradTable {
   int zero[FLOD_MAX_SETS];   // 1: the set's buffers are zero-filled first (flod_grads.overwrite 2)
 };
 
+// ---------------------------------------------------------------------------------------
+// Adam (the Adam step of Algorithm 1) on the parameter arrays of a set
+// ---------------------------------------------------------------------------------------
+struct AdamArrays {
+  const float* in[5];   // current parameters: means, quats, s_opt, opacity logits, sh
+  float* out[5];        // where the updated parameters go (may alias in)
+  float* m[5];          // first moments
+  float* v[5];          // second moments
+};
+
+struct AdamHyper {
+  float lr[6];          // means, quats, s_opt, opacity logits, SH coefficient 0, SH 1..K-1
+  double beta1, beta2;  // exact, for the bias corrections
+  float b1, b2, omb1, omb2, eps;   // beta and 1 - beta rounded from double, eps
+  const uint32_t* d_step;   // steps taken so far: this step is t = *d_step + 1
+};
+
+struct AdamTable {
+  AdamArrays a[FLOD_MAX_SETS];
+  AdamHyper h;
+};
+
+// Bias corrections of step t: 1 / (1 - beta1^t) and 1 / sqrt(1 - beta2^t), in double.
+struct AdamCoef {
+  float b1, b2, omb1, omb2, eps, bc1, bc2s;
+};
+
+__device__ __forceinline__ AdamCoef adam_coef(const AdamHyper& h) {
+  const double t = (double)(*h.d_step) + 1.0;
+  AdamCoef c;
+  c.b1 = h.b1;
+  c.b2 = h.b2;
+  c.omb1 = h.omb1;
+  c.omb2 = h.omb2;
+  c.eps = h.eps;
+  c.bc1 = (float)(1.0 / (1.0 - pow(h.beta1, t)));
+  c.bc2s = (float)(1.0 / sqrt(1.0 - pow(h.beta2, t)));
+  return c;
+}
+
+// One Adam step of one entry: m, v updated in place, the new parameter returned.
+__device__ __forceinline__ float adam1(float p, float g, float& m, float& v, float lr,
+                                       const AdamCoef& c) {
+  m = fmaf(c.b1, m, c.omb1 * g);
+  v = fmaf(c.b2, v, c.omb2 * (g * g));
+  return p - lr * (m * c.bc1) / fmaf(sqrtf(v), c.bc2s, c.eps);
+}
+
+// Learning rate of entry e (0 .. 3K-1) of a Gaussian's SH coefficients: coefficient 0 (the
+// DC term) has its own rate.
+__device__ __forceinline__ float sh_lr(const AdamHyper& h, int e) { return e < 3 ? h.lr[4] : h.lr[5]; }
+
+// Learning rates of the four entries i .. i+3 of parameter array f (one modulo per chunk).
+__device__ __forceinline__ void chunk_lr(const AdamHyper& h, int f, uint64_t i, int K3,
+                                         float (&lr)[4]) {
+  if (f != 4) {
+    lr[0] = lr[1] = lr[2] = lr[3] = h.lr[f];
+    return;
+  }
+  const int e0 = (int)(i % (uint64_t)K3);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    int e = e0 + t;
+    e = e >= K3 ? e - K3 : e;
+    lr[t] = sh_lr(h, e);
+  }
+}
+
+// adam.cu
+cudaError_t launch_adam(const AdamArrays* a, const flod_param_arrays* grads, const int* n,
+                        const int* sh_degree, int n_sets, const AdamHyper& h, int grid,
+                        cudaStream_t st);
+cudaError_t launch_adam_tick(uint32_t* d_step, cudaStream_t st);
+
+// loss.cu
+size_t loss_scratch_bytes(const int* widths, const int* heights, int n, uint32_t* ctas,
+                          uint64_t* pixels);
+cudaError_t launch_loss(const float* img, const float* tgt, const int* widths, const int* heights,
+                        int n, float lambda, float* loss, float* dL, void* scratch,
+                        cudaStream_t st);
+
 // preprocess.cu
 template <int MAXV>
 cudaError_t launch_preprocess(const Batch<MAXV>& b, const Ws& ws, cudaStream_t st);
 template <int MAXV>
 cudaError_t launch_preprocess_bwd(const Batch<MAXV>& b, const Ws& ws, const GradTable& gt,
                                   cudaStream_t st);
+// the preprocess backward with an Adam step on each entry in place of writing its gradient
+template <int MAXV>
+cudaError_t launch_preprocess_bwd_adam(const Batch<MAXV>& b, const Ws& ws, const AdamTable& at,
+                                       cudaStream_t st);
 // zero-fills the gradient buffers of the sets with gt.zero set (one launch, in stream order)
 template <int MAXV>
 cudaError_t launch_zero_grads(const Batch<MAXV>& b, const GradTable& gt, int grid, cudaStream_t st);

@@ -65,13 +65,6 @@ __device__ __forceinline__ bool next_tile(const Ws& ws, uint32_t n_tiles, int co
 // ---------------------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------------------
-// Pairs of float32 values in one instruction (sm_100 and later): the two pixels of a pair
-// share every per-Gaussian operand, so one packed instruction does the work of two scalar ones.
-__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
 // Both walks stage at most 128 Gaussians per batch (a configured batch of 256 is taken as
 // 128): the smaller shared arrays leave more of each SM's L1 to the batch loads' gathers
 // (backward 0.58 -> 0.52 ms, forward 0.256 -> 0.249 ms at 3M / 1080p, against 256).

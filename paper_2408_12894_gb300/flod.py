@@ -65,6 +65,22 @@ class Grads(C.Structure):
                 ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("overwrite", C.c_int)]
 
 
+class ParamArrays(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("quats", C.c_void_p), ("s_opt", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class AdamConfig(C.Structure):
+    _fields_ = [("lr_means", C.c_float), ("lr_quats", C.c_float), ("lr_s_opt", C.c_float),
+                ("lr_opacity", C.c_float), ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("d_step", C.c_void_p)]
+
+
+class AdamState(C.Structure):
+    _fields_ = [("params", ParamArrays), ("m", ParamArrays), ("v", ParamArrays)]
+
+
 class WsLayout(C.Structure):
     _fields_ = [(n, C.c_size_t) for n in ("total", "status", "pair_count", "plan", "xy", "depth",
                                           "conic_o", "rgb", "radius", "ext", "trec", "tiles_touched",
@@ -106,6 +122,11 @@ def lib() -> C.CDLL:
         L.flod_select_levels_noalloc.argtypes = [P, I, P, C.c_float, C.c_float, P, P,
                                                  C.c_uint32, P, P]
         L.flod_adjust_scale.argtypes = [P, C.c_int64, C.c_float, C.c_float, P]
+        L.flod_loss_scratch_size.argtypes = [P, P, I]
+        L.flod_loss_scratch_size.restype = SZ
+        L.flod_loss.argtypes = [P, P, P, P, I, C.c_float, P, P, P, SZ, P]
+        L.flod_adam_step.argtypes = [P, P, P, P, P, P, I, P, P]
+        L.flod_preprocess_bwd_adam.argtypes = [P, I, P, I, P, P, SZ, U64, P, P, P]
         L.flod_read_status.argtypes = [P, P, P]
         L.flod_status_string.argtypes = [I]
         L.flod_status_string.restype = C.c_char_p
@@ -113,7 +134,8 @@ def lib() -> C.CDLL:
                      "flod_bin_sort_phase",
                      "flod_render_fwd", "flod_render_bwd", "flod_blend_bwd",
                      "flod_preprocess_bwd", "flod_select_levels", "flod_select_levels_noalloc",
-                     "flod_adjust_scale", "flod_read_status"):
+                     "flod_adjust_scale", "flod_read_status", "flod_loss", "flod_adam_step",
+                     "flod_preprocess_bwd_adam"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -326,6 +348,72 @@ def flod_select_levels_noalloc(levels, origin, out_sel: torch.Tensor, d_count: t
            "flod_select_levels_noalloc")
 
 
+# ---------------------------------------------------------------------------------------
+# training step: loss and Adam
+# ---------------------------------------------------------------------------------------
+
+#: the loss weight and the Adam settings of the 3DGS backbone the paper keeps (Sec. 5.1.4)
+LOSS_LAMBDA = 0.2
+ADAM_BETAS = (0.9, 0.999)
+ADAM_EPS = 1e-15
+
+
+def param_arrays(tensors) -> ParamArrays:
+    """ParamArrays of five tensors in GaussianSet.FIELDS order."""
+    return ParamArrays(*[_ptr(t) for t in tensors])
+
+
+def flod_loss_scratch_size(sizes) -> int:
+    """sizes: [(width, height), ...] of the images."""
+    w = _array(C.c_int, [int(a) for a, _ in sizes])
+    h = _array(C.c_int, [int(b) for _, b in sizes])
+    n = lib().flod_loss_scratch_size(w, h, len(sizes))
+    if n == 0:
+        raise FlodError("flod_loss_scratch_size: invalid sizes")
+    return n
+
+
+def flod_loss(img: torch.Tensor, target: torch.Tensor, sizes, dL: torch.Tensor,
+              scratch: torch.Tensor, d_loss: torch.Tensor | None = None,
+              lam: float = LOSS_LAMBDA, stream=None):
+    w = _array(C.c_int, [int(a) for a, _ in sizes])
+    h = _array(C.c_int, [int(b) for _, b in sizes])
+    _check(lib().flod_loss(img.data_ptr(), target.data_ptr(), w, h, len(sizes), lam,
+                           _ptr(d_loss), dL.data_ptr(), scratch.data_ptr(), scratch.numel(),
+                           _stream(stream)), "flod_loss")
+
+
+def adam_config(lrs: dict, d_step: torch.Tensor, betas=ADAM_BETAS, eps=ADAM_EPS) -> AdamConfig:
+    """lrs: means, quats, s_opt, opacity_logit, sh_dc, sh_rest; d_step: a device int32 [1]
+    counter of the steps taken (start at 0)."""
+    return AdamConfig(lrs["means"], lrs["quats"], lrs["s_opt"], lrs["opacity_logit"],
+                      lrs["sh_dc"], lrs["sh_rest"], betas[0], betas[1], eps, d_step.data_ptr())
+
+
+def flod_adam_step(params, grads, m, v, ns, sh_degrees, cfg: AdamConfig, stream=None):
+    """One Adam step of several sets: params, grads, m, v are per-set lists of five tensors
+    (GaussianSet.FIELDS order); ns, sh_degrees per set."""
+    k = len(params)
+    P_, G_, M_, V_ = (_array(ParamArrays, [param_arrays(t) for t in x]) for x in (params, grads, m, v))
+    _check(lib().flod_adam_step(P_, G_, M_, V_, _array(C.c_int, [int(n) for n in ns]),
+                                _array(C.c_int, [int(d) for d in sh_degrees]), k, C.byref(cfg),
+                                _stream(stream)), "flod_adam_step")
+
+
+def adam_states(states) -> C.Array:
+    """states: per set, (params out, m, v), each five tensors."""
+    return _array(AdamState, [AdamState(param_arrays(p), param_arrays(m), param_arrays(v))
+                              for p, m, v in states])
+
+
+def flod_preprocess_bwd_adam(sets, views, cfg, ws, pair_capacity, states_c, acfg: AdamConfig,
+                             stream=None):
+    _check(lib().flod_preprocess_bwd_adam(sets, len(sets), views, len(views), C.byref(cfg),
+                                          ws.data_ptr(), ws.numel(), pair_capacity, states_c,
+                                          C.byref(acfg), _stream(stream)),
+           "flod_preprocess_bwd_adam")
+
+
 def flod_adjust_scale(s_opt: torch.Tensor, s_min_cur: float, s_min_next: float, stream=None):
     _check(lib().flod_adjust_scale(s_opt.data_ptr(), s_opt.numel(), s_min_cur, s_min_next,
                                    _stream(stream)), "flod_adjust_scale")
@@ -415,6 +503,11 @@ class Rasterizer:
         """grads_c: the result of grads_struct (built once, reused every step)."""
         flod_preprocess_bwd(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity,
                             grads_c, stream)
+
+    def preprocess_bwd_adam(self, states_c, acfg: AdamConfig, stream=None):
+        """states_c: the result of adam_states (built once, reused every step)."""
+        flod_preprocess_bwd_adam(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity,
+                                 states_c, acfg, stream)
 
     def eval_counts(self):
         """Running counts of (pixel, Gaussian) pairs: (forward evaluations, backward

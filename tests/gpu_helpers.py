@@ -227,10 +227,10 @@ def clear_units(rast):
     rast.region("tiles_touched", torch.int32, U).zero_()
 
 
-def assert_grad_close(got: dict, ref: dict, what: str = ""):
+def assert_grad_close(got: dict, ref: dict, what: str = "", floor_abs: float = 0.0):
     """Both bars of the gradient parity: per parameter tensor, relative L2 error <= GRAD_REL,
-    and per entry |g - g_ref| <= GRAD_REL |g_ref| + GRAD_FLOOR max|g_ref| (max over the
-    compared entries of that tensor)."""
+    and per entry |g - g_ref| <= GRAD_REL |g_ref| + GRAD_FLOOR max|g_ref| + floor_abs (max over
+    the compared entries of that tensor; floor_abs is 0 except where a test derives one)."""
     for k in ref:
         a = np.asarray(got[k], dtype=np.float64).reshape(-1)
         b = np.asarray(ref[k], dtype=np.float64).reshape(-1)
@@ -240,7 +240,7 @@ def assert_grad_close(got: dict, ref: dict, what: str = ""):
             continue
         rel = np.linalg.norm(a - b) / nb
         assert rel <= GRAD_REL, f"{what} {k}: relative L2 error {rel:.2e}"
-        bound = GRAD_REL * np.abs(b) + GRAD_FLOOR * np.abs(b).max()
+        bound = GRAD_REL * np.abs(b) + GRAD_FLOOR * np.abs(b).max() + floor_abs
         bad = np.nonzero(np.abs(a - b) > bound)[0]
         assert bad.size == 0, (f"{what} {k}: {bad.size} of {b.size} entries off, worst "
                                f"|d|={np.abs(a - b)[bad].max():.3e} at |g_ref|={np.abs(b)[bad[0]]:.3e}")

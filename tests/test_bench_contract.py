@@ -55,3 +55,31 @@ def test_traffic_guard_rejects_changed_sources(tmp_path, monkeypatch):
     src.write_bytes(b"kernel source, edited\n")
     assert bench.measured_traffic("k_x") is None
     assert bench.measured_traffic("k_missing") is None
+
+
+def test_stage_work_and_rooflines():
+    w = bench.stage_work(n=1000, n_vis=600, pairs=5000, tiles=100, depth_passes=3, tile_passes=2,
+                         deg=3, evals=(1e6, 9e5, 4e5), pixels=200)
+    assert w["preprocess"] == ("hbm", 1000 * (236 + 84), "B")
+    assert w["tile_sort"] == ("hbm", 20 * 5000 * 2, "B")
+    assert w["bwd_adam"] == ("hbm", 1000 * (6 * 236 + 4) + 600 * 52, "B")
+    assert w["render_fwd"] == ("alu", 1e6 * bench.FLOP_FWD_EVAL + 4e5 * bench.FLOP_FWD_BLEND, "FLOP")
+    assert w["loss"][1] == 3 * 200 * bench.FLOP_LOSS_PX
+    roof = bench.rooflines({"preprocess": 0.5, "render_fwd": 2.0}, w, 6000.0, 80.0)
+    assert set(roof) == {"preprocess", "render_fwd"}
+    p = roof["preprocess"]
+    assert abs(p["achieved"] - 320000 / 0.5e-3 / 1e9) < 1e-9 and abs(p["frac"] - p["achieved"] / 6000.0) < 1e-12
+    assert roof["render_fwd"]["unit"] == "TFLOP/s"
+    assert abs(bench.alu_peak_tflops(152, 2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+
+
+def test_oracle_step_strata_cover_every_tile():
+    from paper_2408_12894_gb300 import synth
+    g = synth.gaussian_set(3, 3000, k=8, radius=20.0, sh_degree=3, s_mean=-2.0)
+    cam = synth.camera((0.0, 0.0, -40.0), 320, 180)
+    ost = bench.OracleStep(g, cam, 0.03125, slice_n=500, tiles=16)
+    assert ost.weight.sum() == ost.n_tiles == 20 * 12
+    assert len(ost.sample) == 16 and ost.sample.max() < ost.n_tiles
+    # ordered by pair count: the strata's representatives are non-decreasing in it
+    assert (ost.sample_pairs[1:] >= ost.sample_pairs[:-1]).all()
+    assert ost.step_seconds(threads=1) > 0
