@@ -724,10 +724,12 @@ def selective_sets(scale: float = 1.0):
 
 
 def selective_section(a):
-    """Per-view selective rendering (Eq. 6 per frame from the camera position) along the
-    32-frame path, forward only, at 1920x1080 and 3840x2160."""
+    """Selective rendering along the 32-frame path, forward only, at 1920x1080 and 3840x2160:
+    per-view selection (Eq. 6 every frame from the camera position) over resident levels; the
+    predetermined set (Sec. 5.2) gathered once into one compact resident set; and per-view
+    selection with the levels streamed from pinned host memory."""
     import torch
-    from paper_2408_12894_gb300 import flod, multiview, synth
+    from paper_2408_12894_gb300 import flod, multiview, selective, synth
     sets = selective_sets(a.scale)
     th = list(synth.SELECTIVE_THRESHOLDS[::-1])
     out = {"workload": "5-level scene x5 (radius 100), thresholds {10,25,50,100}, 32-frame path, "
@@ -755,7 +757,7 @@ def selective_section(a):
         units = st.rast.layout.units
         per_frame_bytes = [int(n * (236 + 84) + units * 4 + st.rast.pair_capacity * 16 + w * h * 20)
                            for n in sel]
-        out["resolutions"][f"{w}x{h}"] = {
+        res = {
             "fps": 1e3 / ms, "ms_per_frame": ms,
             "selected_per_frame": {"min": min(sel), "max": max(sel), "mean": sum(sel) / len(sel)},
             "selected_param_bytes_per_frame_mean": 236 * sum(sel) / len(sel),
@@ -763,6 +765,53 @@ def selective_section(a):
             "all_levels_param_bytes": 236 * sum(s.n for s in sets)}
         del st
         torch.cuda.empty_cache()
+        # predetermined set (Sec. 5.2): selected once from the mean camera position of the
+        # path, gathered into one compact resident set; frames render only that set
+        origin = selective.mean_camera_position(path)
+        compact, n_pre = selective.predetermined_set(sets, origin, th)
+        r = flod.Rasterizer([compact], [flod.view_struct(path[0])])
+        need = 0
+        for cam in path:
+            r.views[0] = flod.view_struct(cam)
+            r.refresh_structs()
+            r.forward()
+            torch.cuda.synchronize()
+            need = max(need, int(r.pair_count.item()))
+        r.pair_capacity = int(need * 1.1) + 4096
+        r._alloc()
+        outs = r.new_outputs()
+        fr = [0]
+
+        def pre_frame():
+            r.views[0] = flod.view_struct(path[fr[0] % len(path)])
+            r.refresh_structs()
+            fr[0] += 1
+            r.preprocess()
+            r.bin_sort()
+            r.render_fwd(*outs)
+        ms_pre = timed(pre_frame, max(a.steps, len(path)), 3)
+        res["predetermined"] = {"fps": 1e3 / ms_pre, "ms_per_frame": ms_pre, "selected": n_pre,
+                                "resident_param_bytes": 236 * n_pre,
+                                "resident_vs_all_levels": n_pre / sum(s.n for s in sets)}
+        del r, outs, compact
+        torch.cuda.empty_cache()
+        # per-view selection streamed from pinned host memory: only the means of every
+        # level and a buffer for the largest selection stay on the device
+        sl = selective.StreamedLevels(sets, th, capacity=int(max(sel) * 1.05) + 1024)
+        sl.size_capacity(path)
+        fr = [0]
+
+        def stream_frame():
+            sl.frame(path[fr[0] % len(path)])
+            fr[0] += 1
+        ms_st = timed(stream_frame, max(a.steps, len(path)), 3)
+        res["streamed_per_view"] = {"fps": 1e3 / ms_st, "ms_per_frame": ms_st,
+                                    "device_param_bytes": sl.device_bytes(),
+                                    "host_param_bytes": sl.host_bytes(),
+                                    "gathered_bytes_per_frame_mean": 224 * sum(sel) / len(sel)}
+        del sl
+        torch.cuda.empty_cache()
+        out["resolutions"][f"{w}x{h}"] = res
     del sets
     torch.cuda.empty_cache()
     return out

@@ -340,6 +340,24 @@ flod_status flod_preprocess_bwd_adam(const flod_gaussians *sets, int n_sets,
                                      uint64_t pair_capacity, const flod_adam_state *states,
                                      const flod_adam_config *acfg, flod_stream stream);
 
+/* Copies selected Gaussians of one or more sets into one compact set (structure of arrays):
+ * for k < min(*d_count, capacity), output Gaussian k is a copy of sets[e >> 28][e & mask]
+ * with e = entries[k] (entries may be NULL: then e = k, from set 0). Uses: the predetermined
+ * selective set of Sec. 5.2 (the entries of flod_select_levels from the mean training-camera
+ * position) made resident on its own instead of all levels; level chunks streamed from host
+ * memory (the source arrays may be pinned host memory mapped for the device: the copy then
+ * reads across the CPU-GPU link); pruned or densified sets.
+ * - out: device arrays with room for `capacity` Gaussians at out_sh_degree (quats and, at
+ *   degree 1 or 3, sh 16-byte aligned); SH coefficients beyond a source's degree are zero.
+ * - fold_s_min = 1: the source set's s_min is moved into the scale parameter,
+ *   s_opt' = log(exp(s_opt) + s_min), so the output renders at s_min = 0 with each
+ *   Gaussian's own Eq. 4 scale (Gaussians of several levels in one set); 0: s_opt copied.
+ * - out_s_min (optional, device float [capacity]): each output Gaussian's source s_min.
+ * Entries naming a missing set or index leave their output untouched. */
+flod_status flod_gather(const flod_gaussians *sets, int n_sets, const uint32_t *entries,
+                        const uint32_t *d_count, uint32_t capacity, const flod_param_arrays *out,
+                        int out_sh_degree, int fold_s_min, float *out_s_min, flod_stream stream);
+
 /* Eq. 6 with the thresholds of Eq. 7. levels[0..n_levels-1] are given coarse to fine.
  * d_thresh (host array of n_levels-1 floats, descending) gives d_proj of each level but the
  * last; if NULL, d_proj = s_min * focal / gamma (Eq. 7). The last level's band ends at 0 and

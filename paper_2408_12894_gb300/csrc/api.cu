@@ -609,6 +609,60 @@ flod_status flod_preprocess_bwd_adam(const flod_gaussians* sets, int n_sets, con
                     [&](const auto& B) { return launch_preprocess_bwd_adam(B, w, at, st); });
 }
 
+flod_status flod_gather(const flod_gaussians* sets, int n_sets, const uint32_t* entries,
+                        const uint32_t* d_count, uint32_t capacity, const flod_param_arrays* out,
+                        int out_sh_degree, int fold_s_min, float* out_s_min, flod_stream stream) {
+  if (!sets || n_sets < 1 || n_sets > FLOD_MAX_SETS || !d_count || !out || out_sh_degree < 0 ||
+      out_sh_degree > 3 || (fold_s_min != 0 && fold_s_min != 1))
+    return FLOD_ERR_INVALID_ARG;
+  if (capacity > 0 && (!all_set(out) || !aligned16(out->quats) ||
+                       ((out_sh_degree == 1 || out_sh_degree == 3) && !aligned16(out->sh))))
+    return FLOD_ERR_INVALID_ARG;
+  static thread_local GatherP g;
+  memset(&g, 0, sizeof(g));
+  for (int k = 0; k < n_sets; ++k) {
+    const flod_gaussians& S = sets[k];
+    if (S.n < 0 || S.n >= (1 << FLOD_SEL_SHIFT) || S.sh_degree < 0 || S.sh_degree > 3 ||
+        !(S.s_min >= 0.f))
+      return FLOD_ERR_INVALID_ARG;
+    if (S.n > 0 && (!S.means || !S.quats || !S.s_opt || !S.opacity_logit || !S.sh ||
+                    !aligned16(S.quats) || ((S.sh_degree == 1 || S.sh_degree == 3) && !aligned16(S.sh))))
+      return FLOD_ERR_INVALID_ARG;
+    const float* src[5] = {S.means, S.quats, S.s_opt, S.opacity_logit, S.sh};
+    if (S.n > 0) {
+      // device memory, or host memory the device can address (pinned: its device address);
+      // pageable host memory is refused here instead of faulting the kernel
+      for (int f = 0; f < 5; ++f) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, src[f]) != cudaSuccess) {
+          cudaGetLastError();
+          return FLOD_ERR_INVALID_ARG;
+        }
+        if (at.type == cudaMemoryTypeUnregistered || !at.devicePointer) return FLOD_ERR_INVALID_ARG;
+        src[f] = static_cast<const float*>(at.devicePointer);
+      }
+    }
+    g.sets[k] = SetP{src[0], src[1], src[2], src[3], src[4], S.n, S.sh_degree, S.s_min, 0};
+  }
+  g.n_sets = n_sets;
+  g.entries = entries;
+  g.d_count = d_count;
+  g.capacity = capacity;
+  g.out = *out;
+  g.out_s_min = out_s_min;
+  g.out_K3 = 3 * (out_sh_degree + 1) * (out_sh_degree + 1);
+  g.fold = fold_s_min;
+  if (capacity == 0) return FLOD_OK;
+  DevInfo* dev = nullptr;
+  flod_status s = device_info(&dev);
+  if (s != FLOD_OK) return s;
+  const uint64_t want = (capacity + 255u) / 256u;
+  const int grid = (int)(want < (uint64_t)dev->res_small ? want : (uint64_t)dev->res_small);
+  return launch_gather(g, grid > 0 ? grid : 1, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FLOD_OK
+             : FLOD_ERR_CUDA;
+}
+
 size_t flod_select_scratch_size(const flod_gaussians* levels, int n_levels) {
   if (!levels || n_levels < 1 || n_levels > FLOD_MAX_SETS) return 0;
   int ns[FLOD_MAX_SETS];

@@ -106,6 +106,20 @@ cudaError_t launch_adam(const AdamArrays* a, const flod_param_arrays* grads, con
                         cudaStream_t st);
 cudaError_t launch_adam_tick(uint32_t* d_step, cudaStream_t st);
 
+// gather.cu
+struct GatherP {
+  SetP sets[FLOD_MAX_SETS];
+  int n_sets;
+  const uint32_t* entries;   // (set << FLOD_SEL_SHIFT) | index, or NULL: index k of set 0
+  const uint32_t* d_count;   // entries to copy (device)
+  uint32_t capacity;         // at most this many
+  flod_param_arrays out;
+  float* out_s_min;          // optional: the source set's s_min of every output Gaussian
+  int out_K3;                // SH floats per output Gaussian
+  int fold;                  // 1: s_opt' = log(exp(s_opt) + s_min) (output at s_min = 0)
+};
+cudaError_t launch_gather(const GatherP& g, int grid, cudaStream_t st);
+
 // loss.cu
 size_t loss_scratch_bytes(const int* widths, const int* heights, int n, uint32_t* ctas,
                           uint64_t* pixels);

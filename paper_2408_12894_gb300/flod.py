@@ -127,6 +127,7 @@ def lib() -> C.CDLL:
         L.flod_loss.argtypes = [P, P, P, P, I, C.c_float, P, P, P, SZ, P]
         L.flod_adam_step.argtypes = [P, P, P, P, P, P, I, P, P]
         L.flod_preprocess_bwd_adam.argtypes = [P, I, P, I, P, P, SZ, U64, P, P, P]
+        L.flod_gather.argtypes = [P, I, P, P, C.c_uint32, P, I, I, P, P]
         L.flod_read_status.argtypes = [P, P, P]
         L.flod_status_string.argtypes = [I]
         L.flod_status_string.restype = C.c_char_p
@@ -135,7 +136,7 @@ def lib() -> C.CDLL:
                      "flod_render_fwd", "flod_render_bwd", "flod_blend_bwd",
                      "flod_preprocess_bwd", "flod_select_levels", "flod_select_levels_noalloc",
                      "flod_adjust_scale", "flod_read_status", "flod_loss", "flod_adam_step",
-                     "flod_preprocess_bwd_adam"):
+                     "flod_preprocess_bwd_adam", "flod_gather"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -412,6 +413,31 @@ def flod_preprocess_bwd_adam(sets, views, cfg, ws, pair_capacity, states_c, acfg
                                           ws.data_ptr(), ws.numel(), pair_capacity, states_c,
                                           C.byref(acfg), _stream(stream)),
            "flod_preprocess_bwd_adam")
+
+
+def flod_gather(sets, entries, d_count, capacity: int, out, out_sh_degree: int,
+                fold_s_min: bool = False, out_s_min=None, stream=None):
+    """sets: GaussianSets (or Gaussians structs, e.g. of host-mapped arrays); entries: device
+    int32 selection entries or None (identity over set 0); d_count: device int32 [1]; out:
+    five device tensors with room for `capacity` Gaussians."""
+    arr = _array(Gaussians, [g.struct() if isinstance(g, GaussianSet) else g for g in sets])
+    o = param_arrays(out)
+    _check(lib().flod_gather(arr, len(sets), _ptr(entries), d_count.data_ptr(), capacity,
+                             C.byref(o), out_sh_degree, int(fold_s_min), _ptr(out_s_min),
+                             _stream(stream)), "flod_gather")
+
+
+def gather_set(sets, entries, d_count, capacity: int, sh_degree: int, fold_s_min=True,
+               device="cuda", stream=None) -> "GaussianSet":
+    """A new GaussianSet of `capacity` Gaussians gathered by flod_gather (s_min 0 when folded;
+    entries past *d_count are left zero)."""
+    K = (sh_degree + 1) ** 2
+    out = [torch.zeros(capacity, 3, device=device), torch.zeros(capacity, 4, device=device),
+           torch.zeros(capacity, 3, device=device), torch.zeros(capacity, device=device),
+           torch.zeros(capacity, K, 3, device=device)]
+    flod_gather(sets, entries, d_count, capacity, out, sh_degree, fold_s_min, None, stream)
+    s_min = 0.0 if fold_s_min else (sets[0].s_min if isinstance(sets[0], GaussianSet) else sets[0].s_min)
+    return GaussianSet(*out, sh_degree=sh_degree, s_min=s_min)
 
 
 def flod_adjust_scale(s_opt: torch.Tensor, s_min_cur: float, s_min_next: float, stream=None):
