@@ -21,9 +21,10 @@ Modules and the passages they follow:
 * ``loss``        -- the training loss of every level, L1 + D-SSIM (Sec. 5.1.4, the Loss
                      step of Algorithm 1), and its gradient.
 * ``adam``        -- the Adam step of Algorithm 1 over one Gaussian set.
+* ``prune``       -- overlap pruning (Sec. 4.3): the three nearest neighbours by brute force.
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py`` against
 closed forms, library routines, brute force, finite differences or values the paper
 prints; none is "parity unpinned".
 """
-from . import adam, gaussians, loss, projection, raster, select, sh  # noqa: F401
+from . import adam, gaussians, loss, projection, prune, raster, select, sh  # noqa: F401
