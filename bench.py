@@ -102,6 +102,7 @@ def parse():
     ap.add_argument("--no-selective", action="store_true", help="skip the selective-rendering section")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-view section")
     ap.add_argument("--batched-views", type=int, default=64)
+    ap.add_argument("--no-pruning", action="store_true", help="skip the overlap-pruning section")
     return ap.parse_args()
 
 
@@ -681,6 +682,8 @@ def run_flod(a):
             line["selective"] = selective_section(a)
         if not a.no_batched:
             line["batched"] = batched_section(a)
+        if not a.no_pruning:
+            line["overlap_pruning"] = pruning_section(a)
         if not a.no_cpu_baseline and world == 1:
             try:
                 g_np = dict(g)
@@ -815,6 +818,47 @@ def selective_section(a):
     del sets
     torch.cuda.empty_cache()
     return out
+
+
+def pruning_section(a):
+    """Overlap pruning (Sec. 4.3) of level 4 of the 5-level scene (1M Gaussians, s_min 0.0625,
+    d_OP = 0.03125; it runs at every level but the last) right after a densification step
+    (10% of the Gaussians cloned and moved by N(0, d_OP^2)): the 3-nearest search and mask,
+    and the compaction of the kept Gaussians into a new set."""
+    import torch
+    from paper_2408_12894_gb300 import flod, synth
+    counts = tuple(int(round(c * a.scale)) for c in synth.LEVEL_COUNTS)
+    levels = synth.level_scene(counts=counts[:4])
+    d_op = 0.5 * synth.LEVEL_SMIN[3]
+    g = synth.with_jittered_clones(levels[3][0], 0.1, d_op)
+    gs = flod.GaussianSet.from_numpy(g, synth.LEVEL_SMIN[3])
+    n = gs.n
+    keep = torch.empty(n, dtype=torch.uint8, device="cuda")
+    kept = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    nb = flod.flod_prune_scratch_size(n)
+    scr = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    scr = scr[(-scr.data_ptr()) % 256:][:nb]
+    out = [torch.empty(n, 3, device="cuda"), torch.empty(n, 4, device="cuda"),
+           torch.empty(n, 3, device="cuda"), torch.empty(n, device="cuda"),
+           torch.empty(n, 16, 3, device="cuda")]
+
+    def mask():
+        flod.flod_overlap_prune(gs, d_op, keep, cnt, scr, out_kept=kept)
+
+    def prune_and_compact():
+        mask()
+        flod.flod_gather([gs], kept, cnt, n, out, 3, False)
+    ms_mask = timed(mask, max(10, a.steps // 4), 3)
+    ms_all = timed(prune_and_compact, max(10, a.steps // 4), 3)
+    m = int(cnt.item())
+    res = {"workload": f"level 4 of the 5-level scene with 10% jittered clones: {n} Gaussians, "
+                       f"d_OP = {d_op}",
+           "mask_ms": ms_mask, "prune_and_compact_ms": ms_all, "kept": m, "pruned": n - m,
+           "gaussians_per_s": n * 1e3 / ms_mask}
+    del gs, keep, kept, scr, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def batched_section(a):

@@ -65,6 +65,8 @@ typedef enum {
                                   sets it */
 #define FLOD_DEV_TILESET 0x4u  /* emission listed another tile count than tiles_touched
                                   (only with inconsistent per-unit inputs in the workspace) */
+#define FLOD_DEV_GRID 0x8u     /* flod_overlap_prune: the set spans more than 2^21 cells of
+                                  3 d_OP on an axis; nothing was pruned */
 
 #define FLOD_MAX_VIEWS 128
 #define FLOD_MAX_SETS 16
@@ -357,6 +359,25 @@ flod_status flod_preprocess_bwd_adam(const flod_gaussians *sets, int n_sets,
 flod_status flod_gather(const flod_gaussians *sets, int n_sets, const uint32_t *entries,
                         const uint32_t *d_count, uint32_t capacity, const flod_param_arrays *out,
                         int out_sh_degree, int fold_s_min, float *out_s_min, flod_stream stream);
+
+/* Scratch bytes of flod_overlap_prune for a set of n Gaussians. */
+size_t flod_prune_scratch_size(int n);
+
+/* Overlap pruning (Sec. 4.3): Gaussian i of `set` is removed when the average distance from
+ * its mean to the three nearest other means of the set, d_avg = (d1 + d2 + d3) / 3, is below
+ * d_op (the paper's d_OP = s_min / 2 of the level being trained). Only means within 3 d_op
+ * can make d_avg < d_op, so the search is exact over a uniform grid of that cell edge; a
+ * Gaussian with fewer than three others within 3 d_op is kept and its d_avg reported as
+ * +inf. Distances in float32 (each difference, square and sum rounded, correctly rounded
+ * square root, the mean of the three).
+ * Outputs (device): keep[n] (1 kept, 0 pruned); d_avg[n] (optional); out_kept[n] (optional:
+ * the kept indices in increasing order, ready as flod_gather entries of the set);
+ * *d_kept_count; *d_status (optional) = FLOD_DEV_GRID when the set's bounding box spans more
+ * than 2^21 cells on an axis (then every Gaussian is kept). scratch: device,
+ * flod_prune_scratch_size(n) bytes, 256-byte aligned, no initial contents. */
+flod_status flod_overlap_prune(const flod_gaussians *set, float d_op, uint8_t *keep, float *d_avg,
+                               uint32_t *out_kept, uint32_t *d_kept_count, uint32_t *d_status,
+                               void *scratch, size_t scratch_bytes, flod_stream stream);
 
 /* Eq. 6 with the thresholds of Eq. 7. levels[0..n_levels-1] are given coarse to fine.
  * d_thresh (host array of n_levels-1 floats, descending) gives d_proj of each level but the

@@ -663,6 +663,29 @@ flod_status flod_gather(const flod_gaussians* sets, int n_sets, const uint32_t* 
              : FLOD_ERR_CUDA;
 }
 
+size_t flod_prune_scratch_size(int n) {
+  if (n < 0 || n >= (1 << FLOD_SEL_SHIFT)) return 0;
+  return prune_scratch_bytes((uint32_t)n);
+}
+
+flod_status flod_overlap_prune(const flod_gaussians* set, float d_op, uint8_t* keep, float* d_avg,
+                               uint32_t* out_kept, uint32_t* d_kept_count, uint32_t* d_status,
+                               void* scratch, size_t scratch_bytes, flod_stream stream) {
+  if (!set || set->n < 0 || set->n >= (1 << FLOD_SEL_SHIFT) || !(d_op > 0.f) || !isfinite(d_op) ||
+      !d_kept_count || !scratch || (set->n > 0 && (!set->means || !keep)))
+    return FLOD_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(scratch) & 255u) return FLOD_ERR_INVALID_ARG;
+  if (scratch_bytes < prune_scratch_bytes((uint32_t)set->n)) return FLOD_ERR_WORKSPACE;
+  DevInfo* dev = nullptr;
+  flod_status s = device_info(&dev);
+  if (s != FLOD_OK) return s;
+  return launch_prune(set->means, (uint32_t)set->n, d_op, keep, d_avg, out_kept, d_kept_count,
+                      d_status, scratch, dev->res_small, reinterpret_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? FLOD_OK
+             : FLOD_ERR_CUDA;
+}
+
 size_t flod_select_scratch_size(const flod_gaussians* levels, int n_levels) {
   if (!levels || n_levels < 1 || n_levels > FLOD_MAX_SETS) return 0;
   int ns[FLOD_MAX_SETS];

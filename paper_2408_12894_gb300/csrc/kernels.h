@@ -120,6 +120,12 @@ struct GatherP {
 };
 cudaError_t launch_gather(const GatherP& g, int grid, cudaStream_t st);
 
+// prune.cu
+size_t prune_scratch_bytes(uint32_t n);
+cudaError_t launch_prune(const float* means, uint32_t n, float d_op, uint8_t* keep, float* d_avg,
+                         uint32_t* out_kept, uint32_t* d_kept, uint32_t* d_status, void* scratch,
+                         int grid, cudaStream_t st);
+
 // loss.cu
 size_t loss_scratch_bytes(const int* widths, const int* heights, int n, uint32_t* ctas,
                           uint64_t* pixels);

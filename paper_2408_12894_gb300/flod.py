@@ -28,6 +28,7 @@ MAX_PAIRS = (1 << 32) - 8192
 DEV_CAPACITY = 0x1
 DEV_TIMEOUT = 0x2
 DEV_TILESET = 0x4
+DEV_GRID = 0x8
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "pair capacity exceeded", 3: "device wait timed out",
           4: "CUDA error", 5: "unsupported device (needs sm_103)", 6: "workspace too small"}
@@ -128,6 +129,9 @@ def lib() -> C.CDLL:
         L.flod_adam_step.argtypes = [P, P, P, P, P, P, I, P, P]
         L.flod_preprocess_bwd_adam.argtypes = [P, I, P, I, P, P, SZ, U64, P, P, P]
         L.flod_gather.argtypes = [P, I, P, P, C.c_uint32, P, I, I, P, P]
+        L.flod_prune_scratch_size.argtypes = [I]
+        L.flod_prune_scratch_size.restype = SZ
+        L.flod_overlap_prune.argtypes = [P, C.c_float, P, P, P, P, P, P, SZ, P]
         L.flod_read_status.argtypes = [P, P, P]
         L.flod_status_string.argtypes = [I]
         L.flod_status_string.restype = C.c_char_p
@@ -136,7 +140,7 @@ def lib() -> C.CDLL:
                      "flod_render_fwd", "flod_render_bwd", "flod_blend_bwd",
                      "flod_preprocess_bwd", "flod_select_levels", "flod_select_levels_noalloc",
                      "flod_adjust_scale", "flod_read_status", "flod_loss", "flod_adam_step",
-                     "flod_preprocess_bwd_adam", "flod_gather"):
+                     "flod_preprocess_bwd_adam", "flod_gather", "flod_overlap_prune"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -438,6 +442,39 @@ def gather_set(sets, entries, d_count, capacity: int, sh_degree: int, fold_s_min
     flod_gather(sets, entries, d_count, capacity, out, sh_degree, fold_s_min, None, stream)
     s_min = 0.0 if fold_s_min else (sets[0].s_min if isinstance(sets[0], GaussianSet) else sets[0].s_min)
     return GaussianSet(*out, sh_degree=sh_degree, s_min=s_min)
+
+
+def flod_overlap_prune(gs: "GaussianSet", d_op: float, keep: torch.Tensor, d_kept: torch.Tensor,
+                       scratch: torch.Tensor, d_avg=None, out_kept=None, d_status=None,
+                       stream=None):
+    st = gs.struct()
+    _check(lib().flod_overlap_prune(C.byref(st), d_op, keep.data_ptr(), _ptr(d_avg),
+                                    _ptr(out_kept), d_kept.data_ptr(), _ptr(d_status),
+                                    scratch.data_ptr(), scratch.numel(), _stream(stream)),
+           "flod_overlap_prune")
+
+
+def overlap_prune(gs: "GaussianSet", d_op: float | None = None, stream=None):
+    """Overlap pruning of one level (Sec. 4.3) with d_OP = s_min / 2 by default: returns
+    (the pruned GaussianSet, the keep mask). Reads the kept count back (synchronises)."""
+    dev = gs.means.device
+    d_op = 0.5 * gs.s_min if d_op is None else d_op
+    n = gs.n
+    keep = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    kept = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    scr = torch.empty(flod_prune_scratch_size(n) + 256, dtype=torch.uint8, device=dev)
+    scr = scr[(-scr.data_ptr()) % 256:][:flod_prune_scratch_size(n)]
+    flod_overlap_prune(gs, d_op, keep, cnt, scr, out_kept=kept, stream=stream)
+    m = int(cnt.item())
+    out = gather_set([gs], kept, cnt, max(m, 1), gs.sh_degree, fold_s_min=False, device=dev,
+                     stream=stream)
+    return GaussianSet(*[getattr(out, f)[:m] for f in GaussianSet.FIELDS], gs.sh_degree,
+                       gs.s_min), keep[:n]
+
+
+def flod_prune_scratch_size(n: int) -> int:
+    return lib().flod_prune_scratch_size(int(n))
 
 
 def flod_adjust_scale(s_opt: torch.Tensor, s_min_cur: float, s_min_next: float, stream=None):

@@ -226,3 +226,22 @@ def batched_jobs(seed: int = 4, n_cams: int = 64, n_levels: int = 5, radius: flo
         r = selective_radius if job[i] == n_levels else radius
         cams.append(camera(d[i] * r, w, h))
     return cams, [int(j) for j in job]
+
+
+def with_jittered_clones(g: dict, frac: float, sigma: float, seed: int = 13) -> dict:
+    """A level right after a densification step: a fraction ``frac`` of its Gaussians (drawn
+    without replacement) appended again with their means moved by N(0, sigma^2) per axis and
+    every other parameter copied (the state overlap pruning is applied to)."""
+    rng = _rng(seed)
+    n = g["means"].shape[0]
+    pick = rng.choice(n, int(round(frac * n)), replace=False)
+    out = {}
+    for k, v in g.items():
+        if k == "sh_degree":
+            out[k] = v
+            continue
+        extra = v[pick].copy()
+        if k == "means":
+            extra = (extra + sigma * rng.standard_normal(extra.shape)).astype(np.float32)
+        out[k] = np.ascontiguousarray(np.concatenate([v, extra]))
+    return out
