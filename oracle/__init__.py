@@ -22,9 +22,11 @@ Modules and the passages they follow:
                      step of Algorithm 1), and its gradient.
 * ``adam``        -- the Adam step of Algorithm 1 over one Gaussian set.
 * ``prune``       -- overlap pruning (Sec. 4.3): the three nearest neighbours by brute force.
+* ``densify``     -- density control (Densification and Pruning of Algorithm 1): the
+                     2D-gradient statistics, clone, split and low-opacity pruning.
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py`` against
 closed forms, library routines, brute force, finite differences or values the paper
 prints; none is "parity unpinned".
 """
-from . import adam, gaussians, loss, projection, prune, raster, select, sh  # noqa: F401
+from . import adam, densify, gaussians, loss, projection, prune, raster, select, sh  # noqa: F401
