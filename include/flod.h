@@ -360,6 +360,44 @@ flod_status flod_gather(const flod_gaussians *sets, int n_sets, const uint32_t *
                         const uint32_t *d_count, uint32_t capacity, const flod_param_arrays *out,
                         int out_sh_degree, int fold_s_min, float *out_s_min, flod_stream stream);
 
+/* Density-control statistics (the Densification step of Algorithm 1; the backbone's rule):
+ * after flod_blend_bwd, for every unit that touches a tile, accum[set][i] += || dL/d mean2d ||
+ * with the 2D mean in normalised device coordinates (the pixel gradient times (W/2, H/2)) and
+ * denom[set][i] += 1, for Gaussian i of the unit's set (atomics; several views may render
+ * it). accum, denom: host arrays of n_sets device float pointers (NULL skips a set). The
+ * workspace must hold the backward's per-unit gradients (call before the next blending
+ * backward or preprocess of that workspace). Else as flod_blend_bwd. */
+flod_status flod_densify_stats(const flod_gaussians *sets, int n_sets, const flod_view *views,
+                               int n_views, const flod_raster_config *cfg, void *ws,
+                               size_t ws_bytes, uint64_t pair_capacity, float *const *accum,
+                               float *const *denom, flod_stream stream);
+
+/* Scratch bytes of flod_densify for a set of n Gaussians. */
+size_t flod_densify_scratch_size(int n);
+
+/* The density-control step of a level (Densification and Pruning of Algorithm 1, with the
+ * backbone's rules; the paper does not remove large Gaussians, Sec. 5.1.4). Per Gaussian,
+ * in float32: g = accum / denom (0 when denom is 0); s = exp(s_opt) + s_min (Eq. 4).
+ *   g >= tau and max(s) <= max_clone_scale: cloned (a copy appended);
+ *   g >= tau and max(s) > max_clone_scale: split into two children with means
+ *     mu + R(q) (s * eps), eps = normals[2i], normals[2i + 1] (standard-normal draws given by
+ *     the caller, [2n][3]), s_opt - log 1.6 (the learnable part of the scale over 1.6), every
+ *     other parameter copied; the parent is removed;
+ *   sigmoid(logit) < min_opacity: removed, with its clone or children.
+ * The new set, written to `out` (device arrays with room for `capacity` Gaussians; quats
+ * 16-byte aligned): the Gaussians kept in place by index, then the clones, then the
+ * children, two per split Gaussian. Adam moments (m_in, v_in -> m_out, v_out, all NULL or
+ * all given) follow the survivors and are zero for clones and children. *d_count = the new
+ * set's size (device; only the first `capacity` are written); d_counts3 (optional device
+ * [3]) = kept in place, clones, split Gaussians. scratch: flod_densify_scratch_size(n) bytes. */
+flod_status flod_densify(const flod_gaussians *set, const float *accum, const float *denom,
+                         const float *normals, float tau, float max_clone_scale,
+                         float min_opacity, const flod_param_arrays *m_in,
+                         const flod_param_arrays *v_in, const flod_param_arrays *out,
+                         const flod_param_arrays *m_out, const flod_param_arrays *v_out,
+                         uint32_t capacity, uint32_t *d_count, uint32_t *d_counts3,
+                         void *scratch, size_t scratch_bytes, flod_stream stream);
+
 /* Scratch bytes of flod_overlap_prune for a set of n Gaussians. */
 size_t flod_prune_scratch_size(int n);
 

@@ -663,6 +663,85 @@ flod_status flod_gather(const flod_gaussians* sets, int n_sets, const uint32_t* 
              : FLOD_ERR_CUDA;
 }
 
+flod_status flod_densify_stats(const flod_gaussians* sets, int n_sets, const flod_view* views,
+                               int n_views, const flod_raster_config* cfg, void* ws,
+                               size_t ws_bytes, uint64_t pair_capacity, float* const* accum,
+                               float* const* denom, flod_stream stream) {
+  static thread_local Plan P;
+  DevInfo* dev = nullptr;
+  if (!accum || !denom) return FLOD_ERR_INVALID_ARG;
+  flod_status s = common_checks(sets, n_sets, views, n_views, pair_capacity, cfg, ws, ws_bytes, P, &dev);
+  if (s != FLOD_OK) return s;
+  DensStatsP p;
+  memset(&p, 0, sizeof(p));
+  for (int k = 0; k < n_sets; ++k) {
+    if (!accum[k] != !denom[k]) return FLOD_ERR_INVALID_ARG;
+    p.accum[k] = accum[k];
+    p.denom[k] = denom[k];
+  }
+  const Ws w = ws_ptrs(ws, P);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return with_batch(sets, n_sets, views, n_views, cfg, P,
+                    [&](const auto& B) { return launch_dens_stats(B, w, p, st); });
+}
+
+size_t flod_densify_scratch_size(int n) {
+  if (n < 0 || n >= (1 << FLOD_SEL_SHIFT)) return 0;
+  return dens_scratch_bytes((uint32_t)n);
+}
+
+flod_status flod_densify(const flod_gaussians* set, const float* accum, const float* denom,
+                         const float* normals, float tau, float max_clone_scale,
+                         float min_opacity, const flod_param_arrays* m_in,
+                         const flod_param_arrays* v_in, const flod_param_arrays* out,
+                         const flod_param_arrays* m_out, const flod_param_arrays* v_out,
+                         uint32_t capacity, uint32_t* d_count, uint32_t* d_counts3,
+                         void* scratch, size_t scratch_bytes, flod_stream stream) {
+  if (!set || set->n < 0 || set->n >= (1 << FLOD_SEL_SHIFT) || set->sh_degree < 0 ||
+      set->sh_degree > 3 || !d_count || !scratch || !(tau >= 0.f) || !(max_clone_scale >= 0.f) ||
+      !(min_opacity >= 0.f))
+    return FLOD_ERR_INVALID_ARG;
+  if (set->n > 0 && (!set->means || !set->quats || !set->s_opt || !set->opacity_logit ||
+                     !set->sh || !accum || !denom || !normals || !aligned16(set->quats)))
+    return FLOD_ERR_INVALID_ARG;
+  if (capacity > 0 && (!all_set(out) || !aligned16(out->quats))) return FLOD_ERR_INVALID_ARG;
+  const int nm = (m_in != nullptr) + (v_in != nullptr) + (m_out != nullptr) + (v_out != nullptr);
+  if (nm != 0 && nm != 4) return FLOD_ERR_INVALID_ARG;
+  if (nm == 4 && (!all_set(m_in) || !all_set(v_in) || (capacity > 0 && (!all_set(m_out) || !all_set(v_out)))))
+    return FLOD_ERR_INVALID_ARG;
+  if (scratch_bytes < dens_scratch_bytes((uint32_t)set->n)) return FLOD_ERR_WORKSPACE;
+  DevInfo* dev = nullptr;
+  flod_status s = device_info(&dev);
+  if (s != FLOD_OK) return s;
+  DensP p;
+  memset(&p, 0, sizeof(p));
+  p.in = SetP{set->means, set->quats, set->s_opt, set->opacity_logit, set->sh, set->n,
+              set->sh_degree, set->s_min, 0};
+  p.n = (uint32_t)set->n;
+  p.s_min = set->s_min;
+  p.K3 = 3 * (set->sh_degree + 1) * (set->sh_degree + 1);
+  p.accum = accum;
+  p.denom = denom;
+  p.normals = normals;
+  p.tau = tau;
+  p.max_clone_scale = max_clone_scale;
+  p.min_opacity = min_opacity;
+  if (out) p.out = *out;
+  if (nm == 4) {
+    p.m_in = *m_in;
+    p.v_in = *v_in;
+    p.m_out = *m_out;
+    p.v_out = *v_out;
+    p.has_moments = 1;
+  }
+  p.capacity = capacity;
+  p.d_count = d_count;
+  p.d_counts3 = d_counts3;
+  return launch_densify(p, scratch, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FLOD_OK
+             : FLOD_ERR_CUDA;
+}
+
 size_t flod_prune_scratch_size(int n) {
   if (n < 0 || n >= (1 << FLOD_SEL_SHIFT)) return 0;
   return prune_scratch_bytes((uint32_t)n);

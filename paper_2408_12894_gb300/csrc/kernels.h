@@ -120,6 +120,33 @@ struct GatherP {
 };
 cudaError_t launch_gather(const GatherP& g, int grid, cudaStream_t st);
 
+// densify.cu
+struct DensStatsP {
+  float* accum[FLOD_MAX_SETS];   // per set (NULL: skipped)
+  float* denom[FLOD_MAX_SETS];
+};
+struct DensP {
+  SetP in;
+  uint32_t n;
+  float s_min;
+  int K3;
+  const float* accum;
+  const float* denom;
+  const float* normals;          // [2n, 3] standard normal draws for the split children
+  float tau, max_clone_scale, min_opacity;
+  flod_param_arrays out, m_in, v_in, m_out, v_out;
+  int has_moments;
+  uint32_t capacity;
+  uint32_t* d_count;
+  uint32_t* d_counts3;
+  uint32_t* blocks;
+  uint32_t nb;
+};
+template <int MAXV>
+cudaError_t launch_dens_stats(const Batch<MAXV>& b, const Ws& ws, const DensStatsP& p, cudaStream_t st);
+size_t dens_scratch_bytes(uint32_t n);
+cudaError_t launch_densify(DensP p, void* scratch, cudaStream_t st);
+
 // prune.cu
 size_t prune_scratch_bytes(uint32_t n);
 cudaError_t launch_prune(const float* means, uint32_t n, float d_op, uint8_t* keep, float* d_avg,

@@ -129,6 +129,11 @@ def lib() -> C.CDLL:
         L.flod_adam_step.argtypes = [P, P, P, P, P, P, I, P, P]
         L.flod_preprocess_bwd_adam.argtypes = [P, I, P, I, P, P, SZ, U64, P, P, P]
         L.flod_gather.argtypes = [P, I, P, P, C.c_uint32, P, I, I, P, P]
+        L.flod_densify_stats.argtypes = [P, I, P, I, P, P, SZ, U64, P, P, P]
+        L.flod_densify_scratch_size.argtypes = [I]
+        L.flod_densify_scratch_size.restype = SZ
+        L.flod_densify.argtypes = [P, P, P, P, C.c_float, C.c_float, C.c_float, P, P, P, P, P,
+                                   C.c_uint32, P, P, P, SZ, P]
         L.flod_prune_scratch_size.argtypes = [I]
         L.flod_prune_scratch_size.restype = SZ
         L.flod_overlap_prune.argtypes = [P, C.c_float, P, P, P, P, P, P, SZ, P]
@@ -140,7 +145,8 @@ def lib() -> C.CDLL:
                      "flod_render_fwd", "flod_render_bwd", "flod_blend_bwd",
                      "flod_preprocess_bwd", "flod_select_levels", "flod_select_levels_noalloc",
                      "flod_adjust_scale", "flod_read_status", "flod_loss", "flod_adam_step",
-                     "flod_preprocess_bwd_adam", "flod_gather", "flod_overlap_prune"):
+                     "flod_preprocess_bwd_adam", "flod_gather", "flod_overlap_prune",
+                     "flod_densify_stats", "flod_densify"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -473,6 +479,53 @@ def overlap_prune(gs: "GaussianSet", d_op: float | None = None, stream=None):
                        gs.s_min), keep[:n]
 
 
+def flod_densify_stats(sets, views, cfg, ws, pair_capacity, accum, denom, stream=None):
+    """accum, denom: per set a device float tensor [n] (or None to skip the set)."""
+    a = (C.c_void_p * len(accum))(*[_ptr(t) for t in accum])
+    d = (C.c_void_p * len(denom))(*[_ptr(t) for t in denom])
+    _check(lib().flod_densify_stats(sets, len(sets), views, len(views), C.byref(cfg),
+                                    ws.data_ptr(), ws.numel(), pair_capacity, a, d,
+                                    _stream(stream)), "flod_densify_stats")
+
+
+#: density-control settings of the 3DGS backbone (gradient threshold, the fraction of the
+#: scene extent below which a Gaussian is cloned rather than split, minimum opacity)
+DENSIFY_TAU, PERCENT_DENSE, MIN_OPACITY = 2e-4, 0.01, 0.005
+
+
+def densify(gs: "GaussianSet", accum, denom, normals, tau=DENSIFY_TAU, max_clone_scale=None,
+            extent: float = 1.0, min_opacity=MIN_OPACITY, m=None, v=None, stream=None):
+    """The density-control step of one level: returns (new GaussianSet, new m, new v,
+    (kept in place, clones, split)); m, v are five tensors each or None. Reads the new size
+    back (synchronises)."""
+    dev = gs.means.device
+    n = gs.n
+    mcs = PERCENT_DENSE * extent if max_clone_scale is None else max_clone_scale
+    cap = 3 * n + 1
+    K = (gs.sh_degree + 1) ** 2
+
+    def arrays():
+        return [torch.zeros(cap, 3, device=dev), torch.zeros(cap, 4, device=dev),
+                torch.zeros(cap, 3, device=dev), torch.zeros(cap, device=dev),
+                torch.zeros(cap, K, 3, device=dev)]
+    out = arrays()
+    mo, vo = (arrays(), arrays()) if m is not None else (None, None)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    c3 = torch.zeros(3, dtype=torch.int32, device=dev)
+    nb = lib().flod_densify_scratch_size(n)
+    scr = torch.empty(max(nb, 4), dtype=torch.uint8, device=dev)
+    st = gs.struct()
+    pa = [C.byref(param_arrays(x)) if x is not None else None for x in (m, v, out, mo, vo)]
+    _check(lib().flod_densify(C.byref(st), accum.data_ptr(), denom.data_ptr(), normals.data_ptr(),
+                              tau, mcs, min_opacity, pa[0], pa[1], pa[2], pa[3], pa[4], cap,
+                              cnt.data_ptr(), c3.data_ptr(), scr.data_ptr(), scr.numel(),
+                              _stream(stream)), "flod_densify")
+    k = int(cnt.item())
+    new = GaussianSet(*[t[:k] for t in out], gs.sh_degree, gs.s_min)
+    return (new, None if mo is None else [t[:k] for t in mo],
+            None if vo is None else [t[:k] for t in vo], tuple(int(x) for x in c3.cpu()))
+
+
 def flod_prune_scratch_size(n: int) -> int:
     return lib().flod_prune_scratch_size(int(n))
 
@@ -571,6 +624,11 @@ class Rasterizer:
         """states_c: the result of adam_states (built once, reused every step)."""
         flod_preprocess_bwd_adam(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity,
                                  states_c, acfg, stream)
+
+    def densify_stats(self, accum, denom, stream=None):
+        """Accumulate the density-control statistics of the last blending backward."""
+        flod_densify_stats(self.c_sets, self.c_views, self.cfg, self.ws, self.pair_capacity,
+                           accum, denom, stream)
 
     def eval_counts(self):
         """Running counts of (pixel, Gaussian) pairs: (forward evaluations, backward
