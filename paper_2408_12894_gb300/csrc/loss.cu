@@ -64,13 +64,20 @@ __device__ __forceinline__ int image_of_cta(const LossBatch& B, uint32_t c) {
 // and synchronises the CTA.
 __device__ __forceinline__ void stage_plane(float* dst, const float* __restrict__ src, int W, int H,
                                             int x0, int y0) {
-  for (int i = threadIdx.x; i < kLH * kLH; i += kLThreads) {
-    const int r = i / kLH, c = i % kLH;
-    const int gx = x0 - kLR + c, gy = y0 - kLR + r;
-    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-    const float* a = in ? src + (size_t)gy * W + gx : src;   // a valid address either way
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst + r * kLS + c)),
-                 "l"(a), "r"(in ? 4 : 0) : "memory");
+  // rows by warps, columns by lanes (no division per element)
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < kLH; r += kLThreads / 32) {
+    const int gy = y0 - kLR + r;
+    const bool rok = gy >= 0 && gy < H;
+    const float* row = src + (size_t)(rok ? gy : 0) * W;
+    const uint32_t d = smem_addr(dst + r * kLS);
+    for (int c = lane; c < kLH; c += 32) {
+      const int gx = x0 - kLR + c;
+      const bool in = rok && gx >= 0 && gx < W;
+      const float* a = in ? row + gx : src;   // a valid address either way
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d + 4u * c), "l"(a),
+                   "r"(in ? 4 : 0) : "memory");
+    }
   }
 }
 
@@ -271,6 +278,18 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_grad(const __grid_constant__
   cta_image(B, im, ch, x0, y0);
   const LossImg& I = B.img[im];
   const size_t base = 3 * I.pix_off + (size_t)ch * I.width * I.height;
+  const int tx = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * 4;
+  // this thread's four outputs' image and target values, requested first so that their
+  // latency passes under the staging and the window sums
+  float xv[4], yv[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gx = x0 + tx, gy = y0 + r0 + q;
+    const bool in = gx < I.width && gy < I.height;
+    const size_t p = base + (size_t)(in ? gy : 0) * I.width + (in ? gx : 0);
+    xv[q] = img[p];
+    yv[q] = tgt[p];
+  }
 #pragma unroll
   for (int v = 0; v < 3; ++v)
     stage_plane(S.f[v], maps + v * plane_total + base, I.width, I.height, x0, y0);
@@ -284,17 +303,15 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_grad(const __grid_constant__
   __syncthreads();
   float g[3][4];
   col_pass<3>(W, S.h, g);
-  const int tx = threadIdx.x % kLT, r0 = (threadIdx.x / kLT) * 4;
   const float kL1 = (1.f - B.lambda) * I.inv_n;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int gx = x0 + tx, gy = y0 + r0 + q;
     if (gx >= I.width || gy >= I.height) continue;
     const size_t p = base + (size_t)gy * I.width + gx;
-    const float xv = img[p], yv = tgt[p];
-    const float d = xv - yv;
+    const float d = xv[q] - yv[q];
     const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-    dL[p] = g[0][q] + 2.f * xv * g[1][q] + yv * g[2][q] + kL1 * sg;
+    dL[p] = g[0][q] + 2.f * xv[q] * g[1][q] + yv[q] * g[2][q] + kL1 * sg;
   }
   // the image's loss, by its first CTA: (1 - lambda) sum|x - y| / N + lambda (1 - sum S / N)
   if (loss && blockIdx.x == I.cta_off) {
