@@ -559,26 +559,34 @@ __device__ __forceinline__ void unit_backward(const Batch<MAXV>& b, const Ws& ws
   }
 }
 
-// Zero-fill of the gradient buffers of the sets marked in gt.zero: blockIdx.y picks one
-// (set, parameter) buffer, the CTAs of that row stride over it (16-byte stores where the
-// buffer allows them).
+// Zero-fill of the gradient buffers of the sets marked in gt.zero, over a flat index of
+// 16-byte chunks of every (set, parameter) buffer (so a 576 MB SH buffer gets its share of
+// the grid like a 12 MB one), scalar stores for unaligned buffers and ragged ends.
 struct ZeroSegs {
   float* p[5 * FLOD_MAX_SETS];
-  uint64_t n[5 * FLOD_MAX_SETS];
+  uint64_t n[5 * FLOD_MAX_SETS];            // floats of the buffer
+  uint64_t c0[5 * FLOD_MAX_SETS + 1];       // first chunk (4 floats) of each buffer
+  int ns;
 };
 
 __global__ void __launch_bounds__(256) k_zero_grads(const __grid_constant__ ZeroSegs z) {
   pdl_entry();
-  float* p = z.p[blockIdx.y];
-  const uint64_t n = z.n[blockIdx.y];
+  const uint64_t total = z.c0[z.ns];
   const uint64_t stride = (uint64_t)gridDim.x * 256u;
-  uint64_t i = (uint64_t)blockIdx.x * 256u + threadIdx.x;
-  if (!(reinterpret_cast<uintptr_t>(p) & 15u)) {
-    float4* q = reinterpret_cast<float4*>(p);
-    for (uint64_t k = i; k < n / 4; k += stride) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint64_t k = n / 4 * 4 + i; k < n; k += stride) p[k] = 0.f;
-  } else {
-    for (uint64_t k = i; k < n; k += stride) p[k] = 0.f;
+  for (uint64_t q = (uint64_t)blockIdx.x * 256u + threadIdx.x; q < total; q += stride) {
+    int lo = 0, hi = z.ns - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (z.c0[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    float* p = z.p[lo];
+    const uint64_t i = 4 * (q - z.c0[lo]);
+    const uint64_t n = z.n[lo];
+    if (i + 4 <= n && !(reinterpret_cast<uintptr_t>(p) & 15u)) {
+      *reinterpret_cast<float4*>(p + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (uint64_t k = i; k < n && k < i + 4; ++k) p[k] = 0.f;
+    }
   }
 }
 
@@ -616,6 +624,19 @@ __global__ void __launch_bounds__(kBA, 6) k_preprocess_bwd_adam(const __grid_con
   const int K3 = 3 * (S.deg + 1) * (S.deg + 1);
   const uint32_t g0 = u0 - V.unit_off;                 // the CTA's first Gaussian
   const uint32_t cnt = g0 < (uint32_t)S.n ? min((uint32_t)kBA, (uint32_t)S.n - g0) : 0u;
+  {
+    // request the Adam pass's lines (parameters and both moments of the CTA's chunk) into L2
+    // now, under the gradient pass (1.162 -> 1.129 ms at 3M Gaussians)
+    const AdamArrays& A0 = at.a[V.set];
+    for (int f = 0; f < 5; ++f) {
+      const uint64_t base = (uint64_t)per_gauss(f, K3) * g0;
+      const uint32_t bytes = 4u * (uint32_t)per_gauss(f, K3) * cnt;
+      const float* ptrs[3] = {A0.in[f], A0.m[f], A0.v[f]};
+      for (int a = 0; a < 3; ++a)
+        for (uint32_t o = threadIdx.x * 128u; o < bytes; o += kBA * 128u)
+          prefetch_l2(reinterpret_cast<const char*>(ptrs[a] + base) + o);
+    }
+  }
   const uint32_t u = u0 + threadIdx.x;
   int si = 0;
   uint32_t gi = 0;
@@ -680,6 +701,7 @@ template <int MAXV>
 cudaError_t launch_zero_grads(const Batch<MAXV>& b, const GradTable& gt, int grid, cudaStream_t st) {
   ZeroSegs z;
   int ns = 0;
+  uint64_t chunks = 0;
   for (int s = 0; s < b.n_sets; ++s) {
     if (!gt.zero[s] || b.sets[s].n == 0) continue;
     const uint64_t n = (uint64_t)b.sets[s].n;
@@ -691,11 +713,17 @@ cudaError_t launch_zero_grads(const Batch<MAXV>& b, const GradTable& gt, int gri
       if (!ptr[f]) continue;
       z.p[ns] = ptr[f];
       z.n[ns] = cnt[f];
+      z.c0[ns] = chunks;
+      chunks += (cnt[f] + 3) / 4;
       ++ns;
     }
   }
   if (!ns) return cudaSuccess;
-  launch_k(k_zero_grads, dim3((unsigned)max(1, grid / ns), (unsigned)ns), dim3(256), 0, st, z);
+  z.c0[ns] = chunks;
+  z.ns = ns;
+  const uint64_t want = (chunks + 2047) / 2048;   // about eight chunks per thread
+  const unsigned blocks = (unsigned)(want < (uint64_t)grid ? (want ? want : 1) : (uint64_t)grid);
+  launch_k(k_zero_grads, dim3(blocks), dim3(256), 0, st, z);
   return cudaGetLastError();
 }
 

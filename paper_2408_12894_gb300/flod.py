@@ -647,9 +647,16 @@ class Rasterizer:
         self._alloc()
         return False
 
-    def forward(self, stream=None):
-        """preprocess -> bin_sort (regrowing the pair capacity if needed) -> render_fwd."""
+    def forward(self, stream=None, check_capacity: bool = True):
+        """preprocess -> bin_sort (regrowing the pair capacity if needed) -> render_fwd.
+        check_capacity=False skips the host read of the pair count (no synchronisation; an
+        overflow then only sets FLOD_DEV_CAPACITY in the status word)."""
         out = self.new_outputs()
+        if not check_capacity:
+            self.preprocess(stream)
+            self.bin_sort(stream)
+            self.render_fwd(*out, stream)
+            return out
         for _ in range(3):
             self.preprocess(stream)
             self.bin_sort(stream)
@@ -698,8 +705,8 @@ def image_views(flat: torch.Tensor, views, channels: int = 1):
 
 class _Rasterize(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, rast: Rasterizer, *params):
-        rgb, T, nc = rast.forward()
+    def forward(ctx, rast: Rasterizer, check_capacity: bool, *params):
+        rgb, T, nc = rast.forward(check_capacity=check_capacity)
         ctx.rast = rast
         # the backward re-walks the workspace this forward sorted: remember which one
         ctx.generation = rast.generation
@@ -720,15 +727,16 @@ class _Rasterize(torch.autograd.Function):
         grads = [[torch.empty_like(getattr(s, f)) for f in GaussianSet.FIELDS] for s in rast.sets]
         rast.render_bwd(d_rgb.contiguous(), T, nc, grads, overwrite=rast.grad_modes())
         flat = [g for per_set in grads for g in per_set]
-        return (None, *flat)
+        return (None, None, *flat)
 
 
-def rasterize(rast: Rasterizer):
+def rasterize(rast: Rasterizer, check_capacity: bool = True):
     """Differentiable render of every view of ``rast``: returns (rgb, T, n_contrib), the
     concatenated per-view outputs; gradients flow to every parameter tensor of every set
-    (each set's tensors must have requires_grad set by the caller)."""
+    (each set's tensors must have requires_grad set by the caller). check_capacity=False
+    skips the pair-capacity read-back (for loops that sized the capacity once)."""
     params = [getattr(s, f) for s in rast.sets for f in GaussianSet.FIELDS]
-    return _Rasterize.apply(rast, *params)
+    return _Rasterize.apply(rast, check_capacity, *params)
 
 
 def focal_from_hfov(width: int, hfov_deg: float) -> float:

@@ -68,8 +68,13 @@ class BatchedStep:
         self.dL = dL
         self.graph = None
         if backward:
+            # gradients of the sets the jobs render (directly or through a selection); the
+            # others get none (NULL buffers: not written, not zero-filled)
+            rendered = set()
+            for j in self.jobs:
+                rendered.update(j.levels if j.levels is not None else [j.set_index])
             self.grads = [[torch.empty_like(getattr(s, f)) for f in flod.GaussianSet.FIELDS]
-                          for s in self.sets]
+                          if k in rendered else [None] * 5 for k, s in enumerate(self.sets)]
             # the library writes (mode 1) or zero-fills then accumulates (mode 2) every set's
             # gradients inside the step: no fill kernels of its own are needed here
             self.grads_c = flod.grads_struct(self.grads, self.rast.grad_modes())
