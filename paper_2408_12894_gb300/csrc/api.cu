@@ -606,7 +606,7 @@ flod_status flod_preprocess_bwd_adam(const flod_gaussians* sets, int n_sets, con
   const Ws w = ws_ptrs(ws, P);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   return with_batch(sets, n_sets, views, n_views, cfg, P,
-                    [&](const auto& B) { return launch_preprocess_bwd_adam(B, w, at, st); });
+                    [&](const auto& B) { return launch_preprocess_bwd_adam(B, w, at, dev->sms, st); });
 }
 
 flod_status flod_gather(const flod_gaussians* sets, int n_sets, const uint32_t* entries,

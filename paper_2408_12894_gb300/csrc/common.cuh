@@ -345,6 +345,19 @@ __device__ __forceinline__ void async_copy_wait() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Named CTA barriers (ids 1..15; 0 is __syncthreads) for producer / consumer hand-offs
+// between warp groups: `arrive` counts the calling warp in and goes on, `sync` waits until
+// n threads (a multiple of 32) have arrived or synced; both order the shared-memory
+// accesses before them against those after the barrier completes. The warps of both
+// groups stay resident in the same CTA, so every wait ends once the other group reaches
+// its matching arrive.
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
