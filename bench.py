@@ -656,6 +656,23 @@ def run_flod(a):
         t.requires_grad_(False)
     del ag, ag_dL
 
+    # ---- the same iteration captured once in a CUDA graph and replayed (no host launches)
+    reset()
+    ts.capture()
+    for _ in range(max(a.warmup, 3)):
+        ts.replay()
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(st)
+    for _ in range(a.steps):
+        ts.replay()
+    g1.record(st)
+    barrier()
+    graph_ms = g0.elapsed_time(g1) / a.steps
+    assert flod.flod_read_status(r.ws) == 0, "device status error (graph replay)"
+    ts.graph = None
+    graph_ms, = replicas.max_over_ranks([graph_ms], device="cuda")
+
     # ---- rooflines
     hbm, hbm_src = hbm_peak()
     mhz = clocks.get("sm_max_mhz") or 2070.0
@@ -694,6 +711,8 @@ def run_flod(a):
                        "parallelism": f"replicas x{world}"},
             "fwd_fps": world * 1e3 / fwd_ms, "fwd_ms": fwd_ms,
             "raster_fwd_bwd_it_s": world * 1e3 / raster_ms, "raster_fwd_bwd_ms": raster_ms,
+            "graph_replay": {"it_s": world * 1e3 / graph_ms, "ms": graph_ms,
+                             "what": "the same iteration captured once in a CUDA graph"},
             "autograd_path": {"it_s": 1e3 / autograd_ms, "ms": autograd_ms,
                               "what": "flod.rasterize under torch autograd + flod_loss + "
                                       "flod_adam_step on the .grad tensors (gradient then "

@@ -98,20 +98,24 @@ __device__ __forceinline__ Win2 win_pairs(const float (&win)[2 * kLR + 1]) {
 
 // Row pass: for every staged row and every output column, the window sum along the row of
 // NV values produced by `val(j)` from the staged arrays. out[v][row * kLT + col]. Items are
-// (staged row, 4 output columns).
+// (staged row, kRowCols output columns).
+constexpr int kRowCols = 4;
 template <int NV, typename F>
 __device__ __forceinline__ void row_pass(const Win2& W, float (*out)[kLH * kLT], F&& val) {
-  for (int it = threadIdx.x; it < kLH * (kLT / 4); it += kLThreads) {
-    const int r = it / (kLT / 4), c0 = (it % (kLT / 4)) * 4;
-    float2 acc[NV][2];
+  constexpr int NP = kRowCols / 2;   // output pairs per item
+  for (int it = threadIdx.x; it < kLH * (kLT / kRowCols); it += kLThreads) {
+    const int r = it / (kLT / kRowCols), c0 = (it % (kLT / kRowCols)) * kRowCols;
+    float2 acc[NV][NP];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v][0] = acc[v][1] = dup2(0.f);
+    for (int v = 0; v < NV; ++v)
 #pragma unroll
-    for (int j = 0; j < 2 * kLR + 4; ++j) {
+      for (int p = 0; p < NP; ++p) acc[v][p] = dup2(0.f);
+#pragma unroll
+    for (int j = 0; j < 2 * kLR + 2 + kRowCols - 2; ++j) {
       float e[NV];
       val(r * kLS + c0 + j, e);
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
+      for (int p = 0; p < NP; ++p) {
         const int m = j - 2 * p;
         if (m >= 0 && m <= 2 * kLR + 1) {
 #pragma unroll
@@ -122,10 +126,11 @@ __device__ __forceinline__ void row_pass(const Win2& W, float (*out)[kLH * kLT],
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       float* o = out[v] + r * kLT + c0;
-      o[0] = acc[v][0].x;
-      o[1] = acc[v][0].y;
-      o[2] = acc[v][1].x;
-      o[3] = acc[v][1].y;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        o[2 * p] = acc[v][p].x;
+        o[2 * p + 1] = acc[v][p].y;
+      }
     }
   }
 }
