@@ -623,7 +623,8 @@ constexpr int kBAAdam = 256;                    // Adam threads (eight warps)
 constexpr int kBAThreads = kBA + kBAAdam;
 constexpr int kBAUnroll = 2;                    // 16-byte slots per Adam thread and round
 constexpr int kBACtasPerSM = 2;
-constexpr int kBarFull = 1, kBarEmpty = 3;   // named barrier ids (two each)
+constexpr int kBAStages = 2;                  // shared gradient buffers per CTA
+constexpr int kBarFull = 1, kBarEmpty = 1 + kBAStages;   // named barrier ids (one per buffer each)
 
 struct ChunkInfo {
   int set, K3;
@@ -722,8 +723,8 @@ __global__ void __launch_bounds__(kBAThreads, kBACtasPerSM)
     // gradient group: chunk k of this CTA into buffer k % 2
     uint32_t k = 0;
     for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++k) {
-      const int s = k & 1;
-      if (k >= 2) named_sync(kBarEmpty + s, kBAThreads);
+      const int s = (int)(k % kBAStages);
+      if (k >= (uint32_t)kBAStages) named_sync(kBarEmpty + s, kBAThreads);
       const uint32_t u = c * (uint32_t)kBA + threadIdx.x;
       const ViewP& V = b.views[view_of_unit(b, u)];
       const SetP& S = b.sets[V.set];
@@ -740,11 +741,11 @@ __global__ void __launch_bounds__(kBAThreads, kBACtasPerSM)
     const int t = threadIdx.x - kBA;
     uint32_t k = 0;
     for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x, ++k) {
-      const int s = k & 1;
+      const int s = (int)(k % kBAStages);
       named_sync(kBarFull + s, kBAThreads);
       const ChunkInfo ci = chunk_info(b, ch);
       if (ci.cnt) adam_chunk(at.a[ci.set], at.h, c, buf[s], ci, t);
-      if (ch + 2 * gridDim.x < n_chunks) named_arrive(kBarEmpty + s, kBAThreads);
+      if (ch + kBAStages * gridDim.x < n_chunks) named_arrive(kBarEmpty + s, kBAThreads);
     }
   }
 }
@@ -808,7 +809,7 @@ template <int MAXV>
 cudaError_t launch_preprocess_bwd_adam(const Batch<MAXV>& b, const Ws& ws, const AdamTable& at,
                                        int sms, cudaStream_t st) {
   if (b.units) {
-    constexpr int smem = 2 * (int)sizeof(BwdAdamSmem);
+    constexpr int smem = kBAStages * (int)sizeof(BwdAdamSmem);
     static int per_sm = 0;   // resident CTAs per SM, once per template instance
     if (!per_sm) {
       cudaError_t e = cudaFuncSetAttribute(k_preprocess_bwd_adam<MAXV>,
