@@ -801,6 +801,9 @@ def selective_section(a):
         path = synth.camera_path(width=w, height=h)
         st = multiview.BatchedStep(sets, [multiview.Job(path[0], levels=[0, 1, 2, 3, 4], thresholds=th)],
                                    flod.default_config())
+        # the selection buffer (the view's units) sized to the path's longest selection + 10%
+        # instead of every Gaussian of the five levels
+        st.fit_selection({0: path}, headroom=1.1)
         # size the pairs for the whole path and record the selected working set per frame
         need, sel = 0, []
         for cam in path:
@@ -824,6 +827,7 @@ def selective_section(a):
             "fps": 1e3 / ms, "ms_per_frame": ms,
             "selected_per_frame": {"min": min(sel), "max": max(sel), "mean": sum(sel) / len(sel)},
             "selected_param_bytes_per_frame_mean": 236 * sum(sel) / len(sel),
+            "selection_capacity": st.selection_capacity(0),
             "working_set_bytes_per_frame_max": max(per_frame_bytes),
             "all_levels_param_bytes": 236 * sum(s.n for s in sets)}
         del st
@@ -944,6 +948,11 @@ def batched_section(a):
     jobs = [multiview.Job(c, levels=[0, 1, 2, 3, 4], thresholds=th) if j == 5
             else multiview.Job(c, set_index=5 + j) for c, j in zip(cams, job_ids)]
     dL = torch.as_tensor(synth.upstream_gradient(11, cams), device="cuda")
+    # each selective job's selection buffer sized to its selection + 10% (kept on the jobs,
+    # so the batch, the autotuner and the per-view arm all use the same units)
+    fit = multiview.BatchedStep(sets, jobs, flod.default_config(), backward=True, dL=dL)
+    fit.fit_selection(headroom=1.1)
+    del fit
     t0 = time.perf_counter()
     cfg, times = multiview.autotune(sets, jobs, backward=True, dL=dL, steps=2)
     tune_s = time.perf_counter() - t0

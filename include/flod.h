@@ -61,12 +61,15 @@ typedef enum {
 /* Device status bits (flod_read_status). */
 #define FLOD_DEV_CAPACITY 0x1u /* pairs exceeded pair_capacity: pairs beyond it dropped */
 #define FLOD_DEV_TIMEOUT 0x2u  /* reserved for a bounded device-side wait that gave up; no
-                                  kernel of this library spins on a flag or barrier, so none
-                                  sets it */
+                                  kernel of this library spins on a flag (its only waits are
+                                  barriers among the threads of one CTA), so none sets it */
 #define FLOD_DEV_TILESET 0x4u  /* emission listed another tile count than tiles_touched
                                   (only with inconsistent per-unit inputs in the workspace) */
 #define FLOD_DEV_GRID 0x8u     /* flod_overlap_prune: the set spans more than 2^21 cells of
                                   3 d_OP on an axis; nothing was pruned */
+#define FLOD_DEV_SELECTION 0x10u /* flod_preprocess: a view's *sel_count exceeded its
+                                    sel_capacity; the entries past the capacity were not
+                                    rendered (grow the selection buffer and the view) */
 
 #define FLOD_MAX_VIEWS 128
 #define FLOD_MAX_SETS 16
@@ -96,7 +99,9 @@ typedef struct {
   int set;                    /* index into the `sets` array when sel == NULL */
   const uint32_t *sel;        /* optional selection entries (set << 28) | index */
   const uint32_t *sel_count;  /* device count of valid entries of sel (with sel) */
-  uint32_t sel_capacity;      /* entries reserved for sel (the units of this view) */
+  uint32_t sel_capacity;      /* entries reserved for sel (the units of this view; a
+                                 *sel_count above it renders the first sel_capacity entries
+                                 and sets FLOD_DEV_SELECTION) */
 } flod_view;
 
 typedef struct {

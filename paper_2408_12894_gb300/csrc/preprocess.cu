@@ -170,6 +170,10 @@ __global__ void __launch_bounds__(kStageN) k_preprocess(const __grid_constant__ 
   const uint32_t u = blockIdx.x * (uint32_t)kStageN + threadIdx.x;
   const bool in_range = u < b.units;   // always true (units are padded to 1024); kept for safety
   const ViewP& V = b.views[view_of_unit(b, in_range ? u : 0u)];
+  // a selection longer than the view's units: reported once per view (its first CTA)
+  if (V.sel && threadIdx.x == 0 && blockIdx.x * (uint32_t)kStageN == V.unit_off &&
+      *V.sel_count > V.cap)
+    set_status(ws.status, FLOD_DEV_SELECTION);
   // a whole chunk of one set (no selection, all kStageN Gaussians present): stage it (the
   // condition is the same for every thread of the CTA, whose units lie in one view)
   const uint32_t local0 = blockIdx.x * (uint32_t)kStageN - V.unit_off;

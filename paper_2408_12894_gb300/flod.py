@@ -29,6 +29,7 @@ DEV_CAPACITY = 0x1
 DEV_TIMEOUT = 0x2
 DEV_TILESET = 0x4
 DEV_GRID = 0x8
+DEV_SELECTION = 0x10
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "pair capacity exceeded", 3: "device wait timed out",
           4: "CUDA error", 5: "unsupported device (needs sm_103)", 6: "workspace too small"}

@@ -24,11 +24,14 @@ class Job:
     """One camera and what it renders: ``set_index`` (a whole set) or, when ``levels`` is
     given, the selective mix of those set indices (coarse to fine) with ``thresholds``."""
 
-    def __init__(self, cam: dict, set_index: int = 0, levels=None, thresholds=None):
+    def __init__(self, cam: dict, set_index: int = 0, levels=None, thresholds=None,
+                 capacity: int | None = None):
         self.cam = cam
         self.set_index = set_index
         self.levels = None if levels is None else list(levels)
         self.thresholds = None if thresholds is None else [float(t) for t in thresholds]
+        # selection entries reserved (the view's units); None: every Gaussian of the levels
+        self.capacity = capacity
 
 
 class BatchedStep:
@@ -43,27 +46,7 @@ class BatchedStep:
         self.jobs = list(jobs)
         self.backward = backward
         self.cfg = cfg if cfg is not None else flod.default_config(persistent=1)
-        dev = self.sets[0].means.device
-        self.sel = []
-        views = []
-        for j in self.jobs:
-            if j.levels is None:
-                views.append(flod.view_struct(j.cam, j.set_index))
-                self.sel.append(None)
-            else:
-                lv = [self.sets[i] for i in j.levels]
-                cap = sum(s.n for s in lv)
-                buf = torch.zeros(cap, dtype=torch.int32, device=dev)
-                cnt = torch.zeros(1, dtype=torch.int32, device=dev)
-                scr = torch.zeros(max(flod.flod_select_scratch_size(lv), 4), dtype=torch.uint8,
-                                  device=dev)
-                # selection entries are (level index << 28) | i and index the sets array
-                # directly, so a selective job's levels must be sets 0 .. n-1
-                if j.levels != list(range(len(j.levels))):
-                    raise flod.FlodError("selective levels must be the first sets, in order")
-                self.sel.append((lv, buf, cnt, scr))
-                views.append(flod.view_struct(j.cam, 0, sel=buf, sel_count=cnt, sel_capacity=cap))
-        self.rast = flod.Rasterizer(self.sets, views, self.cfg, pair_capacity)
+        self._build(pair_capacity)
         self.out = self.rast.new_outputs()
         self.dL = dL
         self.graph = None
@@ -78,6 +61,67 @@ class BatchedStep:
             # the library writes (mode 1) or zero-fills then accumulates (mode 2) every set's
             # gradients inside the step: no fill kernels of its own are needed here
             self.grads_c = flod.grads_struct(self.grads, self.rast.grad_modes())
+
+    def _build(self, pair_capacity):
+        """Selection buffers, views and the rasterizer (workspace) for the jobs."""
+        dev = self.sets[0].means.device
+        self.sel = []
+        views = []
+        for j in self.jobs:
+            if j.levels is None:
+                views.append(flod.view_struct(j.cam, j.set_index))
+                self.sel.append(None)
+            else:
+                lv = [self.sets[i] for i in j.levels]
+                cap = sum(s.n for s in lv)
+                if j.capacity is not None:
+                    cap = max(1, min(cap, int(j.capacity)))
+                buf = torch.zeros(cap, dtype=torch.int32, device=dev)
+                cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+                scr = torch.zeros(max(flod.flod_select_scratch_size(lv), 4), dtype=torch.uint8,
+                                  device=dev)
+                # selection entries are (level index << 28) | i and index the sets array
+                # directly, so a selective job's levels must be sets 0 .. n-1
+                if j.levels != list(range(len(j.levels))):
+                    raise flod.FlodError("selective levels must be the first sets, in order")
+                self.sel.append((lv, buf, cnt, scr))
+                views.append(flod.view_struct(j.cam, 0, sel=buf, sel_count=cnt, sel_capacity=cap))
+        self.rast = flod.Rasterizer(self.sets, views, self.cfg, pair_capacity)
+        if getattr(self, "grads", None) is not None:
+            self.grads_c = flod.grads_struct(self.grads, self.rast.grad_modes())
+
+    def selection_capacity(self, i: int) -> int:
+        """Entries reserved for job i's selection (its view's units)."""
+        return int(self.sel[i][1].numel()) if self.sel[i] is not None else self.sets[self.jobs[i].set_index].n
+
+    def fit_selection(self, cams=None, headroom: float = 1.1, grow_only: bool = False):
+        """Size each selective job's selection buffer (its view's units) to the longest
+        selection over ``cams[i]`` (a list of cameras for job i; by default its current
+        camera) times ``headroom``, then rebuild the views and the workspace, keeping the
+        pair capacity (synchronises; invalidates a captured graph). Fewer units make every
+        stage that runs over a view's units cheaper; a later selection longer than the
+        capacity sets DEV_SELECTION in the device status and renders only the first
+        capacity entries."""
+        cams = cams or {}
+        changed = False
+        for i, (j, s) in enumerate(zip(self.jobs, self.sel)):
+            if s is None:
+                continue
+            lv, buf, cnt, scr = s
+            need = 0
+            for cam in cams.get(i, [j.cam]):
+                flod.flod_select_levels(lv, cam["cam_pos"], buf, cnt, scr, d_thresh=j.thresholds)
+                torch.cuda.synchronize()
+                need = max(need, int(cnt.item()))
+            cap = int(need * headroom) + 1024
+            if grow_only:
+                cap = max(cap, int(buf.numel()))
+            if cap != buf.numel():
+                j.capacity = cap
+                changed = True
+        if changed:
+            self._build(self.rast.pair_capacity)
+            self.graph = None
 
     def set_camera(self, i: int, cam: dict):
         """Move job i's camera (and, for a selective job, its selection origin). A captured
@@ -110,10 +154,14 @@ class BatchedStep:
             r.preprocess_bwd(self.grads_c, stream)
 
     def size_capacity(self, headroom: float = 1.15):
-        """Run once eagerly and grow the pair capacity to fit (synchronises)."""
+        """Run once eagerly and grow the pair capacity to fit, and any selection buffer
+        that the current cameras' selections overflow (synchronises)."""
         for _ in range(4):
             self.run()
             torch.cuda.synchronize()
+            if flod.flod_read_status(self.rast.ws) & flod.DEV_SELECTION:
+                self.fit_selection(grow_only=True)
+                continue
             need = int(self.rast.pair_count.item())
             if need <= self.rast.pair_capacity:
                 return need
@@ -141,7 +189,7 @@ class BatchedStep:
 def signature(sets, jobs, backward: bool):
     return (tuple(s.n for s in sets), backward,
             tuple((j.cam["width"], j.cam["height"], j.set_index,
-                   None if j.levels is None else tuple(j.levels)) for j in jobs))
+                   None if j.levels is None else tuple(j.levels), j.capacity) for j in jobs))
 
 
 _cache: dict = {}

@@ -155,3 +155,34 @@ def test_autotuner_picks_a_candidate():
     again, _ = multiview.autotune(sets, jobs[:3], steps=1, shapes=((16, 16), (8, 8)),
                                   batches=(256, 64))
     assert (again.tile_w, again.batch) == (cfg.tile_w, cfg.batch)
+
+
+def test_selection_capacity_fitted_renders_the_same_and_overflow_is_reported():
+    sets, jobs, _ = _scene()
+    j = jobs[2]                               # a selective job
+    full = multiview.BatchedStep(sets, [j], flod.default_config())
+    full.size_capacity()
+    torch.cuda.synchronize()
+    n_sel = full.selected_count(0)
+    img_full = full.out[0].clone()
+    # a selection buffer sized to the selection: the same units in the same order
+    small = multiview.BatchedStep(sets, [multiview.Job(j.cam, levels=j.levels, thresholds=j.thresholds)],
+                                  flod.default_config())
+    small.fit_selection(headroom=1.0)
+    assert small.selection_capacity(0) == n_sel + 1024
+    small.size_capacity()
+    torch.cuda.synchronize()
+    assert flod.flod_read_status(small.rast.ws) == 0
+    assert torch.equal(small.out[0], img_full)
+    # a buffer shorter than the selection: the status bit, then size_capacity grows it
+    short = multiview.BatchedStep(sets, [multiview.Job(j.cam, levels=j.levels, thresholds=j.thresholds,
+                                                       capacity=n_sel // 2)], flod.default_config())
+    assert short.selection_capacity(0) == n_sel // 2
+    short.run()
+    torch.cuda.synchronize()
+    assert flod.flod_read_status(short.rast.ws) & flod.DEV_SELECTION
+    short.size_capacity()
+    torch.cuda.synchronize()
+    assert short.selection_capacity(0) >= n_sel
+    assert flod.flod_read_status(short.rast.ws) == 0
+    assert torch.equal(short.out[0], img_full)
