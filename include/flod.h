@@ -428,7 +428,10 @@ flod_status flod_overlap_prune(const flod_gaussians *set, float d_op, uint8_t *k
  * the first level's at infinity. A Gaussian of level k is kept iff
  * d_thresh[k-1] > d >= d_thresh[k], d = ||mean - origin|| in float32. Writes the kept
  * entries (k << 28) | i to out_sel in (level, index) order and their number to *d_count
- * (device). scratch: device bytes of flod_select_scratch_size(). */
+ * (device). scratch: device bytes of flod_select_scratch_size() (a count per block of 2048
+ * Gaussians, then their keep bits); scratch_bytes of at least 4 (blocks + 1) hold the counts
+ * alone, which gives the same result with a second evaluation of Eq. 6 in the write kernel;
+ * less returns FLOD_ERR_WORKSPACE. */
 size_t flod_select_scratch_size(const flod_gaussians *levels, int n_levels);
 flod_status flod_select_levels(const flod_gaussians *levels, int n_levels, const float *d_thresh,
                                float gamma, float focal, const float origin[3],

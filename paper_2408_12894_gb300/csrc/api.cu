@@ -769,7 +769,8 @@ size_t flod_select_scratch_size(const flod_gaussians* levels, int n_levels) {
   if (!levels || n_levels < 1 || n_levels > FLOD_MAX_SETS) return 0;
   int ns[FLOD_MAX_SETS];
   for (int l = 0; l < n_levels; ++l) ns[l] = levels[l].n < 0 ? 0 : levels[l].n;
-  return 4 * (size_t)(select_blocks(ns, n_levels) + 1);
+  const size_t nb = select_blocks(ns, n_levels);
+  return 4 * (nb + 1 + nb * select_mask_words());   // block counts, then keep bits
 }
 
 flod_status flod_select_levels(const flod_gaussians* levels, int n_levels, const float* d_thresh,
@@ -809,8 +810,12 @@ flod_status flod_select_levels(const flod_gaussians* levels, int n_levels, const
   flod_status s = device_info(&dev);
   if (s != FLOD_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the keep bits when the scratch holds them (else the write kernel decides again)
+  uint32_t* counts = static_cast<uint32_t*>(scratch);
+  uint32_t* masks = nb && scratch_bytes >= 4 * ((size_t)nb + 1 + (size_t)nb * select_mask_words())
+                        ? counts + nb + 1 : nullptr;
   cudaError_t e = launch_select(lv, n_levels, lo, hi, origin, out_sel, sel_capacity, d_count,
-                                static_cast<uint32_t*>(scratch), nb, st);
+                                counts, masks, nb, st);
   return e == cudaSuccess ? FLOD_OK : FLOD_ERR_CUDA;
 }
 

@@ -228,9 +228,10 @@ cudaError_t launch_clear_status(uint32_t* status, cudaStream_t st);
 // select.cu
 cudaError_t launch_select(const SetP* levels, int n_levels, const float* thresh_lo,
                           const float* thresh_hi, const float origin[3], uint32_t* out,
-                          uint32_t cap, uint32_t* d_count, uint32_t* scratch, uint32_t n_blocks,
-                          cudaStream_t st);
+                          uint32_t cap, uint32_t* d_count, uint32_t* scratch, uint32_t* masks,
+                          uint32_t n_blocks, cudaStream_t st);
 uint32_t select_blocks(const int* ns, int n_levels);
+uint32_t select_mask_words();   // keep-bit words per selection block
 cudaError_t launch_adjust_scale(float* s_opt, int64_t n, float s_cur, float s_next,
                                 cudaStream_t st);
 

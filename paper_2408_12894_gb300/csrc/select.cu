@@ -6,6 +6,10 @@
 // difference, square and sum rounded to nearest, then a correctly rounded square root), so
 // that the decision is reproducible by any float32 implementation. Three launches: per-block
 // counts, one-CTA scan of the counts, ordered write. The output is in (level, index) order.
+// With room in the scratch, the count kernel also stores each block's keep bits (one ballot
+// word per warp and round), and the write kernel places the kept entries from those bits
+// and one 64-entry scan per block, without reading the means or deciding again; with only
+// the counts (the fixed scratch of the allocation-free entry point) it decides again.
 #include <mutex>
 
 #include "common.cuh"
@@ -43,18 +47,26 @@ __device__ __forceinline__ int level_of_block(const SelP& s, uint32_t blk) {
   return lv;
 }
 
+constexpr int kSelWords = kSelPerThread * (kSelThreads / 32);   // keep-bit words per block
+
 __global__ void __launch_bounds__(kSelThreads) k_sel_count(const __grid_constant__ SelP s,
-                                                           uint32_t* counts) {
+                                                           uint32_t* counts, uint32_t* masks) {
   pdl_entry();
   __shared__ uint32_t red[kSelThreads / 32];
   const int lv = level_of_block(s, blockIdx.x);
   const uint32_t i0 = blockIdx.x * (uint32_t)kSelBlock - s.start[lv];
   const uint32_t n = (uint32_t)s.lv[lv].n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t c = 0;
 #pragma unroll
   for (int j = 0; j < kSelPerThread; ++j) {
     const uint32_t i = i0 + j * kSelThreads + threadIdx.x;
-    if (i < n && sel_keep(s, lv, i)) ++c;
+    const bool keep = i < n && sel_keep(s, lv, i);
+    c += keep;
+    if (masks) {   // word (round j, warp wid): bit lane = Gaussian i0 + 256 j + 32 wid + lane
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) masks[(size_t)blockIdx.x * kSelWords + j * (kSelThreads / 32) + wid] = bal;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -106,7 +118,8 @@ __global__ void __launch_bounds__(1024) k_sel_scan(uint32_t* counts, uint32_t nb
 }
 
 __global__ void __launch_bounds__(kSelThreads) k_sel_write(const __grid_constant__ SelP s,
-                                                           const uint32_t* offsets, uint32_t* out,
+                                                           const uint32_t* offsets,
+                                                           const uint32_t* masks, uint32_t* out,
                                                            uint32_t cap) {
   pdl_entry();
   __shared__ uint32_t wcnt[kSelThreads / 32];
@@ -115,6 +128,36 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const __grid_constant
   const uint32_t i0 = blockIdx.x * (uint32_t)kSelBlock - s.start[lv];
   const uint32_t n = (uint32_t)s.lv[lv].n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (masks) {
+    static_assert(kSelWords == 64, "two keep-bit words per lane of one warp");
+    __shared__ uint32_t m[kSelWords], pre[kSelWords];
+    if (threadIdx.x < kSelWords) m[threadIdx.x] = masks[(size_t)blockIdx.x * kSelWords + threadIdx.x];
+    __syncthreads();
+    if (wid == 0) {   // exclusive prefix of the words' counts, in (round, warp) order
+      const uint32_t a = __popc(m[2 * lane]), b = __popc(m[2 * lane + 1]);
+      uint32_t x = a + b;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      pre[2 * lane] = x - a - b;
+      pre[2 * lane + 1] = x - b;
+    }
+    __syncthreads();
+    const uint32_t base = offsets[blockIdx.x];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kSelPerThread; ++j) {
+      const int q = j * (kSelThreads / 32) + wid;
+      const uint32_t bal = m[q];
+      if ((bal >> lane) & 1u) {
+        const uint32_t pos = base + pre[q] + __popc(bal & lt);
+        if (pos < cap) out[pos] = ((uint32_t)lv << FLOD_SEL_SHIFT) | (i0 + j * kSelThreads + threadIdx.x);
+      }
+    }
+    return;
+  }
   if (threadIdx.x == 0) base_s = offsets[blockIdx.x];
   // rounds of 256 consecutive Gaussians; inside a round, order = thread order
   for (int j = 0; j < kSelPerThread; ++j) {
@@ -139,7 +182,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const __grid_constant
 
 cudaError_t launch_select(const SetP* levels, int n_levels, const float* lo, const float* hi,
                           const float origin[3], uint32_t* out, uint32_t cap, uint32_t* d_count,
-                          uint32_t* scratch, uint32_t n_blocks, cudaStream_t st) {
+                          uint32_t* scratch, uint32_t* masks, uint32_t n_blocks, cudaStream_t st) {
   SelP s{};
   s.n_levels = n_levels;
   uint32_t g = 0;
@@ -158,11 +201,14 @@ cudaError_t launch_select(const SetP* levels, int n_levels, const float* lo, con
   if (n_blocks == 0) {
     return cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
   }
-  launch_k(k_sel_count, dim3(n_blocks), dim3(kSelThreads), 0, st, s, scratch);
+  launch_k(k_sel_count, dim3(n_blocks), dim3(kSelThreads), 0, st, s, scratch, masks);
   launch_k(k_sel_scan, dim3(1), dim3(1024), 0, st, scratch, n_blocks, d_count);
-  launch_k(k_sel_write, dim3(n_blocks), dim3(kSelThreads), 0, st, s, scratch, out, cap);
+  launch_k(k_sel_write, dim3(n_blocks), dim3(kSelThreads), 0, st, s, (const uint32_t*)scratch,
+           (const uint32_t*)masks, out, cap);
   return cudaGetLastError();
 }
+
+uint32_t select_mask_words() { return (uint32_t)kSelWords; }
 
 uint32_t select_blocks(const int* ns, int n_levels) {
   uint32_t b = 0;
