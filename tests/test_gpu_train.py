@@ -180,6 +180,54 @@ def test_fused_backward_adam_equals_gradient_then_adam():
     assert int(step_a.item()) == 2 and int(step_b.item()) == 2
 
 
+def test_fused_backward_adam_two_sets_ragged_and_many_chunks_per_cta():
+    # two sets, each rendered by its own view: 200,003 Gaussians at SH degree 3 (about five
+    # 128-Gaussian chunks per persistent CTA, so both shared buffers are reused) and 1,333 at
+    # degree 1 (a last chunk of 53: the scalar tails); the fused step against gradient then
+    # Adam, two steps
+    g1 = synth.gaussian_set(31, 200_003, k=16, radius=1.0, sh_degree=3, s_mean=-4.0)
+    g2 = synth.gaussian_set(32, 1_333, k=4, radius=1.0, sh_degree=1, s_mean=-3.0)
+    cams = [synth.camera((0.4, 0.2, -3.0), 96, 72), synth.camera((-0.3, 0.1, -2.5), 128, 96)]
+    dL = torch.as_tensor(synth.upstream_gradient(24, cams), device="cuda")
+    ra = rasterizer([g1, g2], cams, [0.01, 0.02], view_sets=[0, 1])
+    rb = rasterizer([g1, g2], cams, [0.01, 0.02], view_sets=[0, 1])
+    step_a = torch.zeros(1, dtype=torch.int32, device="cuda")
+    step_b = torch.zeros(1, dtype=torch.int32, device="cuda")
+    fa, fb, ga = [], [], []
+    for k in range(2):
+        pa = [getattr(ra.sets[k], f) for f in flod.GaussianSet.FIELDS]
+        pb = [getattr(rb.sets[k], f) for f in flod.GaussianSet.FIELDS]
+        fa.append((pa, [torch.zeros_like(t) for t in pa], [torch.zeros_like(t) for t in pa]))
+        fb.append((pb, [torch.zeros_like(t) for t in pb], [torch.zeros_like(t) for t in pb]))
+        ga.append([torch.empty_like(t) for t in pb])
+    states = flod.adam_states(fa)
+    for t in range(2):
+        rgb, T, nc = ra.forward()
+        ra.blend_bwd(dL, T, nc)
+        ra.preprocess_bwd_adam(states, flod.adam_config(LRS, step_a))
+        rgb2, T2, nc2 = rb.forward()
+        rb.blend_bwd(dL, T2, nc2)
+        rb.preprocess_bwd(flod.grads_struct(ga, overwrite=True))
+        flod.flod_adam_step([x[0] for x in fb], ga, [x[1] for x in fb], [x[2] for x in fb],
+                            [s.n for s in rb.sets], [s.sh_degree for s in rb.sets],
+                            flod.adam_config(LRS, step_b))
+        torch.cuda.synchronize()
+        for k in range(2):
+            for a, b in zip(fa[k][1], fb[k][1]):
+                assert torch.allclose(a, b, rtol=1e-4, atol=1e-7 * float(b.abs().max()) + 1e-30), (k, t)
+            for a, b in zip(fa[k][2], fb[k][2]):
+                assert torch.allclose(a, b, rtol=1e-4, atol=1e-7 * float(b.abs().max()) + 1e-30), (k, t)
+            for f, a, b, mbv in zip(flod.GaussianSet.FIELDS, fa[k][0], fb[k][0], fb[k][1]):
+                settled = mbv.abs() > 1e-3 * mbv.abs().max()
+                lr = torch.as_tensor(AD.lr_of(f, tuple(b.shape), LRS), device="cuda", dtype=torch.float32)
+                d = (a - b).abs()
+                tol = 4e-7 * b.abs() + 1e-3 * lr
+                assert bool((d <= tol)[settled].all()), (k, f, t)
+                # untouched entries (zero moments) keep their value on both paths
+                assert torch.equal(a[mbv == 0], b[mbv == 0]), (k, f, t)
+    assert int(step_a.item()) == 2 and int(step_b.item()) == 2
+
+
 def test_fused_backward_adam_first_step_matches_oracle():
     # one fused step from zero moments: m = (1 - beta1) g must hold the oracle's gradient, and
     # every parameter whose gradient is clear of zero moves by exactly lr against its sign
