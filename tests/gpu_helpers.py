@@ -227,20 +227,25 @@ def clear_units(rast):
     rast.region("tiles_touched", torch.int32, U).zero_()
 
 
-def assert_grad_close(got: dict, ref: dict, what: str = "", floor_abs: float = 0.0):
+def assert_grad_close(got: dict, ref: dict, what: str = "", floor_abs: float = 0.0,
+                      mag: dict | None = None):
     """Both bars of the gradient parity: per parameter tensor, relative L2 error <= GRAD_REL,
     and per entry |g - g_ref| <= GRAD_REL |g_ref| + GRAD_FLOOR max|g_ref| + floor_abs (max over
-    the compared entries of that tensor; floor_abs is 0 except where a test derives one)."""
+    the compared entries of that tensor; floor_abs is 0 except where a test derives one).
+    mag (optional, same keys and shapes): for a gradient that is a sum of separately computed
+    terms (views), the sum of the terms' magnitudes, which the per-entry relative bar is then
+    taken of (float32 rounds the terms, not their possibly cancelling sum)."""
     for k in ref:
         a = np.asarray(got[k], dtype=np.float64).reshape(-1)
         b = np.asarray(ref[k], dtype=np.float64).reshape(-1)
+        scale = np.abs(b) if mag is None else np.maximum(np.abs(b), np.asarray(mag[k], np.float64).reshape(-1))
         nb = np.linalg.norm(b)
         if nb == 0:
             assert np.all(a == 0), f"{what} {k}: nonzero gradient where the oracle's is zero"
             continue
         rel = np.linalg.norm(a - b) / nb
         assert rel <= GRAD_REL, f"{what} {k}: relative L2 error {rel:.2e}"
-        bound = GRAD_REL * np.abs(b) + GRAD_FLOOR * np.abs(b).max() + floor_abs
+        bound = GRAD_REL * scale + GRAD_FLOOR * np.abs(b).max() + floor_abs
         bad = np.nonzero(np.abs(a - b) > bound)[0]
         assert bad.size == 0, (f"{what} {k}: {bad.size} of {b.size} entries off, worst "
                                f"|d|={np.abs(a - b)[bad].max():.3e} at |g_ref|={np.abs(b)[bad[0]]:.3e}")
@@ -282,6 +287,28 @@ def tile_sample(ranges_tile, tiles_x, tiles_y, n, rng):
     extra = rng.choice(tiles_x * tiles_y, size=2, replace=False)
     picks |= set(int(t) for t in extra)
     return sorted(picks)
+
+
+def blended_gaussians(lists, ref_tiles):
+    """Candidates for sampled-gradient checks: the Gaussians of the oracle's tile lists, in
+    the sampled tiles it rendered, up to each tile's last blended position. A Gaussian behind
+    every pixel's stop (or culled) has an exactly zero gradient, and a sample of such
+    Gaussians would compare zeros with zeros."""
+    _, vals, ranges, _, _ = lists
+    out = set()
+    for t, (_, _, last) in ref_tiles.items():
+        s = int(ranges[t][0])
+        out.update(int(x) for x in vals[s:s + int(np.max(last))])
+    return np.array(sorted(out), dtype=np.int64)
+
+
+def assert_nonvacuous(ref, what="", min_frac=0.75):
+    """At least min_frac of the sampled Gaussians have a nonzero reference gradient."""
+    nz = None
+    for v in ref.values():
+        a = np.abs(np.asarray(v)).reshape(np.asarray(v).shape[0], -1).max(axis=1) > 0
+        nz = a if nz is None else (nz | a)
+    assert nz.mean() >= min_frac, f"{what}: only {int(nz.sum())} of {nz.size} sampled gradients are nonzero"
 
 
 def compare_tiles(img, T, nc, ref_tiles, pre, lists, cam, ocfg, gpu_lists=None):
