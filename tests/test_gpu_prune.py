@@ -84,8 +84,10 @@ def test_prune_full_level_four_sample():
     k, da = _run(means, d_op)
     rng = np.random.default_rng(6)
     n0 = synth.LEVEL_COUNTS[3]
+    # random Gaussians (nearly all kept) and every Gaussian the kernel pruned (up to 100)
     sample = np.concatenate([rng.choice(n0, 150, replace=False),
-                             n0 + rng.choice(means.shape[0] - n0, 150, replace=False)])
+                             n0 + rng.choice(means.shape[0] - n0, 150, replace=False),
+                             np.nonzero(~k)[0][:100]])
     m64 = means.astype(np.float64)
     for i in sample:
         dd = np.sqrt(((m64 - m64[i]) ** 2).sum(axis=1))
